@@ -1,0 +1,259 @@
+/*
+ * sc.h -- C ABI of libsc: all-edge spanning centrality (AESC) on one GPU.
+ *
+ * Method: Zhang, Yang, Tang, Xiao, Tang, "Efficient Approximation Algorithms
+ * for Spanning Centrality" (TGT / TGT+). The spanning centrality s(e) of an
+ * edge is the fraction of spanning trees that contain it (Definition 2.1);
+ * for an unweighted connected graph it equals the effective resistance, and
+ * the paper computes it from the truncated random-walk series of Eq. (2),
+ * accumulated per source node by a deterministic graph traversal
+ * (Algorithm 2) and, for TGT+, completed by random walks (Algorithm 4).
+ *
+ * Conventions shared by every entry point:
+ *  - Graphs are undirected, unweighted, connected and given as symmetric CSR:
+ *    row_ptr int32[n+1] (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz),
+ *    col_idx int32[nnz] with every row strictly increasing, no self-loops,
+ *    and both (i,j) and (j,i) present. nnz = 2m < 2^31.
+ *  - Per-edge outputs have one value per CSR entry, aligned with col_idx;
+ *    the entries (i,j) and (j,i) carry the same value.
+ *  - The caller owns every buffer it passes. A graph owns device copies of
+ *    its CSR and the work buffers it allocates; sc_graph_destroy frees them.
+ *  - All device work of a graph runs on the CUDA stream given to
+ *    sc_graph_create (NULL = legacy default stream). Calls return after
+ *    that work has completed unless stated otherwise. A graph must not be
+ *    used by two host threads at once.
+ *  - No C++ exception crosses this boundary. Each call returns an sc_status;
+ *    sc_last_error_detail() gives a thread-local message for the last
+ *    failing call of the calling thread.
+ *  - Device pointers must come from the CUDA device that was current when
+ *    the graph was created.
+ */
+#ifndef SC_H_
+#define SC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_ABI_VERSION 1
+
+typedef enum sc_status {
+    SC_OK = 0,
+    SC_ERR_INVALID_ARG = 1,        /* null pointer, negative size, bad option value */
+    SC_ERR_BAD_CSR = 2,            /* row_ptr not monotone / wrong ends, column out of range, row not strictly sorted */
+    SC_ERR_NOT_SYMMETRIC = 3,      /* some (i,j) has no (j,i) */
+    SC_ERR_SELF_LOOP = 4,
+    SC_ERR_DUPLICATE_EDGE = 5,
+    SC_ERR_ISOLATED_NODE = 6,      /* a node of degree 0 */
+    SC_ERR_DISCONNECTED = 7,
+    SC_ERR_BIPARTITE = 8,          /* only with SC_FLAG_REJECT_BIPARTITE */
+    SC_ERR_LAMBDA_NOT_CONVERGED = 9,
+    SC_ERR_BOUND_UNMET = 10,       /* an edge failed its tail check after the last allowed extension */
+    SC_ERR_TIMEOUT = 11,           /* a bounded device-side wait gave up */
+    SC_ERR_OOM = 12,
+    SC_ERR_CUDA = 13,
+    SC_ERR_UNSUPPORTED = 14
+} sc_status;
+
+/* ---- flags for sc_graph_create ---------------------------------------- */
+#define SC_PTRS_HOST 0u               /* row_ptr / col_idx are host pointers */
+#define SC_PTRS_DEVICE 1u             /* row_ptr / col_idx are device pointers */
+#define SC_FLAG_REJECT_BIPARTITE 2u   /* fail with SC_ERR_BIPARTITE on a bipartite graph */
+
+typedef struct sc_graph sc_graph;
+
+typedef struct sc_graph_info {
+    int32_t n;
+    int64_t nnz;          /* 2 m */
+    int64_t m;
+    int32_t min_degree;
+    int32_t max_degree;
+    int32_t bipartite;    /* 1 if the graph has no odd cycle */
+    int32_t diameter_lb;  /* eccentricity of node 0 (BFS depth), a lower bound on the diameter */
+} sc_graph_info;
+
+/*
+ * sc_graph_create -- validate a CSR graph and build its device copy.
+ * Cites: the input of Definition 2.2 (an undirected connected graph) and the
+ * notation of Section 2.1 (N(v), d(v), P = D^-1 A).
+ *
+ *   out     : receives the new graph (NULL on failure)
+ *   n       : number of nodes, >= 2
+ *   nnz     : number of CSR entries (2m), >= 2
+ *   row_ptr : int32[n+1], host or device per flags
+ *   col_idx : int32[nnz],  host or device per flags
+ *   flags   : SC_PTRS_HOST | SC_PTRS_DEVICE, optionally SC_FLAG_REJECT_BIPARTITE
+ *   stream  : cudaStream_t for all of this graph's work (NULL = default stream)
+ *
+ * Copies the arrays (the caller may free them on return), validates them on
+ * the device, builds the reverse-entry map and 1/d(v), and runs a BFS from
+ * node 0 for connectivity and the bipartite test. Errors: SC_ERR_BAD_CSR,
+ * SC_ERR_NOT_SYMMETRIC, SC_ERR_SELF_LOOP, SC_ERR_DUPLICATE_EDGE,
+ * SC_ERR_ISOLATED_NODE, SC_ERR_DISCONNECTED, SC_ERR_BIPARTITE, SC_ERR_OOM,
+ * SC_ERR_CUDA, SC_ERR_INVALID_ARG.
+ */
+sc_status sc_graph_create(sc_graph **out, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, uint32_t flags, void *stream);
+
+/* sc_graph_get_info -- sizes and structural facts found by sc_graph_create. */
+sc_status sc_graph_get_info(const sc_graph *g, sc_graph_info *out);
+
+/* sc_graph_destroy -- free the graph and its device memory (NULL is a no-op). */
+void sc_graph_destroy(sc_graph *g);
+
+/* ---- eigenvalue bound --------------------------------------------------- */
+
+typedef struct sc_lambda {
+    double lambda_plus;      /* largest eigenvalue of D^-1/2 A D^-1/2 below 1 (Ritz value) */
+    double lambda_minus;     /* smallest eigenvalue; for a bipartite graph the smallest above -1 */
+    double lambda_star;      /* max(|lambda_plus|, |lambda_minus|) plus the larger residual: the
+                                "second largest in absolute value" of Lemma 3.1 with a safety margin */
+    double residual_plus;    /* ||N y - theta y|| of the two Ritz pairs */
+    double residual_minus;
+    int32_t iterations;      /* Lanczos steps taken */
+    int32_t converged;       /* 1 if both residuals met the tolerance */
+} sc_lambda;
+
+typedef struct sc_lambda_opts {
+    int32_t max_iter;        /* Lanczos steps (0 = 500) */
+    double tol;              /* residual tolerance (0 = 1e-4); the residual is added to lambda_star */
+    uint64_t seed;           /* start vector (Philox4x32-10 stream) */
+} sc_lambda_opts;
+
+/*
+ * sc_estimate_lambda -- spectrum extremes of N = D^{1/2} P D^{-1/2}
+ * (Lemma 3.1), the lambda that sets the truncation length (Eq. 6, Alg. 1
+ * line 1). FP64 Lanczos with full reorthogonalisation on the device, after
+ * deflating the top eigenvector sqrt(d)/sqrt(2m) (and, for a bipartite graph,
+ * the bottom one). opts may be NULL for defaults. The result is also cached
+ * in the graph for sc_all_edges. SC_ERR_LAMBDA_NOT_CONVERGED is returned
+ * (with *out filled) when a residual stays above tol after max_iter steps.
+ */
+sc_status sc_estimate_lambda(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
+
+/*
+ * sc_truncation_length -- tau per edge and per source from Eq. (5)-(6)
+ * with omega = 2 (Alg. 1 line 1), Upsilon = Delta_t = 0:
+ *   f(e_ij, eps) = ceil( log(X_e / (eps (1 - lambda^2))) / log(1/lambda) - 1 ),
+ *   X_e = 1/d_i + 1/d_j - 2/(d_i d_j), tau_ij = smallest odd integer >= max(f, 1),
+ * tau_p(i) = max_j tau_ij (Alg. 2 line 4), ell_global = max_i tau_p(i).
+ *
+ *   eps            : > 0 (TGT uses eps, TGT+ passes eps/2, Alg. 4 line 2)
+ *   lam            : from sc_estimate_lambda; NULL = the graph's cached value
+ *                    (SC_ERR_INVALID_ARG if none); lambda_star must be < 1
+ *   ell_global_out : host int32 (may be NULL)
+ *   per_source_out : host int32[n] (may be NULL)
+ *   per_entry_out  : host int32[nnz] (may be NULL)
+ */
+sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
+                               int32_t *ell_global_out, int32_t *per_source_out,
+                               int32_t *per_entry_out);
+
+/* ---- the all-edge computation --------------------------------------------- */
+
+/* truncation policy */
+#define SC_ELL_GLOBAL 0     /* one length for every edge: max of Eq. (6) over all edges */
+#define SC_ELL_PER_EDGE 1   /* tau_ij of Eq. (6) per edge; sources run tau_p (Alg. 2 line 4) */
+#define SC_ELL_FIXED 2      /* opts.ell_fixed for every edge (no eigenvalue needed) */
+#define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP, extended until the
+                               a-posteriori tail bound meets eps (needs a loaded model) */
+
+/* storage precision of the propagated probability block */
+#define SC_PREC_FP64 0
+#define SC_PREC_FP32 1
+#define SC_PREC_BF16 2      /* bf16 storage, fp32 accumulation */
+
+/* estimator */
+#define SC_EST_PLAIN 0          /* S_tau of Eq. (2) */
+#define SC_EST_END_CORRECTED 1  /* S_tau + t_{tau+1}/2: exact for the lambda = -1 mode of a
+                                   bipartite graph, still a lower bound for odd tau */
+
+/* algorithm */
+#define SC_MODE_TGT 0           /* Algorithm 2: traversal only */
+#define SC_MODE_TGT_PLUS 1      /* Algorithm 4: traversal, then random walks (Eq. 11, 13, 14) */
+
+/* option flags */
+#define SC_OUT_DEVICE 1u        /* s_hat (and aux outputs) are device pointers (else host) */
+#define SC_OPT_RECORD_TAIL 2u   /* run 2 extra hops per source and report the tail bound */
+#define SC_OPT_TIME_KERNELS 4u  /* bracket every propagation launch with CUDA events (report.hop_ms) */
+
+typedef struct sc_options {
+    double eps;               /* absolute error target of Definition 2.2, 0 < eps < 1 */
+    int32_t mode;             /* SC_MODE_* */
+    int32_t precision;        /* SC_PREC_* */
+    int32_t ell_policy;       /* SC_ELL_* */
+    int32_t ell_fixed;        /* tau for SC_ELL_FIXED (>= 0) */
+    int32_t estimator;        /* SC_EST_* */
+    int32_t block_width;      /* sources per block B in {32, 64, 128}; 0 = choose automatically */
+    int32_t rows_split;       /* 16-byte vectors per lane in {1, 2, 4}; 0 = choose automatically */
+    int32_t heavy_threshold;  /* rows above this degree are split over a whole CTA (0 = 128) */
+    int32_t max_slices;       /* blocks propagated together in one launch (0 = fit the L2 budget) */
+    uint32_t flags;           /* SC_OUT_DEVICE | SC_OPT_RECORD_TAIL */
+    uint64_t seed;            /* Philox key for TGT+ walks */
+    double delta;             /* TGT+ failure probability (0 = 1/n, Section 5.1) */
+    int32_t gamma;            /* CalChi candidates (Alg. 3), default 10 when < 0 */
+    int32_t reserved[7];
+} sc_options;
+
+/* fills *opts with defaults: eps 1e-3, TGT, FP32, global length, plain estimator, auto B */
+void sc_options_default(sc_options *opts);
+
+typedef struct sc_report {
+    int32_t ell_global;        /* longest per-edge length used */
+    int32_t ell_min_source;    /* shortest / longest source run (hops) */
+    int32_t ell_max_source;
+    int32_t block_width;       /* B actually used */
+    int32_t rows_split;
+    int32_t slices;            /* blocks per launch */
+    int64_t blocks;            /* source blocks processed */
+    int64_t launches;          /* kernel launches issued */
+    int64_t hops;              /* sum over blocks of hops run */
+    double algorithmic_bytes;  /* bytes the propagation must move (CSR + block read + write per hop) */
+    double foster_sum;         /* sum over edges of s_hat; Foster's theorem: n - 1 for exact values */
+    double max_tail_bound;     /* with SC_OPT_RECORD_TAIL: max a-posteriori tail bound */
+    double lambda_star;        /* lambda used */
+    double propagate_ms;       /* device time of the traversal (events) */
+    double total_ms;
+    double hop_ms;             /* with SC_OPT_TIME_KERNELS: summed duration of the propagation launches */
+    int64_t hop_launches;      /* propagation (SpMM hop) launches */
+    double hop_bytes;          /* algorithmic bytes of those launches (part of algorithmic_bytes) */
+    int64_t walks;             /* TGT+: random walks drawn */
+    int32_t edges_extended;    /* learned policy: edges whose length was extended */
+    int32_t reserved[5];
+} sc_report;
+
+/*
+ * sc_all_edges -- estimate s(e) for every edge (Definition 2.2).
+ * TGT (Algorithm 2): blocks of B sources are propagated together, X_l =
+ * D^-1 A X_{l-1} (Alg. 2 lines 6-9 in pull form), and for each source i and
+ * neighbour j the half sum g(v_i, v_j) of Eq. (9) is accumulated (Alg. 2
+ * line 11) for the hops l <= tau_ij; the output is
+ * s_hat(e_ij) = g(v_i, v_j) + g(v_j, v_i) (Alg. 2 line 12), one length per
+ * edge for both halves.
+ *
+ *   opts       : NULL = defaults (sc_options_default)
+ *   s_hat      : double[nnz], host or device per SC_OUT_DEVICE
+ *   tail_bound : nullable double[nnz]; with SC_OPT_RECORD_TAIL the
+ *                a-posteriori bound on the remaining tail of each edge
+ *   report     : nullable
+ * The global and per-edge policies need lambda: sc_estimate_lambda is run
+ * first if the graph has no cached value. A bipartite graph under these
+ * policies fails with SC_ERR_UNSUPPORTED (lambda_star = 1: no finite length);
+ * use SC_ELL_FIXED or SC_ELL_LEARNED with the end-corrected estimator.
+ */
+sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
+                       sc_report *report);
+
+/* ---- status --------------------------------------------------------------- */
+const char *sc_status_string(sc_status s);
+const char *sc_last_error_detail(void);
+int32_t sc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_H_ */

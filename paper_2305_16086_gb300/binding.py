@@ -1,0 +1,272 @@
+"""ctypes binding of libsc (include/sc.h): argument marshalling only.
+
+Every computation happens inside libsc.so's CUDA kernels. PyTorch is used
+only to hold device memory and to name the CUDA stream. If libsc.so is
+missing or fails to load, ``load()`` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsc.so")
+
+# ---- constants mirrored from sc.h -------------------------------------------
+SC_OK = 0
+STATUS_NAMES = {
+    0: "SC_OK", 1: "SC_ERR_INVALID_ARG", 2: "SC_ERR_BAD_CSR", 3: "SC_ERR_NOT_SYMMETRIC",
+    4: "SC_ERR_SELF_LOOP", 5: "SC_ERR_DUPLICATE_EDGE", 6: "SC_ERR_ISOLATED_NODE",
+    7: "SC_ERR_DISCONNECTED", 8: "SC_ERR_BIPARTITE", 9: "SC_ERR_LAMBDA_NOT_CONVERGED",
+    10: "SC_ERR_BOUND_UNMET", 11: "SC_ERR_TIMEOUT", 12: "SC_ERR_OOM", 13: "SC_ERR_CUDA",
+    14: "SC_ERR_UNSUPPORTED",
+}
+SC_PTRS_HOST, SC_PTRS_DEVICE, SC_FLAG_REJECT_BIPARTITE = 0, 1, 2
+ELL = {"global": 0, "per_edge": 1, "fixed": 2, "learned": 3}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+EST = {"plain": 0, "end_corrected": 1}
+MODE = {"tgt": 0, "tgt_plus": 1}
+SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
+
+# every symbol include/sc.h declares
+EXPORTS = [
+    "sc_graph_create", "sc_graph_get_info", "sc_graph_destroy", "sc_estimate_lambda",
+    "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
+    "sc_last_error_detail", "sc_abi_version",
+]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("min_degree", ctypes.c_int32), ("max_degree", ctypes.c_int32),
+                ("bipartite", ctypes.c_int32), ("diameter_lb", ctypes.c_int32)]
+
+
+class Lambda(ctypes.Structure):
+    _fields_ = [("lambda_plus", ctypes.c_double), ("lambda_minus", ctypes.c_double),
+                ("lambda_star", ctypes.c_double), ("residual_plus", ctypes.c_double),
+                ("residual_minus", ctypes.c_double), ("iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32)]
+
+
+class LambdaOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("ell_policy", ctypes.c_int32), ("ell_fixed", ctypes.c_int32),
+                ("estimator", ctypes.c_int32), ("block_width", ctypes.c_int32),
+                ("rows_split", ctypes.c_int32), ("heavy_threshold", ctypes.c_int32),
+                ("max_slices", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("delta", ctypes.c_double), ("gamma", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("ell_global", ctypes.c_int32), ("ell_min_source", ctypes.c_int32),
+                ("ell_max_source", ctypes.c_int32), ("block_width", ctypes.c_int32),
+                ("rows_split", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("blocks", ctypes.c_int64), ("launches", ctypes.c_int64), ("hops", ctypes.c_int64),
+                ("algorithmic_bytes", ctypes.c_double), ("foster_sum", ctypes.c_double),
+                ("max_tail_bound", ctypes.c_double), ("lambda_star", ctypes.c_double),
+                ("propagate_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("hop_ms", ctypes.c_double), ("hop_launches", ctypes.c_int64), ("hop_bytes", ctypes.c_double),
+                ("walks", ctypes.c_int64), ("edges_extended", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class ScError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.name}: {detail}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsc.so and declare its C signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsc.so not found at {path}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.sc_graph_create.argtypes = [ctypes.POINTER(vp), i32, i64, vp, vp, u32, vp]
+    L.sc_graph_create.restype = ctypes.c_int
+    L.sc_graph_get_info.argtypes = [vp, ctypes.POINTER(GraphInfo)]
+    L.sc_graph_get_info.restype = ctypes.c_int
+    L.sc_graph_destroy.argtypes = [vp]
+    L.sc_graph_destroy.restype = None
+    L.sc_estimate_lambda.argtypes = [vp, ctypes.POINTER(LambdaOpts), ctypes.POINTER(Lambda)]
+    L.sc_estimate_lambda.restype = ctypes.c_int
+    L.sc_truncation_length.argtypes = [vp, f64, ctypes.POINTER(Lambda), i32p, i32p, i32p]
+    L.sc_truncation_length.restype = ctypes.c_int
+    L.sc_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.sc_options_default.restype = None
+    L.sc_all_edges.argtypes = [vp, ctypes.POINTER(Options), vp, vp, ctypes.POINTER(Report)]
+    L.sc_all_edges.restype = ctypes.c_int
+    L.sc_status_string.argtypes = [ctypes.c_int]
+    L.sc_status_string.restype = ctypes.c_char_p
+    L.sc_last_error_detail.argtypes = []
+    L.sc_last_error_detail.restype = ctypes.c_char_p
+    L.sc_abi_version.argtypes = []
+    L.sc_abi_version.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != SC_OK:
+        detail = load().sc_last_error_detail().decode(errors="replace")
+        raise ScError(status, where, detail)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr_and_flag(arr):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor of int32."""
+    try:
+        torch = _torch()
+        if isinstance(arr, torch.Tensor):
+            t = arr.contiguous().to(torch.int32)
+            return ctypes.c_void_p(t.data_ptr()), t.is_cuda, t
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(arr, dtype=np.int32)
+    return ctypes.c_void_p(a.ctypes.data), False, a
+
+
+class Graph:
+    """A validated graph resident on the GPU (wraps ``sc_graph``)."""
+
+    def __init__(self, row_ptr, col_idx, stream=None, reject_bipartite: bool = False):
+        L = load()
+        rp, rp_dev, keep_rp = _ptr_and_flag(row_ptr)
+        ci, ci_dev, keep_ci = _ptr_and_flag(col_idx)
+        if rp_dev != ci_dev:
+            raise ValueError("row_ptr and col_idx must both be host or both be device arrays")
+        n = int(keep_rp.shape[0]) - 1
+        nnz = int(keep_ci.shape[0])
+        flags = (SC_PTRS_DEVICE if rp_dev else SC_PTRS_HOST) | (SC_FLAG_REJECT_BIPARTITE if reject_bipartite else 0)
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.sc_graph_create(ctypes.byref(h), n, nnz, rp, ci, flags, self._stream), "sc_graph_create")
+        self._h = h
+        self.n, self.nnz = n, nnz
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        out = GraphInfo()
+        _check(load().sc_graph_get_info(self._h, ctypes.byref(out)), "sc_graph_get_info")
+        return {name: getattr(out, name) for name, _ in GraphInfo._fields_}
+
+    def estimate_lambda(self, max_iter: int = 0, tol: float = 0.0, seed: int = 0x1a2b3c4d,
+                        allow_unconverged: bool = False) -> dict:
+        opts = LambdaOpts(max_iter, tol, seed)
+        out = Lambda()
+        st = load().sc_estimate_lambda(self._h, ctypes.byref(opts), ctypes.byref(out))
+        if not (allow_unconverged and st == 9):
+            _check(st, "sc_estimate_lambda")
+        return {name: getattr(out, name) for name, _ in Lambda._fields_}
+
+    def truncation_length(self, eps: float, lam: dict | None = None):
+        """(ell_global, per_source int32[n], per_entry int32[nnz]) on the host."""
+        ell = ctypes.c_int32()
+        ps = np.empty(self.n, dtype=np.int32)
+        pe = np.empty(self.nnz, dtype=np.int32)
+        lp = None
+        if lam is not None:
+            lp = ctypes.byref(Lambda(*[lam[name] for name, _ in Lambda._fields_]))
+        _check(load().sc_truncation_length(
+            self._h, eps, lp, ctypes.byref(ell), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            pe.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "sc_truncation_length")
+        return int(ell.value), ps, pe
+
+    @staticmethod
+    def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
+                estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
+                record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None) -> Options:
+        o = Options()
+        load().sc_options_default(ctypes.byref(o))
+        o.eps = eps
+        o.mode = MODE[mode]
+        o.precision = PREC[precision]
+        o.ell_policy = ELL[policy]
+        o.ell_fixed = ell_fixed
+        o.estimator = EST[estimator]
+        o.block_width = block_width
+        o.rows_split = rows_split
+        o.heavy_threshold = heavy_threshold
+        o.max_slices = max_slices
+        o.flags = (SC_OPT_RECORD_TAIL if record_tail else 0) | (SC_OPT_TIME_KERNELS if time_kernels else 0)
+        if seed is not None:
+            o.seed = seed
+        o.delta = delta
+        if gamma is not None:
+            o.gamma = gamma
+        return o
+
+    def all_edges(self, out=None, tail_bound=None, **kw):
+        """Run sc_all_edges. ``out``/``tail_bound``: torch CUDA float64 tensors
+        of nnz entries (device output) or None (host numpy output).
+        Returns (s_hat, tail_bound or None, report dict)."""
+        o = self.options(**kw)
+        rep = Report()
+        if out is not None and not getattr(out, "is_cuda", False):
+            # caller-provided host buffer (e.g. a pinned torch tensor)
+            tb = ctypes.c_void_p(tail_bound.data_ptr()) if tail_bound is not None else None
+            _check(load().sc_all_edges(self._h, ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), tb,
+                                       ctypes.byref(rep)), "sc_all_edges")
+            return out, tail_bound, rep.as_dict()
+        if out is not None:
+            o.flags |= SC_OUT_DEVICE
+            tb = ctypes.c_void_p(tail_bound.data_ptr()) if tail_bound is not None else None
+            _check(load().sc_all_edges(self._h, ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), tb,
+                                       ctypes.byref(rep)), "sc_all_edges")
+            return out, tail_bound, rep.as_dict()
+        s = np.empty(self.nnz, dtype=np.float64)
+        b = np.empty(self.nnz, dtype=np.float64) if kw.get("record_tail") or kw.get("estimator") == "end_corrected" else None
+        _check(load().sc_all_edges(self._h, ctypes.byref(o), ctypes.c_void_p(s.ctypes.data),
+                                   ctypes.c_void_p(b.ctypes.data) if b is not None else None,
+                                   ctypes.byref(rep)), "sc_all_edges")
+        return s, b, rep.as_dict()

@@ -1,0 +1,163 @@
+// Internal helpers shared by the libsc translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sc.h"
+
+namespace sc {
+
+// ---------------------------------------------------------------------------
+// Error reporting: every ABI call returns a status; the detail string is
+// thread-local and describes the last failing call of the calling thread.
+// ---------------------------------------------------------------------------
+void set_detail(const char *fmt, ...);
+void clear_detail();
+
+struct Failure {
+    sc_status status;
+};
+
+#define SC_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ::sc::set_detail("%s:%d %s: %s", __FILE__, __LINE__, #call,                   \
+                             cudaGetErrorString(e_));                                     \
+            throw ::sc::Failure{e_ == cudaErrorMemoryAllocation ? SC_ERR_OOM : SC_ERR_CUDA}; \
+        }                                                                                 \
+    } while (0)
+
+#define SC_FAIL(status, ...)                     \
+    do {                                         \
+        ::sc::set_detail(__VA_ARGS__);           \
+        throw ::sc::Failure{status};             \
+    } while (0)
+
+#define SC_LAUNCH_CHECK() SC_CUDA(cudaGetLastError())
+
+// Wraps the body of an ABI function: converts Failure / std::bad_alloc into
+// a status so no exception leaves the library.
+template <typename F>
+sc_status guarded(F &&body) {
+    try {
+        clear_detail();
+        body();
+        return SC_OK;
+    } catch (const Failure &f) {
+        return f.status;
+    } catch (const std::bad_alloc &) {
+        set_detail("host allocation failed");
+        return SC_ERR_OOM;
+    } catch (...) {
+        set_detail("unexpected internal error");
+        return SC_ERR_CUDA;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device buffer with RAII ownership (plain cudaMalloc / cudaFree).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t count = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        count = 0;
+    }
+    // grow-only: keeps the old allocation if it is large enough
+    void reserve(size_t n) {
+        if (n <= count && ptr) return;
+        release();
+        if (n == 0) return;
+        SC_CUDA(cudaMalloc(reinterpret_cast<void **>(&ptr), n * sizeof(T)));
+        count = n;
+    }
+    T *get() const { return ptr; }
+};
+
+// ---------------------------------------------------------------------------
+// Element types of the propagated block.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct AccOf {
+    using type = float;
+};
+template <>
+struct AccOf<double> {
+    using type = double;
+};
+
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__device__ __forceinline__ T from_acc(typename AccOf<T>::type v);
+template <>
+__device__ __forceinline__ float from_acc<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double from_acc<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+inline int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+
+}  // namespace sc
+
+// ---------------------------------------------------------------------------
+// The graph object behind the opaque sc_graph handle.
+// ---------------------------------------------------------------------------
+struct sc_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t min_degree = 0, max_degree = 0;
+    int32_t bipartite = 0;
+    int32_t bfs_depth = 0;
+    int num_sms = 0;
+    size_t l2_bytes = 0;
+
+    sc::DevBuf<int32_t> row_ptr, col_idx, rev, level;
+    sc::DevBuf<float> inv_deg_f;
+    sc::DevBuf<double> inv_deg_d;
+    std::vector<int32_t> h_row_ptr;  // host copy of the row pointers (degrees, scheduling)
+
+    // heavy rows (degree > threshold), sorted by degree, for the CTA-split path
+    int32_t heavy_threshold_cached = -1;
+    sc::DevBuf<int32_t> heavy_rows;
+    int32_t n_heavy = 0;
+
+    // cached eigenvalue estimate
+    bool has_lambda = false;
+    sc_lambda lam{};
+
+    // work buffers (grow-only)
+    sc::DevBuf<unsigned char> xa, xb;   // probability blocks
+    sc::DevBuf<double> acc_g, acc_t1, acc_t2;
+    sc::DevBuf<int32_t> tau_entry, src_list, status;
+    sc::DevBuf<double> scratch_d;
+    std::vector<cudaEvent_t> hop_events;  // pairs bracketing timed propagation launches
+    ~sc_graph() {
+        for (cudaEvent_t e : hop_events) cudaEventDestroy(e);
+    }
+};
+
+namespace sc {
+void ensure_heavy_rows(sc_graph *g, int32_t threshold);
+void fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s);
+}

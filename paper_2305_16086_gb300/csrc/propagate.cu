@@ -1,0 +1,469 @@
+// sc_all_edges: the truncated graph traversal of Algorithm 2 (TGT) over
+// blocks of sources, the per-edge combine of Alg. 2 line 12, the
+// end-corrected estimator and the a-posteriori tail bound.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "propagate.cuh"
+
+namespace sc {
+
+sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
+void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_entry, int32_t *tau_src,
+                        int32_t *ell_global_host);
+
+// ---------------------------------------------------------------------------
+// accumulator initialisation and combine
+// ---------------------------------------------------------------------------
+// hop 0 of Eq. (9): p_0(v_i,v_i) - p_0(v_j,v_i) = 1 for every entry (Alg. 2 line 3, unscaled)
+__global__ void k_init_acc(double *g, double *t1, double *t2, int64_t nnz) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    g[k] = 1.0;
+    t1[k] = 0.0;
+    t2[k] = 0.0;
+}
+
+// s_hat(e_ij) = g(v_i,v_j) + g(v_j,v_i) (Alg. 2 line 12) with g = unscaled / d,
+// optionally + t_{tau+1}/2; tail bound from q = t_{tau+1} + t_{tau+2}.
+__global__ void k_combine(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                          const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                          const double *__restrict__ g, const double *__restrict__ t1, const double *__restrict__ t2,
+                          int32_t n, int end_corrected, int have_tail, double bound_scale,
+                          double *__restrict__ s_out, double *__restrict__ bound_out) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const double ir = inv_d[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t j = col[k], kr = rev[k];
+        const double ij = inv_d[j];
+        // explicit round-to-nearest products and sums (no FMA contraction), so that
+        // the entries (i,j) and (j,i) evaluate the same commutative expression
+        double s = __dadd_rn(__dmul_rn(g[k], ir), __dmul_rn(g[kr], ij));
+        if (have_tail) {
+            const double a = __dadd_rn(__dmul_rn(t1[k], ir), __dmul_rn(t1[kr], ij));
+            const double b = __dadd_rn(__dmul_rn(t2[k], ir), __dmul_rn(t2[kr], ij));
+            if (end_corrected) s = __dadd_rn(s, __dmul_rn(0.5, a));
+            if (bound_out) bound_out[k] = __dmul_rn(__dadd_rn(a, b), bound_scale);
+        }
+        s_out[k] = s;
+    }
+}
+
+// deterministic reductions: fixed grid, fixed per-thread order, fixed tree
+constexpr int kRedBlocks = 512, kRedThreads = 256;
+
+template <bool MAX>
+__global__ void k_reduce_partial(const double *__restrict__ x, int64_t count, double *__restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double acc = MAX ? -INFINITY : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < count; i += (int64_t)kRedBlocks * kRedThreads)
+        acc = MAX ? fmax(acc, x[i]) : acc + x[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = MAX ? fmax(sh[threadIdx.x], sh[threadIdx.x + w]) : sh[threadIdx.x] + sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+template <bool MAX>
+__global__ void k_reduce_final(const double *__restrict__ partial, double *__restrict__ out) {
+    __shared__ double sh[kRedBlocks];
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) sh[i] = partial[i];
+    __syncthreads();
+    for (int w = kRedBlocks / 2; w > 0; w >>= 1) {
+        for (int i = threadIdx.x; i < w; i += blockDim.x) sh[i] = MAX ? fmax(sh[i], sh[i + w]) : sh[i] + sh[i + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+double device_reduce(const double *x, int64_t count, bool max, double *scratch, cudaStream_t s) {
+    double h = 0.0;
+    if (max) {
+        k_reduce_partial<true><<<kRedBlocks, kRedThreads, 0, s>>>(x, count, scratch);
+        k_reduce_final<true><<<1, kRedThreads, 0, s>>>(scratch, scratch + kRedBlocks);
+    } else {
+        k_reduce_partial<false><<<kRedBlocks, kRedThreads, 0, s>>>(x, count, scratch);
+        k_reduce_final<false><<<1, kRedThreads, 0, s>>>(scratch, scratch + kRedBlocks);
+    }
+    SC_LAUNCH_CHECK();
+    SC_CUDA(cudaMemcpyAsync(&h, scratch + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// kernel dispatch over (precision, B, lane split)
+// ---------------------------------------------------------------------------
+struct HopCfg {
+    int prec, B, vpl;
+    size_t elem;
+};
+
+static size_t elem_size(int prec) { return prec == SC_PREC_FP64 ? 8 : (prec == SC_PREC_FP32 ? 4 : 2); }
+
+template <typename T>
+static const typename AccOf<T>::type *inv_deg_of(const sc_graph *g);
+template <>
+const double *inv_deg_of<double>(const sc_graph *g) { return g->inv_deg_d.get(); }
+template <>
+const float *inv_deg_of<float>(const sc_graph *g) { return g->inv_deg_f.get(); }
+template <>
+const float *inv_deg_of<__nv_bfloat16>(const sc_graph *g) { return g->inv_deg_f.get(); }
+
+template <typename T, int B, int VPL>
+static void launch_hop_t(const sc_graph *g, const void *xp, void *xn, int slices, int heavy_t, cudaStream_t s) {
+    using L = Layout<T, B, VPL>;
+    const int rows_per_cta = kSpmmWarps * L::G;
+    dim3 grid(g->n_heavy + ceil_div(g->n, rows_per_cta), slices);
+    k_spmm_hop<T, B, VPL><<<grid, kSpmmWarps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g),
+                                                          static_cast<const T *>(xp), static_cast<T *>(xn), g->n,
+                                                          heavy_t, g->heavy_rows.get(), g->n_heavy);
+}
+
+template <typename T, int B>
+static void launch_hop_b(const sc_graph *g, int vpl, const void *xp, void *xn, int slices, int heavy_t,
+                         cudaStream_t s) {
+    constexpr int V = B / (16 / static_cast<int>(sizeof(T)));
+    if (vpl == 1) {
+        if constexpr (V <= 32) {
+            launch_hop_t<T, B, 1>(g, xp, xn, slices, heavy_t, s);
+            return;
+        }
+    } else if (vpl == 2) {
+        if constexpr (V >= 2 && V / 2 <= 32) {
+            launch_hop_t<T, B, 2>(g, xp, xn, slices, heavy_t, s);
+            return;
+        }
+    } else if (vpl == 4) {
+        if constexpr (V >= 4 && V / 4 <= 32) {
+            launch_hop_t<T, B, 4>(g, xp, xn, slices, heavy_t, s);
+            return;
+        }
+    }
+    SC_FAIL(SC_ERR_INVALID_ARG, "unsupported lane split %d for B=%d", vpl, B);
+}
+
+template <typename T>
+static void launch_hop_p(const sc_graph *g, int B, int vpl, const void *xp, void *xn, int slices, int heavy_t,
+                         cudaStream_t s) {
+    switch (B) {
+    case 32: launch_hop_b<T, 32>(g, vpl, xp, xn, slices, heavy_t, s); break;
+    case 64: launch_hop_b<T, 64>(g, vpl, xp, xn, slices, heavy_t, s); break;
+    case 128: launch_hop_b<T, 128>(g, vpl, xp, xn, slices, heavy_t, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d not in {32, 64, 128}", B);
+    }
+}
+
+void launch_hop(const sc_graph *g, const HopCfg &c, const void *xp, void *xn, int slices, int heavy_t,
+                cudaStream_t s) {
+    switch (c.prec) {
+    case SC_PREC_FP64: launch_hop_p<double>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
+    case SC_PREC_FP32: launch_hop_p<float>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
+    case SC_PREC_BF16: launch_hop_p<__nv_bfloat16>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", c.prec);
+    }
+    SC_LAUNCH_CHECK();
+}
+
+template <typename T, int B>
+static void first_gather_t(const sc_graph *g, bool first, const void *x, const int32_t *src, int nsrc,
+                           const int32_t *tau, int ell, double *acc_g, double *acc_t1, double *acc_t2,
+                           cudaStream_t s) {
+    const int warps = 8;
+    const int blocks = ceil_div(nsrc, warps);
+    if (first)
+        k_first_hop<T, B><<<blocks, warps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g), src,
+                                                         nsrc, static_cast<T *>(const_cast<void *>(x)), g->n);
+    else
+        k_gather<T, B><<<blocks, warps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), static_cast<const T *>(x),
+                                                      g->n, src, nsrc, tau, ell, acc_g, acc_t1, acc_t2);
+}
+
+template <typename T>
+static void first_gather_p(const sc_graph *g, int B, bool first, const void *x, const int32_t *src, int nsrc,
+                           const int32_t *tau, int ell, double *a, double *b, double *c, cudaStream_t s) {
+    switch (B) {
+    case 32: first_gather_t<T, 32>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
+    case 64: first_gather_t<T, 64>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
+    case 128: first_gather_t<T, 128>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
+    }
+}
+
+void launch_first_or_gather(const sc_graph *g, const HopCfg &c, bool first, const void *x, const int32_t *src,
+                            int nsrc, const int32_t *tau, int ell, double *a, double *b, double *cc,
+                            cudaStream_t s) {
+    switch (c.prec) {
+    case SC_PREC_FP64: first_gather_p<double>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    case SC_PREC_FP32: first_gather_p<float>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    }
+    SC_LAUNCH_CHECK();
+}
+
+// default lane split: 16 lanes per row for wide rows, whole warp otherwise
+static int default_vpl(int prec, int B) {
+    const int V = B / (16 / static_cast<int>(elem_size(prec)));
+    if (V > 32) return V / 32;           // fp64 B=128: 2
+    return V >= 16 ? (V / 16) : 1;      // 16 lanes per row where possible
+}
+
+static int default_block_width(int prec) { return prec == SC_PREC_FP64 ? 64 : (prec == SC_PREC_FP32 ? 64 : 128); }
+
+// ---------------------------------------------------------------------------
+// the driver
+// ---------------------------------------------------------------------------
+static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep) {
+    if (!g || !s_hat) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or output");
+    sc_options o;
+    if (o_in) o = *o_in;
+    else sc_options_default(&o);
+    if (!(o.eps > 0.0 && o.eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1), got %g", o.eps);
+    if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
+    if (o.mode != SC_MODE_TGT) SC_FAIL(SC_ERR_UNSUPPORTED, "mode %d is not available in sc_all_edges yet", o.mode);
+    if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_PER_EDGE && o.ell_policy != SC_ELL_FIXED)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "length policy %d", o.ell_policy);
+    if (o.ell_policy == SC_ELL_FIXED && o.ell_fixed < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_fixed < 0");
+    if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
+    const bool out_dev = (o.flags & SC_OUT_DEVICE) != 0;
+    const bool time_kernels = (o.flags & SC_OPT_TIME_KERNELS) != 0;
+    const bool record_tail = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
+    const bool need_lambda = o.ell_policy != SC_ELL_FIXED || record_tail;
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n;
+    const int64_t nnz = g->nnz;
+
+    cudaEvent_t ev0, ev1, ev2;
+    SC_CUDA(cudaEventCreate(&ev0));
+    SC_CUDA(cudaEventCreate(&ev1));
+    SC_CUDA(cudaEventCreate(&ev2));
+    struct EvGuard {
+        cudaEvent_t a, b, c;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaEventDestroy(c);
+        }
+    } evg{ev0, ev1, ev2};
+    SC_CUDA(cudaEventRecord(ev0, s));
+
+    if (need_lambda && !g->has_lambda) {
+        sc_lambda lam;
+        sc_status st = estimate_lambda_impl(g, nullptr, &lam);
+        if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
+    }
+    if (o.ell_policy != SC_ELL_FIXED && (g->bipartite || g->lam.lambda_star >= 1.0))
+        SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1 (bipartite graph): no finite length meets eps; use a fixed or "
+                                    "learned length with the end-corrected estimator");
+
+    // ---- truncation lengths --------------------------------------------------
+    g->tau_entry.reserve(nnz);
+    DevBuf<int32_t> tau_src;
+    tau_src.reserve(n);
+    std::vector<int32_t> h_tau_src(n);
+    int32_t ell_global = 0;
+    if (o.ell_policy == SC_ELL_FIXED) {
+        ell_global = o.ell_fixed;
+        std::fill(h_tau_src.begin(), h_tau_src.end(), o.ell_fixed);
+        fill_i32(g->tau_entry.get(), nnz, o.ell_fixed, s);
+    } else {
+        tau_entries_device(g, o.eps, g->lam.lambda_star, g->tau_entry.get(), tau_src.get(), &ell_global);
+        if (o.ell_policy == SC_ELL_GLOBAL) {
+            std::fill(h_tau_src.begin(), h_tau_src.end(), ell_global);
+            fill_i32(g->tau_entry.get(), nnz, ell_global, s);
+        } else {
+            SC_CUDA(cudaMemcpyAsync(h_tau_src.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        }
+        SC_CUDA(cudaStreamSynchronize(s));
+    }
+    const int extra = record_tail ? 2 : 0;
+
+    // ---- block configuration -------------------------------------------------
+    HopCfg cfg;
+    cfg.prec = o.precision;
+    cfg.B = o.block_width > 0 ? o.block_width : default_block_width(o.precision);
+    if (cfg.B != 32 && cfg.B != 64 && cfg.B != 128) SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", cfg.B);
+    cfg.vpl = o.rows_split > 0 ? o.rows_split : default_vpl(o.precision, cfg.B);
+    cfg.elem = elem_size(o.precision);
+    const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 128;
+    ensure_heavy_rows(g, heavy_t);
+    const size_t slice_bytes = static_cast<size_t>(n) * cfg.B * cfg.elem;
+    const int64_t nblocks_total = (static_cast<int64_t>(n) + cfg.B - 1) / cfg.B;
+    int slices = o.max_slices;
+    if (slices <= 0) {
+        // both blocks of the ping-pong pair within ~60% of L2
+        const double budget = 0.6 * static_cast<double>(g->l2_bytes ? g->l2_bytes : (64u << 20));
+        slices = static_cast<int>(std::max(1.0, std::floor(budget / (2.0 * static_cast<double>(slice_bytes)))));
+    }
+    slices = static_cast<int>(std::min<int64_t>(std::min<int64_t>(slices, nblocks_total), 65535));
+    const int S = slices * cfg.B;
+
+    // source order: longest runs first so a launch holds similar lengths
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    if (o.ell_policy == SC_ELL_PER_EDGE)
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return h_tau_src[a] > h_tau_src[b]; });
+    const int64_t nsuper = (n + S - 1) / S;
+    std::vector<int32_t> h_src(nsuper * S, -1);
+    std::copy(order.begin(), order.end(), h_src.begin());
+
+    g->src_list.reserve(h_src.size());
+    SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    g->xa.reserve(slices * slice_bytes);
+    g->xb.reserve(slices * slice_bytes);
+    g->acc_g.reserve(nnz);
+    g->acc_t1.reserve(nnz);
+    g->acc_t2.reserve(nnz);
+    k_init_acc<<<ceil_div(nnz, 256), 256, 0, s>>>(g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), nnz);
+    SC_LAUNCH_CHECK();
+    int64_t launches = 1 + (o.ell_policy == SC_ELL_FIXED ? 1 : (o.ell_policy == SC_ELL_GLOBAL ? 2 : 1));
+
+    // events for the timed propagation launches (grow-only pool of pairs)
+    int64_t total_hops = 0;
+    if (time_kernels) {
+        for (int64_t sb = 0; sb < nsuper; ++sb) {
+            int32_t L = 0;
+            const int64_t first = sb * S;
+            const int nsrc = static_cast<int>(std::min<int64_t>(S, n - first));
+            for (int q = 0; q < nsrc; ++q) L = std::max(L, h_tau_src[order[first + q]]);
+            L += extra;
+            total_hops += std::max(L - 1, 0);
+        }
+        while (static_cast<int64_t>(g->hop_events.size()) < 2 * total_hops) {
+            cudaEvent_t e;
+            SC_CUDA(cudaEventCreate(&e));
+            g->hop_events.push_back(e);
+        }
+    }
+    int64_t hop_launches = 0;
+
+    // ---- propagation ----------------------------------------------------------
+    SC_CUDA(cudaEventRecord(ev1, s));
+    int64_t hops = 0;
+    double alg_bytes = 0.0;
+    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (cfg.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
+                                       2.0 * static_cast<double>(slice_bytes);
+    int32_t ell_min_src = INT32_MAX, ell_max_src = 0;
+    for (int64_t sb = 0; sb < nsuper; ++sb) {
+        const int64_t first = sb * S;
+        const int nsrc = static_cast<int>(std::min<int64_t>(S, n - first));
+        const int used_slices = (nsrc + cfg.B - 1) / cfg.B;
+        int32_t L = 0;
+        for (int q = 0; q < nsrc; ++q) L = std::max(L, h_tau_src[order[first + q]]);
+        for (int q = 0; q < nsrc; ++q) {
+            ell_min_src = std::min(ell_min_src, h_tau_src[order[first + q]] + extra);
+            ell_max_src = std::max(ell_max_src, h_tau_src[order[first + q]] + extra);
+        }
+        L += extra;
+        if (L == 0) continue;
+        const int32_t *src = g->src_list.get() + first;
+        void *xa = g->xa.get(), *xb = g->xb.get();
+        SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * slice_bytes, s));
+        launch_first_or_gather(g, cfg, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, s);
+        launches += 1;  // the memset is not a kernel of ours
+        for (int ell = 2; ell <= L; ++ell) {
+            if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches], s));
+            launch_hop(g, cfg, xa, xb, used_slices, heavy_t, s);
+            if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches + 1], s));
+            ++hop_launches;
+            launch_first_or_gather(g, cfg, false, xa, src, nsrc, g->tau_entry.get(), ell - 1, g->acc_g.get(),
+                                   g->acc_t1.get(), g->acc_t2.get(), s);
+            std::swap(xa, xb);
+            launches += 2;
+            alg_bytes += used_slices * hop_bytes_per_slice;
+        }
+        launch_first_or_gather(g, cfg, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(), g->acc_t1.get(),
+                               g->acc_t2.get(), s);
+        launches += 1;
+        hops += L;
+    }
+    SC_CUDA(cudaEventRecord(ev2, s));
+
+    // ---- combine ----------------------------------------------------------------
+    DevBuf<double> tmp_s, tmp_b;
+    double *d_s = s_hat;
+    double *d_b = tail_bound;
+    if (!out_dev) {
+        tmp_s.reserve(nnz);
+        d_s = tmp_s.get();
+        if (tail_bound) {
+            tmp_b.reserve(nnz);
+            d_b = tmp_b.get();
+        }
+    }
+    if (!record_tail) d_b = nullptr;
+    const double lam_plus = g->lam.lambda_plus;
+    const double lam_star = g->lam.lambda_star;
+    // q / (2 (1 - lambda_plus)) for the end-corrected estimator, q / (1 - lambda_star^2) otherwise;
+    // lambda_plus carries its Ritz residual as a safety margin
+    double bound_scale = 0.0;
+    if (record_tail) {
+        const double lp = lam_plus + std::max(g->lam.residual_plus, 0.0);
+        if (o.estimator == SC_EST_END_CORRECTED) bound_scale = lp < 1.0 ? 1.0 / (2.0 * (1.0 - lp)) : INFINITY;
+        else bound_scale = lam_star < 1.0 ? 1.0 / (1.0 - lam_star * lam_star) : INFINITY;
+    }
+    k_combine<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(),
+                                             g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), n,
+                                             o.estimator == SC_EST_END_CORRECTED, record_tail ? 1 : 0, bound_scale,
+                                             d_s, d_b);
+    SC_LAUNCH_CHECK();
+    g->scratch_d.reserve(kRedBlocks + 8);
+    const double foster2 = device_reduce(d_s, nnz, false, g->scratch_d.get(), s);
+    double max_bound = 0.0;
+    if (d_b) max_bound = device_reduce(d_b, nnz, true, g->scratch_d.get(), s);
+    launches += 1 + 2 + (d_b ? 2 : 0);
+    if (!out_dev) {
+        SC_CUDA(cudaMemcpyAsync(s_hat, d_s, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (tail_bound && d_b)
+            SC_CUDA(cudaMemcpyAsync(tail_bound, d_b, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    SC_CUDA(cudaStreamSynchronize(s));
+    float prop_ms = 0.f, total_ms = 0.f;
+    SC_CUDA(cudaEventElapsedTime(&prop_ms, ev1, ev2));
+    SC_CUDA(cudaEventRecord(ev2, s));
+    SC_CUDA(cudaEventSynchronize(ev2));
+    SC_CUDA(cudaEventElapsedTime(&total_ms, ev0, ev2));
+    double hop_ms = 0.0;
+    if (time_kernels) {
+        for (int64_t i = 0; i < hop_launches; ++i) {
+            float ms = 0.f;
+            SC_CUDA(cudaEventElapsedTime(&ms, g->hop_events[2 * i], g->hop_events[2 * i + 1]));
+            hop_ms += ms;
+        }
+    }
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->ell_global = ell_global;
+        rep->ell_min_source = ell_min_src == INT32_MAX ? 0 : ell_min_src;
+        rep->ell_max_source = ell_max_src;
+        rep->block_width = cfg.B;
+        rep->rows_split = cfg.vpl;
+        rep->slices = slices;
+        rep->blocks = nblocks_total;
+        rep->launches = launches;
+        rep->hops = hops;
+        rep->algorithmic_bytes = alg_bytes;
+        rep->foster_sum = 0.5 * foster2;
+        rep->max_tail_bound = max_bound;
+        rep->lambda_star = need_lambda ? lam_star : 0.0;
+        rep->propagate_ms = prop_ms;
+        rep->total_ms = total_ms;
+        rep->hop_ms = hop_ms;
+        rep->hop_launches = hop_launches;
+        rep->hop_bytes = alg_bytes;
+    }
+}
+
+}  // namespace sc
+
+extern "C" sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
+                                  sc_report *report) {
+    return sc::guarded([&] { sc::all_edges_impl(g, opts, s_hat, tail_bound, report); });
+}

@@ -1,0 +1,246 @@
+// Kernels of the truncated graph traversal (Algorithm 2), shared by the
+// single-graph driver (propagate.cu) and the batched driver.
+//
+// Layout: a block of B sources is an n x B row-major matrix X (node x's B
+// probabilities p_l(x, s_b) contiguous, rows 16-byte aligned); S = slices x B
+// sources are propagated by one launch, slice q at X + q * n * B.
+//
+// Hop l: X_l[x, :] = (1/d_x) * sum_{j in N(x)} X_{l-1}[j, :]   (Alg. 2 lines 6-9,
+// pull form of the scatter p_l(v_x, v_i) += p_{l-1}(v_j, v_i) / d(v_x)).
+//
+// Summation order (fixed, independent of B, of the lane split and of the
+// light/heavy row path): the neighbours of a row are cut into chunks of 32
+// consecutive CSR entries; each chunk is summed sequentially in CSR order and
+// the chunk sums are added in chunk order. The result is then scaled once by
+// 1/d_x.
+#pragma once
+
+#include "common.cuh"
+
+namespace sc {
+
+constexpr int kChunk = 32;       // neighbours per sequential chunk
+constexpr int kSpmmWarps = 8;    // warps per CTA of the propagation kernel
+
+template <typename T, int B, int VPL>
+struct Layout {
+    using Acc = typename AccOf<T>::type;
+    static constexpr int E = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte vector
+    static constexpr int V = B / E;                              // vectors per row
+    static constexpr int LG = V / VPL;                           // lanes per row group
+    static constexpr int G = 32 / LG;                            // row groups per warp
+    static constexpr int NACC = VPL * E;                         // accumulators per lane
+    static constexpr int U = (VPL >= 4) ? 2 : (VPL == 2 ? 4 : 8); // neighbours in flight per lane
+    static_assert(V % VPL == 0, "bad split");
+    static_assert(LG >= 1 && LG <= 32 && (32 % LG) == 0, "lanes per row must divide 32");
+    static_assert(kChunk % U == 0, "unroll must divide the chunk");
+};
+
+// ---- 16-byte vector <-> accumulators ---------------------------------------
+__device__ __forceinline__ void vadd(float *acc, const uint4 &v, float) {
+    acc[0] += __uint_as_float(v.x);
+    acc[1] += __uint_as_float(v.y);
+    acc[2] += __uint_as_float(v.z);
+    acc[3] += __uint_as_float(v.w);
+}
+__device__ __forceinline__ void vadd(double *acc, const uint4 &v, double) {
+    acc[0] += __hiloint2double(static_cast<int>(v.y), static_cast<int>(v.x));
+    acc[1] += __hiloint2double(static_cast<int>(v.w), static_cast<int>(v.z));
+}
+__device__ __forceinline__ void vadd(float *acc, const uint4 &v, __nv_bfloat16) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        acc[2 * q] += __uint_as_float(w[q] << 16);
+        acc[2 * q + 1] += __uint_as_float(w[q] & 0xffff0000u);
+    }
+}
+
+__device__ __forceinline__ uint4 vpack(const float *a, float) {
+    return make_uint4(__float_as_uint(a[0]), __float_as_uint(a[1]), __float_as_uint(a[2]), __float_as_uint(a[3]));
+}
+__device__ __forceinline__ uint4 vpack(const double *a, double) {
+    return make_uint4(static_cast<uint32_t>(__double2loint(a[0])), static_cast<uint32_t>(__double2hiint(a[0])),
+                      static_cast<uint32_t>(__double2loint(a[1])), static_cast<uint32_t>(__double2hiint(a[1])));
+}
+__device__ __forceinline__ uint4 vpack(const float *a, __nv_bfloat16) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a[2 * q], a[2 * q + 1]);
+        w[q] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint4 ld_x(const uint4 *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// One hop for S = gridDim.y slices. CTAs [0, n_heavy) each take one heavy row
+// (degree > heavy_threshold) and split its chunks over all warps; the other
+// CTAs give each row group of LG lanes one light row.
+// ---------------------------------------------------------------------------
+template <typename T, int B, int VPL>
+__global__ void __launch_bounds__(kSpmmWarps * 32)
+    k_spmm_hop(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+               const typename AccOf<T>::type *__restrict__ inv_deg, const T *__restrict__ x_prev,
+               T *__restrict__ x_next, int32_t n, int32_t heavy_threshold, const int32_t *__restrict__ heavy_rows,
+               int32_t n_heavy) {
+    using L = Layout<T, B, VPL>;
+    using Acc = typename L::Acc;
+    const int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
+    const uint4 *xp = reinterpret_cast<const uint4 *>(x_prev + slice_off);
+    uint4 *xn = reinterpret_cast<uint4 *>(x_next + slice_off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / L::LG, gl = lane % L::LG;
+
+    if (static_cast<int32_t>(blockIdx.x) < n_heavy) {
+        // ---------------- heavy row: chunks spread over the CTA ----------------
+        constexpr int NGRP = kSpmmWarps * L::G;  // chunk slots per round
+        __shared__ Acc part[NGRP][B];
+        const int32_t row = heavy_rows[blockIdx.x];
+        const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
+        const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
+        Acc total = Acc(0);  // thread t < B owns column t
+        for (int32_t base = 0; base < nchunks; base += NGRP) {
+            const int slot = warp * L::G + grp;
+            const int32_t c = base + slot;
+            Acc acc[L::NACC];
+#pragma unroll
+            for (int a = 0; a < L::NACC; ++a) acc[a] = Acc(0);
+            if (c < nchunks) {
+                const int32_t kb = rb + c * kChunk;
+                const int32_t ke = min(kb + kChunk, re);
+                int32_t k = kb;
+                for (; k + L::U <= ke; k += L::U) {
+                    int32_t j[L::U];
+#pragma unroll
+                    for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
+                    uint4 v[L::U][VPL];
+#pragma unroll
+                    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+                        for (int p = 0; p < VPL; ++p) v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
+#pragma unroll
+                    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+                        for (int p = 0; p < VPL; ++p) vadd(acc + p * L::E, v[u][p], T());
+                }
+                for (; k < ke; ++k) {
+                    const int32_t j = col[k];
+#pragma unroll
+                    for (int p = 0; p < VPL; ++p)
+                        vadd(acc + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < VPL; ++p)
+#pragma unroll
+                for (int e = 0; e < L::E; ++e) part[slot][(gl + p * L::LG) * L::E + e] = acc[p * L::E + e];
+            __syncthreads();
+            if (threadIdx.x < B) {
+                const int cnt = min(NGRP, nchunks - base);
+                for (int q = 0; q < cnt; ++q) total += part[q][threadIdx.x];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < B) {
+            T *out = x_next + slice_off + static_cast<int64_t>(row) * B;
+            out[threadIdx.x] = from_acc<T>(total * inv_deg[row]);
+        }
+        return;
+    }
+
+    // ---------------- light rows: one row per group of LG lanes ----------------
+    const int64_t row = (static_cast<int64_t>(blockIdx.x - n_heavy) * kSpmmWarps + warp) * L::G + grp;
+    if (row >= n) return;
+    const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
+    if (re - rb > heavy_threshold) return;  // done by a heavy CTA
+    Acc acc[L::NACC], chunk[L::NACC];
+#pragma unroll
+    for (int a = 0; a < L::NACC; ++a) {
+        acc[a] = Acc(0);
+        chunk[a] = Acc(0);
+    }
+    int32_t k = rb;
+    for (; k + L::U <= re; k += L::U) {
+        int32_t j[L::U];
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
+        uint4 v[L::U][VPL];
+#pragma unroll
+        for (int u = 0; u < L::U; ++u)
+#pragma unroll
+            for (int p = 0; p < VPL; ++p) v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
+#pragma unroll
+        for (int u = 0; u < L::U; ++u)
+#pragma unroll
+            for (int p = 0; p < VPL; ++p) vadd(chunk + p * L::E, v[u][p], T());
+        if (((k + L::U - rb) % kChunk) == 0) {  // chunk boundary reached
+#pragma unroll
+            for (int a = 0; a < L::NACC; ++a) {
+                acc[a] += chunk[a];
+                chunk[a] = Acc(0);
+            }
+        }
+    }
+    for (; k < re; ++k) {
+        const int32_t j = col[k];
+#pragma unroll
+        for (int p = 0; p < VPL; ++p)
+            vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
+    }
+#pragma unroll
+    for (int a = 0; a < L::NACC; ++a) acc[a] += chunk[a];
+    const Acc s = inv_deg[row];
+#pragma unroll
+    for (int a = 0; a < L::NACC; ++a) acc[a] *= s;
+#pragma unroll
+    for (int p = 0; p < VPL; ++p) xn[row * L::V + gl + p * L::LG] = vpack(acc + p * L::E, T());
+}
+
+// X_1 = P e_s for each source s of the launch (Alg. 2 line 2 followed by the
+// first hop): X_1[j, b] = 1/d_j for j in N(s_b). X_1 must be zero on entry.
+template <typename T, int B>
+__global__ void k_first_hop(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                            const typename AccOf<T>::type *__restrict__ inv_deg, const int32_t *__restrict__ src,
+                            int32_t nsrc, T *__restrict__ x1, int32_t n) {
+    const int32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    if (s < 0) return;
+    T *xs = x1 + static_cast<int64_t>(q / B) * n * B + (q % B);
+    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
+        const int32_t j = col[k];
+        xs[static_cast<int64_t>(j) * B] = from_acc<T>(inv_deg[j]);
+    }
+}
+
+// Alg. 2 lines 10-11 for hop `ell`: for source i = s_b and each entry k = (i -> j)
+// the unscaled half term p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while
+// ell <= tau[k]; the terms of hops tau[k]+1 and tau[k]+2 are stored in t1, t2.
+// (The 1/d(v_i) factor of Eq. 9 is applied once in the combine.)
+template <typename T, int B>
+__global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                         const T *__restrict__ x, int32_t n, const int32_t *__restrict__ src, int32_t nsrc,
+                         const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
+                         double *__restrict__ t1, double *__restrict__ t2) {
+    const int32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    if (s < 0) return;
+    const T *xs = x + static_cast<int64_t>(q / B) * n * B + (q % B);
+    const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s) * B]));
+    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
+        const int32_t j = col[k];
+        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j) * B]));
+        const int32_t tk = tau[k];
+        if (ell <= tk) g[k] += term;
+        else if (ell == tk + 1) t1[k] = term;
+        else if (ell == tk + 2) t2[k] = term;
+    }
+}
+
+}  // namespace sc

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+function include/sc.h declares, and the ctypes structures have the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2305_16086_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sc.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = binding.load()
+    declared = _declared_functions()
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(lib, name), f"libsc.so does not export {name}"
+    assert sorted(binding.EXPORTS) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (sc_\w+)", out))
+    assert set(declared) <= exported
+
+
+def test_abi_version_and_status_strings():
+    lib = binding.load()
+    assert lib.sc_abi_version() == 1
+    for code in range(15):
+        assert lib.sc_status_string(code)
+    assert lib.sc_status_string(3) == b"adjacency is not symmetric"
+
+
+def test_options_default():
+    o = binding.Options()
+    binding.load().sc_options_default(ctypes.byref(o))
+    assert o.eps == 1e-3 and o.mode == 0 and o.precision == 1 and o.ell_policy == 0 and o.gamma == 10
+
+
+LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "sc.h"
+#define F(T, f) printf("%s.%s %zu\n", #T, #f, offsetof(T, f));
+int main(void) {
+  printf("sc_graph_info %zu\nsc_lambda %zu\nsc_lambda_opts %zu\nsc_options %zu\nsc_report %zu\n",
+         sizeof(sc_graph_info), sizeof(sc_lambda), sizeof(sc_lambda_opts), sizeof(sc_options), sizeof(sc_report));
+  F(sc_options, seed) F(sc_options, delta) F(sc_options, gamma) F(sc_options, flags)
+  F(sc_report, algorithmic_bytes) F(sc_report, walks) F(sc_report, edges_extended) F(sc_report, total_ms)
+  F(sc_report, hop_ms) F(sc_report, hop_launches) F(sc_report, hop_bytes)
+  F(sc_lambda, iterations) F(sc_graph_info, diameter_lb) F(sc_lambda_opts, seed)
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = dict(line.split() for line in lines if line.strip())
+    py = {"sc_graph_info": binding.GraphInfo, "sc_lambda": binding.Lambda, "sc_lambda_opts": binding.LambdaOpts,
+          "sc_options": binding.Options, "sc_report": binding.Report}
+    for name, cls in py.items():
+        assert int(c[name]) == ctypes.sizeof(cls), name
+    for key, val in c.items():
+        if "." in key:
+            sname, field = key.split(".")
+            assert getattr(py[sname], field).offset == int(val), key
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="libsc.so not found"):
+        binding.load(str(tmp_path / "libsc.so"))
