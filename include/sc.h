@@ -247,6 +247,46 @@ typedef struct sc_report {
 sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                        sc_report *report);
 
+/* ---- allocation-free variant ---------------------------------------------- */
+
+/* size of the file-scope device array that sc_all_edges_noalloc works in */
+#define SC_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * sc_all_edges_noalloc -- the all-edges traversal without any device
+ * allocation. The paper has no counterpart: this is an entry point for
+ * callers that cannot call cudaMalloc -- code running under a memory manager
+ * that owns the whole device budget (a serving arena, a framework's caching
+ * allocator), latency-critical paths where cudaMalloc / cudaFree would block
+ * or synchronise the device, and embedders that must not hit out-of-memory
+ * mid-run.
+ *
+ * Computes what sc_all_edges computes with SC_ELL_FIXED (length `ell` for
+ * every edge), SC_PREC_FP64, block width 32 and the plain estimator, with
+ * every work buffer carved from one static device array of
+ * SC_NOALLOC_SCRATCH_BYTES (64 MiB) that each GPU loading the library holds
+ * until the process exits.
+ *
+ *   n, nnz           : graph size; the call needs about 524 n + 16 nnz bytes of
+ *                      scratch and fails with SC_ERR_INVALID_ARG above the limit
+ *                      (no partial work is done)
+ *   row_ptr, col_idx : device pointers to the symmetric CSR (validated as by
+ *                      sc_graph_create, except connectivity)
+ *   ell              : truncation length >= 0
+ *   s_hat            : device double[nnz] output
+ *   stream           : cudaStream_t (NULL = default); the call returns after its work
+ *
+ * Calls no cudaMalloc, cudaFree or other allocating routine. All calls share
+ * the one array and it keeps the previous call's contents; each call clears
+ * what must start at zero itself. Calls that overlap on the GPU (two streams
+ * or two host threads at once) race on the array: serialise them. The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current) and caches it; make that first call before any
+ * stream capture.
+ */
+sc_status sc_all_edges_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                               int32_t ell, double *s_hat, void *stream);
+
 /* ---- status --------------------------------------------------------------- */
 const char *sc_status_string(sc_status s);
 const char *sc_last_error_detail(void);

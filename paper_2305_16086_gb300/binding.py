@@ -34,7 +34,7 @@ SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
 EXPORTS = [
     "sc_graph_create", "sc_graph_get_info", "sc_graph_destroy", "sc_estimate_lambda",
     "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
-    "sc_last_error_detail", "sc_abi_version",
+    "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc",
 ]
 
 
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     L.sc_last_error_detail.restype = ctypes.c_char_p
     L.sc_abi_version.argtypes = []
     L.sc_abi_version.restype = ctypes.c_int32
+    L.sc_all_edges_noalloc.argtypes = [i32, i64, vp, vp, i32, vp, vp]
+    L.sc_all_edges_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -270,3 +272,16 @@ class Graph:
                                    ctypes.c_void_p(b.ctypes.data) if b is not None else None,
                                    ctypes.byref(rep)), "sc_all_edges")
         return s, b, rep.as_dict()
+
+
+def all_edges_noalloc(row_ptr, col_idx, ell: int, out, stream=None):
+    """sc_all_edges_noalloc on torch CUDA tensors (int32 CSR, float64 output of
+    nnz entries): the traversal for callers that cannot allocate device memory.
+    Works in the library's fixed 64 MiB device array; see include/sc.h."""
+    n = int(row_ptr.shape[0]) - 1
+    nnz = int(col_idx.shape[0])
+    _check(load().sc_all_edges_noalloc(n, nnz, ctypes.c_void_p(row_ptr.data_ptr()),
+                                       ctypes.c_void_p(col_idx.data_ptr()), int(ell),
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "sc_all_edges_noalloc")
+    return out
