@@ -7,6 +7,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -137,10 +138,17 @@ struct sc_graph {
     sc::DevBuf<double> inv_deg_d;
     std::vector<int32_t> h_row_ptr;  // host copy of the row pointers (degrees, scheduling)
 
-    // heavy rows (degree > threshold), sorted by degree, for the CTA-split path
+    // row schedule of the SIMT propagation kernel: heavy rows (degree above
+    // the threshold, one CTA each, longest first) then light rows in order
+    sc::DevBuf<int32_t> row_order;
     int32_t heavy_threshold_cached = -1;
-    sc::DevBuf<int32_t> heavy_rows;
     int32_t n_heavy = 0;
+    // row runs of about equal CSR entries, one per warp, for the TMA kernel
+    sc::DevBuf<int32_t> part;
+    int32_t nparts = 0;
+    int32_t part_target = -1;
+    // autotuned (block width, lane split) per request key
+    std::map<long long, std::pair<int, int>> tuned;
 
     // cached eigenvalue estimate
     bool has_lambda = false;
@@ -158,6 +166,7 @@ struct sc_graph {
 };
 
 namespace sc {
-void ensure_heavy_rows(sc_graph *g, int32_t threshold);
+void ensure_row_order(sc_graph *g, int32_t heavy_threshold);
+void ensure_partition(sc_graph *g, int32_t target);
 void fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s);
 }

@@ -140,22 +140,50 @@ void fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s) {
     SC_LAUNCH_CHECK();
 }
 
-void ensure_heavy_rows(sc_graph *g, int32_t threshold) {
-    if (g->heavy_threshold_cached == threshold) return;
-    std::vector<int32_t> rows;
+void ensure_row_order(sc_graph *g, int32_t heavy_threshold) {
+    if (g->heavy_threshold_cached == heavy_threshold) return;
+    auto deg = [&](int32_t r) { return g->h_row_ptr[r + 1] - g->h_row_ptr[r]; };
+    std::vector<int32_t> heavy, order;
+    order.reserve(g->n);
     for (int32_t r = 0; r < g->n; ++r)
-        if (g->h_row_ptr[r + 1] - g->h_row_ptr[r] > threshold) rows.push_back(r);
-    // longest rows first: their CTAs are scheduled first
-    std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
-        return (g->h_row_ptr[a + 1] - g->h_row_ptr[a]) > (g->h_row_ptr[b + 1] - g->h_row_ptr[b]);
-    });
-    g->heavy_rows.reserve(std::max<size_t>(rows.size(), 1));
-    if (!rows.empty())
-        SC_CUDA(cudaMemcpyAsync(g->heavy_rows.get(), rows.data(), rows.size() * sizeof(int32_t),
-                                cudaMemcpyHostToDevice, g->stream));
+        if (deg(r) > heavy_threshold) heavy.push_back(r);
+    // heavy rows longest first (their CTAs are scheduled first), then the light
+    // rows in natural order (neighbouring rows share cache lines of X on
+    // locally numbered graphs)
+    std::stable_sort(heavy.begin(), heavy.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    order = heavy;
+    for (int32_t r = 0; r < g->n; ++r)
+        if (deg(r) <= heavy_threshold) order.push_back(r);
+    g->row_order.reserve(g->n);
+    SC_CUDA(cudaMemcpyAsync(g->row_order.get(), order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            g->stream));
     SC_CUDA(cudaStreamSynchronize(g->stream));
-    g->n_heavy = static_cast<int32_t>(rows.size());
-    g->heavy_threshold_cached = threshold;
+    g->n_heavy = static_cast<int32_t>(heavy.size());
+    g->heavy_threshold_cached = heavy_threshold;
+}
+
+void ensure_partition(sc_graph *g, int32_t target) {
+    if (g->part_target == target) return;
+    // consecutive rows per warp until about `target` CSR entries (a row longer
+    // than the target forms a run of its own)
+    std::vector<int32_t> part;
+    part.push_back(0);
+    int64_t acc = 0;
+    for (int32_t r = 0; r < g->n; ++r) {
+        const int32_t d = g->h_row_ptr[r + 1] - g->h_row_ptr[r];
+        if (acc > 0 && acc + d > target) {
+            part.push_back(r);
+            acc = 0;
+        }
+        acc += d;
+    }
+    part.push_back(g->n);
+    g->part.reserve(part.size());
+    SC_CUDA(cudaMemcpyAsync(g->part.get(), part.data(), part.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            g->stream));
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+    g->nparts = static_cast<int32_t>(part.size()) - 1;
+    g->part_target = target;
 }
 
 static void create_impl(sc_graph **out, int32_t n, int64_t nnz, const int32_t *row_ptr,

@@ -187,8 +187,6 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
     k_na_init<<<ceil_div(nnz, tb), tb, 0, s>>>(acc, tau, nnz, ell);
     k_na_sources<<<ceil_div(nsrc, tb), tb, 0, s>>>(src, nsrc, n);
     SC_LAUNCH_CHECK();
-    using Lay = Layout<double, B, 1>;
-    const dim3 hop_grid(ceil_div(n, kSpmmWarps * Lay::G), 1);
     for (int64_t first = 0; first < n && ell > 0; first += B) {
         const int nb = static_cast<int>(std::min<int64_t>(B, n - first));
         const int32_t *bsrc = src + first;
@@ -196,12 +194,26 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
         SC_CUDA(cudaMemsetAsync(a, 0, 8 * static_cast<size_t>(B) * n, s));
         k_first_hop<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, inv_deg, bsrc, nb, a, n);
         for (int hop = 2; hop <= ell; ++hop) {
-            // every row takes the light path (no heavy-row list without allocation)
-            k_spmm_hop<double, B, 1><<<hop_grid, kSpmmWarps * 32, 0, s>>>(row_ptr, col_idx, inv_deg, a, b, n,
-                                                                          INT32_MAX, nullptr, 0);
-            // hop - 1 <= ell = tau[k] always, so the hop tau+1 / tau+2 records are never written
-            k_gather<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, hop - 1, acc,
-                                                                nullptr, nullptr);
+            // natural row order, every row on the light path (no schedule array
+            // without allocation); the tail CTAs gather X_{hop-1}. hop - 1 <= ell
+            // = tau[k] always, so the hop tau+1 / tau+2 records are never written.
+            HopArgs<double> ha{};
+            ha.row_ptr = row_ptr;
+            ha.col = col_idx;
+            ha.inv_deg = inv_deg;
+            ha.x_prev = a;
+            ha.x_next = b;
+            ha.n = n;
+            ha.row_order = nullptr;
+            ha.n_heavy = 0;
+            ha.src = bsrc;
+            ha.nsrc = nb;
+            ha.tau = tau;
+            ha.gather_ell = hop - 1;
+            ha.g = acc;
+            ha.t1 = nullptr;
+            ha.t2 = nullptr;
+            launch_spmm_hop<double, B, 1>(ha, 1, s);
             std::swap(a, b);
         }
         k_gather<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,

@@ -6,6 +6,9 @@
 #include <cstring>
 #include <numeric>
 
+#include <cudaTypedefs.h>
+
+#include "hop_tma.cuh"
 #include "propagate.cuh"
 
 namespace sc {
@@ -101,11 +104,6 @@ double device_reduce(const double *x, int64_t count, bool max, double *scratch, 
 // ---------------------------------------------------------------------------
 // kernel dispatch over (precision, B, lane split)
 // ---------------------------------------------------------------------------
-struct HopCfg {
-    int prec, B, vpl;
-    size_t elem;
-};
-
 static size_t elem_size(int prec) { return prec == SC_PREC_FP64 ? 8 : (prec == SC_PREC_FP32 ? 4 : 2); }
 
 template <typename T>
@@ -117,57 +115,158 @@ const float *inv_deg_of<float>(const sc_graph *g) { return g->inv_deg_f.get(); }
 template <>
 const float *inv_deg_of<__nv_bfloat16>(const sc_graph *g) { return g->inv_deg_f.get(); }
 
+// type-erased arguments of one hop launch
+struct HopLaunch {
+    const void *xp;
+    void *xn;
+    int slices;
+    const int32_t *src;
+    int nsrc;
+    const int32_t *tau;
+    int gather_ell;  // 0: no fused gather
+    double *g, *t1, *t2;
+    int32_t *status;  // TMA kernel: bounded-wait expiry flag
+};
+
+// ---- TMA-gather variant (lane split value 0) --------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        SC_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) SC_FAIL(SC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map over `rows` rows of B elements (row pitch B * sizeof(T)), box of one
+// full row: the shape tile::gather4 requires
+template <typename T>
+static CUtensorMap row_tensor_map(const void *base, int B, int64_t rows) {
+    CUtensorMap m;
+    const CUtensorMapDataType dt = std::is_same<T, double>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : std::is_same<T, float>::value  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(B), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(B) * sizeof(T)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(B), 1};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = tensor_map_encoder()(&m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) SC_FAIL(SC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return m;
+}
+
+constexpr int kTmaPartEntries = 256;  // CSR entries per warp run
+
+template <typename T, int B>
+static void hop_tma_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
+    using TL = TmaLayout<T, B>;
+    static uint64_t attr_set = 0;  // per instantiation, one bit per device
+    const uint64_t bit = 1ull << (g->device & 63);
+    if (!(attr_set & bit)) {
+        SC_CUDA(cudaFuncSetAttribute(k_hop_tma<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(TL::SMEM)));
+        attr_set |= bit;
+    }
+    const CUtensorMap m = row_tensor_map<T>(h.xp, B, static_cast<int64_t>(h.slices) * g->n);
+    TmaHopArgs a{};
+    a.row_ptr = g->row_ptr.get();
+    a.col = g->col_idx.get();
+    a.inv_deg = inv_deg_of<T>(g);
+    a.x_next = h.xn;
+    a.n = g->n;
+    a.part = g->part.get();
+    a.nparts = g->nparts;
+    a.part_ctas = ceil_div(g->nparts, kTmaWarps);
+    a.x_prev = h.xp;
+    a.src = h.src;
+    a.nsrc = h.nsrc;
+    a.tau = h.tau;
+    a.gather_ell = h.gather_ell;
+    a.g = h.g;
+    a.t1 = h.t1;
+    a.t2 = h.t2;
+    a.status = h.status;
+    const int gather_ctas = h.gather_ell > 0 ? ceil_div(B, kTmaWarps) : 0;
+    dim3 grid(a.part_ctas + gather_ctas, h.slices);
+    k_hop_tma<T, B><<<grid, kTmaWarps * 32, TL::SMEM, s>>>(m, a);
+}
+
 template <typename T, int B, int VPL>
-static void launch_hop_t(const sc_graph *g, const void *xp, void *xn, int slices, int heavy_t, cudaStream_t s) {
-    using L = Layout<T, B, VPL>;
-    const int rows_per_cta = kSpmmWarps * L::G;
-    dim3 grid(g->n_heavy + ceil_div(g->n, rows_per_cta), slices);
-    k_spmm_hop<T, B, VPL><<<grid, kSpmmWarps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g),
-                                                          static_cast<const T *>(xp), static_cast<T *>(xn), g->n,
-                                                          heavy_t, g->heavy_rows.get(), g->n_heavy);
+static void hop_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
+    HopArgs<T> a{};
+    a.row_ptr = g->row_ptr.get();
+    a.col = g->col_idx.get();
+    a.inv_deg = inv_deg_of<T>(g);
+    a.x_prev = static_cast<const T *>(h.xp);
+    a.x_next = static_cast<T *>(h.xn);
+    a.n = g->n;
+    a.row_order = g->row_order.get();
+    a.n_heavy = g->n_heavy;
+    a.src = h.src;
+    a.nsrc = h.nsrc;
+    a.tau = h.tau;
+    a.gather_ell = h.gather_ell;
+    a.g = h.g;
+    a.t1 = h.t1;
+    a.t2 = h.t2;
+    launch_spmm_hop<T, B, VPL>(a, h.slices, s);
+}
+
+// lane split 0 = the TMA-gather kernel; 1, 2, 4 = 16-byte vectors per lane of the SIMT kernel
+template <typename T, int B>
+static constexpr bool vpl_valid(int vpl) {
+    constexpr int V = B / (16 / static_cast<int>(sizeof(T)));
+    if (vpl == 0) return B * static_cast<int>(sizeof(T)) * 4 * 2 <= kTmaWarpRingBytes;
+    return (vpl == 1 || vpl == 2 || vpl == 4) && V % vpl == 0 && V / vpl <= 32;
 }
 
 template <typename T, int B>
-static void launch_hop_b(const sc_graph *g, int vpl, const void *xp, void *xn, int slices, int heavy_t,
-                         cudaStream_t s) {
-    constexpr int V = B / (16 / static_cast<int>(sizeof(T)));
+static void hop_b(const sc_graph *g, int vpl, const HopLaunch &h, cudaStream_t s) {
+    if (vpl == 0) return hop_tma_t<T, B>(g, h, s);
     if (vpl == 1) {
-        if constexpr (V <= 32) {
-            launch_hop_t<T, B, 1>(g, xp, xn, slices, heavy_t, s);
-            return;
-        }
+        if constexpr (vpl_valid<T, B>(1)) return hop_t<T, B, 1>(g, h, s);
     } else if (vpl == 2) {
-        if constexpr (V >= 2 && V / 2 <= 32) {
-            launch_hop_t<T, B, 2>(g, xp, xn, slices, heavy_t, s);
-            return;
-        }
+        if constexpr (vpl_valid<T, B>(2)) return hop_t<T, B, 2>(g, h, s);
     } else if (vpl == 4) {
-        if constexpr (V >= 4 && V / 4 <= 32) {
-            launch_hop_t<T, B, 4>(g, xp, xn, slices, heavy_t, s);
-            return;
-        }
+        if constexpr (vpl_valid<T, B>(4)) return hop_t<T, B, 4>(g, h, s);
     }
     SC_FAIL(SC_ERR_INVALID_ARG, "unsupported lane split %d for B=%d", vpl, B);
 }
 
 template <typename T>
-static void launch_hop_p(const sc_graph *g, int B, int vpl, const void *xp, void *xn, int slices, int heavy_t,
-                         cudaStream_t s) {
+static void hop_p(const sc_graph *g, int B, int vpl, const HopLaunch &h, cudaStream_t s) {
     switch (B) {
-    case 32: launch_hop_b<T, 32>(g, vpl, xp, xn, slices, heavy_t, s); break;
-    case 64: launch_hop_b<T, 64>(g, vpl, xp, xn, slices, heavy_t, s); break;
-    case 128: launch_hop_b<T, 128>(g, vpl, xp, xn, slices, heavy_t, s); break;
+    case 32: hop_b<T, 32>(g, vpl, h, s); break;
+    case 64: hop_b<T, 64>(g, vpl, h, s); break;
+    case 128: hop_b<T, 128>(g, vpl, h, s); break;
     default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d not in {32, 64, 128}", B);
     }
 }
 
-void launch_hop(const sc_graph *g, const HopCfg &c, const void *xp, void *xn, int slices, int heavy_t,
-                cudaStream_t s) {
-    switch (c.prec) {
-    case SC_PREC_FP64: launch_hop_p<double>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
-    case SC_PREC_FP32: launch_hop_p<float>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
-    case SC_PREC_BF16: launch_hop_p<__nv_bfloat16>(g, c.B, c.vpl, xp, xn, slices, heavy_t, s); break;
-    default: SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", c.prec);
+static bool cfg_valid(int prec, int B, int vpl) {
+    switch (prec) {
+    case SC_PREC_FP64:
+        return B == 32 ? vpl_valid<double, 32>(vpl) : B == 64 ? vpl_valid<double, 64>(vpl) : B == 128 && vpl_valid<double, 128>(vpl);
+    case SC_PREC_FP32:
+        return B == 32 ? vpl_valid<float, 32>(vpl) : B == 64 ? vpl_valid<float, 64>(vpl) : B == 128 && vpl_valid<float, 128>(vpl);
+    case SC_PREC_BF16:
+        return B == 32 ? vpl_valid<__nv_bfloat16, 32>(vpl) : B == 64 ? vpl_valid<__nv_bfloat16, 64>(vpl)
+                                                             : B == 128 && vpl_valid<__nv_bfloat16, 128>(vpl);
+    }
+    return false;
+}
+
+void launch_hop(const sc_graph *g, int prec, int B, int vpl, const HopLaunch &h, cudaStream_t s) {
+    switch (prec) {
+    case SC_PREC_FP64: hop_p<double>(g, B, vpl, h, s); break;
+    case SC_PREC_FP32: hop_p<float>(g, B, vpl, h, s); break;
+    case SC_PREC_BF16: hop_p<__nv_bfloat16>(g, B, vpl, h, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", prec);
     }
     SC_LAUNCH_CHECK();
 }
@@ -197,25 +296,84 @@ static void first_gather_p(const sc_graph *g, int B, bool first, const void *x, 
     }
 }
 
-void launch_first_or_gather(const sc_graph *g, const HopCfg &c, bool first, const void *x, const int32_t *src,
+void launch_first_or_gather(const sc_graph *g, int prec, int B, bool first, const void *x, const int32_t *src,
                             int nsrc, const int32_t *tau, int ell, double *a, double *b, double *cc,
                             cudaStream_t s) {
-    switch (c.prec) {
-    case SC_PREC_FP64: first_gather_p<double>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
-    case SC_PREC_FP32: first_gather_p<float>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
-    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, c.B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    switch (prec) {
+    case SC_PREC_FP64: first_gather_p<double>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    case SC_PREC_FP32: first_gather_p<float>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
     }
     SC_LAUNCH_CHECK();
 }
 
-// default lane split: 16 lanes per row for wide rows, whole warp otherwise
-static int default_vpl(int prec, int B) {
-    const int V = B / (16 / static_cast<int>(elem_size(prec)));
-    if (V > 32) return V / 32;           // fp64 B=128: 2
-    return V >= 16 ? (V / 16) : 1;      // 16 lanes per row where possible
+// blocks propagated per launch: both ping-pong blocks within ~60% of L2
+static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
+    const size_t slice_bytes = static_cast<size_t>(g->n) * B * elem;
+    const int64_t nblocks = (static_cast<int64_t>(g->n) + B - 1) / B;
+    int slices = max_slices;
+    if (slices <= 0) {
+        const double budget = 0.6 * static_cast<double>(g->l2_bytes ? g->l2_bytes : (64u << 20));
+        slices = static_cast<int>(std::max(1.0, std::floor(budget / (2.0 * static_cast<double>(slice_bytes)))));
+    }
+    return static_cast<int>(std::min<int64_t>(std::min<int64_t>(slices, nblocks), 65535));
 }
 
-static int default_block_width(int prec) { return prec == SC_PREC_FP64 ? 64 : (prec == SC_PREC_FP32 ? 64 : 128); }
+// Autotuner: time a few hops of every admissible (B, lane split) on this
+// graph (values do not change the kernel's cost, so zero blocks are used) and
+// keep the fastest per source-hop. Cached per graph, precision and request.
+struct TuneResult {
+    int B, vpl;
+};
+
+static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_slices, cudaStream_t s) {
+    const long long key = (static_cast<long long>(prec) << 40) ^ (static_cast<long long>(fixB) << 24) ^
+                          (static_cast<long long>(fixV) << 16) ^ static_cast<long long>(max_slices & 0xffff) ^
+                          (static_cast<long long>(g->n_heavy) << 44);
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) return TuneResult{it->second.first, it->second.second};
+    std::vector<std::pair<int, int>> cands;
+    for (int B : {32, 64, 128})
+        for (int v : {0, 1, 2, 4})
+            if ((fixB == 0 || fixB == B) && (fixV < 0 || fixV == v) && cfg_valid(prec, B, v)) cands.push_back({B, v});
+    if (cands.empty()) SC_FAIL(SC_ERR_INVALID_ARG, "no admissible kernel for B=%d split=%d", fixB, fixV);
+    if (cands.size() == 1) {
+        g->tuned[key] = cands[0];
+        return TuneResult{cands[0].first, cands[0].second};
+    }
+    const size_t elem = elem_size(prec);
+    size_t need = 0;
+    for (auto &c : cands) need = std::max(need, slices_for(g, c.first, elem, max_slices) * static_cast<size_t>(g->n) * c.first * elem);
+    g->xa.reserve(need);
+    g->xb.reserve(need);
+    SC_CUDA(cudaMemsetAsync(g->xa.get(), 0, need, s));
+    cudaEvent_t e0, e1;
+    SC_CUDA(cudaEventCreate(&e0));
+    SC_CUDA(cudaEventCreate(&e1));
+    double best = INFINITY;
+    std::pair<int, int> pick = cands[0];
+    for (auto &c : cands) {
+        const int sl = slices_for(g, c.first, elem, max_slices);
+        HopLaunch h{g->xa.get(), g->xb.get(), sl, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr, g->status.get()};
+        launch_hop(g, prec, c.first, c.second, h, s);  // warm-up
+        SC_CUDA(cudaEventRecord(e0, s));
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r) launch_hop(g, prec, c.first, c.second, h, s);
+        SC_CUDA(cudaEventRecord(e1, s));
+        SC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_source_hop = ms / (reps * static_cast<double>(sl) * c.first);
+        if (per_source_hop < best) {
+            best = per_source_hop;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tuned[key] = pick;
+    return TuneResult{pick.first, pick.second};
+}
 
 // ---------------------------------------------------------------------------
 // the driver
@@ -286,24 +444,24 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     const int extra = record_tail ? 2 : 0;
 
     // ---- block configuration -------------------------------------------------
-    HopCfg cfg;
-    cfg.prec = o.precision;
-    cfg.B = o.block_width > 0 ? o.block_width : default_block_width(o.precision);
-    if (cfg.B != 32 && cfg.B != 64 && cfg.B != 128) SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", cfg.B);
-    cfg.vpl = o.rows_split > 0 ? o.rows_split : default_vpl(o.precision, cfg.B);
-    cfg.elem = elem_size(o.precision);
-    const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 128;
-    ensure_heavy_rows(g, heavy_t);
-    const size_t slice_bytes = static_cast<size_t>(n) * cfg.B * cfg.elem;
-    const int64_t nblocks_total = (static_cast<int64_t>(n) + cfg.B - 1) / cfg.B;
-    int slices = o.max_slices;
-    if (slices <= 0) {
-        // both blocks of the ping-pong pair within ~60% of L2
-        const double budget = 0.6 * static_cast<double>(g->l2_bytes ? g->l2_bytes : (64u << 20));
-        slices = static_cast<int>(std::max(1.0, std::floor(budget / (2.0 * static_cast<double>(slice_bytes)))));
-    }
-    slices = static_cast<int>(std::min<int64_t>(std::min<int64_t>(slices, nblocks_total), 65535));
-    const int S = slices * cfg.B;
+    const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 256;
+    ensure_row_order(g, heavy_t);
+    if (o.block_width != 0 && o.block_width != 32 && o.block_width != 64 && o.block_width != 128)
+        SC_FAIL(SC_ERR_INVALID_ARG, "block width %d not in {32, 64, 128}", o.block_width);
+    if (o.rows_split < -1 || o.rows_split == 3 || o.rows_split > 4)
+        SC_FAIL(SC_ERR_INVALID_ARG, "lane split %d not in {-1 (TMA gather), 1, 2, 4}", o.rows_split);
+    ensure_partition(g, kTmaPartEntries);
+    g->status.reserve(4);
+    SC_CUDA(cudaMemsetAsync(g->status.get(), 0, 4 * sizeof(int32_t), s));
+    // rows_split: 0 = automatic, -1 = the TMA-gather kernel, 1/2/4 = SIMT lane split
+    const int fixV = o.rows_split == 0 ? -1 : (o.rows_split < 0 ? 0 : o.rows_split);
+    const TuneResult tr = autotune(g, o.precision, o.block_width, fixV, o.max_slices, s);
+    const int prec = o.precision, B = tr.B, vpl = tr.vpl;
+    const size_t elem = elem_size(prec);
+    const size_t slice_bytes = static_cast<size_t>(n) * B * elem;
+    const int64_t nblocks_total = (static_cast<int64_t>(n) + B - 1) / B;
+    const int slices = slices_for(g, B, elem, o.max_slices);
+    const int S = slices * B;
 
     // source order: longest runs first so a launch holds similar lengths
     std::vector<int32_t> order(n);
@@ -348,13 +506,13 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaEventRecord(ev1, s));
     int64_t hops = 0;
     double alg_bytes = 0.0;
-    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (cfg.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
+    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
                                        2.0 * static_cast<double>(slice_bytes);
     int32_t ell_min_src = INT32_MAX, ell_max_src = 0;
     for (int64_t sb = 0; sb < nsuper; ++sb) {
         const int64_t first = sb * S;
         const int nsrc = static_cast<int>(std::min<int64_t>(S, n - first));
-        const int used_slices = (nsrc + cfg.B - 1) / cfg.B;
+        const int used_slices = (nsrc + B - 1) / B;
         int32_t L = 0;
         for (int q = 0; q < nsrc; ++q) L = std::max(L, h_tau_src[order[first + q]]);
         for (int q = 0; q < nsrc; ++q) {
@@ -366,25 +524,32 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         const int32_t *src = g->src_list.get() + first;
         void *xa = g->xa.get(), *xb = g->xb.get();
         SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * slice_bytes, s));
-        launch_first_or_gather(g, cfg, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, s);
+        launch_first_or_gather(g, prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, s);
         launches += 1;  // the memset is not a kernel of ours
         for (int ell = 2; ell <= L; ++ell) {
+            // hop ell computes X_ell and, in its tail CTAs, gathers X_{ell-1}
+            HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
+                        g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get()};
             if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches], s));
-            launch_hop(g, cfg, xa, xb, used_slices, heavy_t, s);
+            launch_hop(g, prec, B, vpl, h, s);
             if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches + 1], s));
             ++hop_launches;
-            launch_first_or_gather(g, cfg, false, xa, src, nsrc, g->tau_entry.get(), ell - 1, g->acc_g.get(),
-                                   g->acc_t1.get(), g->acc_t2.get(), s);
             std::swap(xa, xb);
-            launches += 2;
+            launches += 1;
             alg_bytes += used_slices * hop_bytes_per_slice;
         }
-        launch_first_or_gather(g, cfg, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(), g->acc_t1.get(),
-                               g->acc_t2.get(), s);
+        launch_first_or_gather(g, prec, B, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(),
+                               g->acc_t1.get(), g->acc_t2.get(), s);
         launches += 1;
         hops += L;
     }
     SC_CUDA(cudaEventRecord(ev2, s));
+    {
+        int32_t h_status = 0;
+        SC_CUDA(cudaMemcpyAsync(&h_status, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+        if (h_status & 1) SC_FAIL(SC_ERR_TIMEOUT, "a bounded mbarrier wait expired in the TMA hop kernel");
+    }
 
     // ---- combine ----------------------------------------------------------------
     DevBuf<double> tmp_s, tmp_b;
@@ -443,8 +608,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->ell_global = ell_global;
         rep->ell_min_source = ell_min_src == INT32_MAX ? 0 : ell_min_src;
         rep->ell_max_source = ell_max_src;
-        rep->block_width = cfg.B;
-        rep->rows_split = cfg.vpl;
+        rep->block_width = B;
+        rep->rows_split = vpl == 0 ? -1 : vpl;
         rep->slices = slices;
         rep->blocks = nblocks_total;
         rep->launches = launches;

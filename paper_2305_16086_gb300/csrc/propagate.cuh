@@ -1,5 +1,6 @@
 // Kernels of the truncated graph traversal (Algorithm 2), shared by the
-// single-graph driver (propagate.cu) and the batched driver.
+// single-graph driver (propagate.cu), the allocation-free driver and the
+// batched driver.
 //
 // Layout: a block of B sources is an n x B row-major matrix X (node x's B
 // probabilities p_l(x, s_b) contiguous, rows 16-byte aligned); S = slices x B
@@ -8,11 +9,11 @@
 // Hop l: X_l[x, :] = (1/d_x) * sum_{j in N(x)} X_{l-1}[j, :]   (Alg. 2 lines 6-9,
 // pull form of the scatter p_l(v_x, v_i) += p_{l-1}(v_j, v_i) / d(v_x)).
 //
-// Summation order (fixed, independent of B, of the lane split and of the
-// light/heavy row path): the neighbours of a row are cut into chunks of 32
-// consecutive CSR entries; each chunk is summed sequentially in CSR order and
-// the chunk sums are added in chunk order. The result is then scaled once by
-// 1/d_x.
+// Summation order (fixed, independent of B, of the lane split, of the row
+// schedule, of the light/heavy row path and of the TMA variant in hop_tma.cuh): the neighbours of a row are cut
+// into chunks of 32 consecutive CSR entries; each chunk is summed
+// sequentially in CSR order and the chunk sums are added in chunk order. The
+// result is then scaled once by 1/d_x.
 #pragma once
 
 #include "common.cuh"
@@ -30,7 +31,7 @@ struct Layout {
     static constexpr int LG = V / VPL;                           // lanes per row group
     static constexpr int G = 32 / LG;                            // row groups per warp
     static constexpr int NACC = VPL * E;                         // accumulators per lane
-    static constexpr int U = (VPL >= 4) ? 2 : (VPL == 2 ? 4 : 8); // neighbours in flight per lane
+    static constexpr int U = (VPL >= 4) ? 2 : (VPL == 2 ? 4 : 8);  // row loads in flight per lane
     static_assert(V % VPL == 0, "bad split");
     static_assert(LG >= 1 && LG <= 32 && (32 % LG) == 0, "lanes per row must divide 32");
     static_assert(kChunk % U == 0, "unroll must divide the chunk");
@@ -75,30 +76,78 @@ __device__ __forceinline__ uint4 vpack(const float *a, __nv_bfloat16) {
 
 __device__ __forceinline__ uint4 ld_x(const uint4 *p) { return __ldg(p); }
 
+// Arguments of one hop launch.
+template <typename T>
+struct HopArgs {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const typename AccOf<T>::type *inv_deg;
+    const T *x_prev;   // X_{l-1}, slices x n x B
+    T *x_next;         // X_l
+    int32_t n;
+    // row schedule: row_order[0 .. n_heavy) are the rows of degree above the
+    // heavy threshold (one CTA each, longest first), the rest are the light
+    // rows in natural order for the row groups; row_order == nullptr means
+    // natural order with no heavy rows
+    const int32_t *row_order;
+    int32_t n_heavy;
+    int32_t light_ctas;
+    // fused gather of X_{l-1} for the launch's sources (gather_ell > 0):
+    // see gather_source
+    const int32_t *src;
+    int32_t nsrc;
+    const int32_t *tau;
+    int32_t gather_ell;
+    double *g, *t1, *t2;
+};
+
+// Alg. 2 lines 10-11 for hop `ell` and launch source q (slice q / B, column
+// q % B): for source i = s_b and each entry k = (i -> j) the unscaled half term
+// p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while ell <= tau[k]; the terms
+// of hops tau[k]+1 and tau[k]+2 are stored in t1, t2. (The 1/d(v_i) factor of
+// Eq. 9 is applied once in the combine.) One warp per source.
+template <typename T, int B>
+__device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                              const T *__restrict__ x, int32_t n, int32_t s, int32_t q,
+                                              const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
+                                              double *__restrict__ t1, double *__restrict__ t2, int lane) {
+    const T *xs = x + static_cast<int64_t>(q / B) * n * B + (q % B);
+    const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s) * B]));
+    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
+        const int32_t j = col[k];
+        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j) * B]));
+        const int32_t tk = tau[k];
+        if (ell <= tk) g[k] += term;
+        else if (ell == tk + 1) t1[k] = term;
+        else if (ell == tk + 2) t2[k] = term;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One hop for S = gridDim.y slices. CTAs [0, n_heavy) each take one heavy row
-// (degree > heavy_threshold) and split its chunks over all warps; the other
-// CTAs give each row group of LG lanes one light row.
+// and split its chunks over all warps; the next light_ctas CTAs give each row
+// group of LG lanes one light row; the remaining CTAs (if any) gather X_{l-1}
+// for the launch's sources.
 // ---------------------------------------------------------------------------
 template <typename T, int B, int VPL>
-__global__ void __launch_bounds__(kSpmmWarps * 32)
-    k_spmm_hop(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-               const typename AccOf<T>::type *__restrict__ inv_deg, const T *__restrict__ x_prev,
-               T *__restrict__ x_next, int32_t n, int32_t heavy_threshold, const int32_t *__restrict__ heavy_rows,
-               int32_t n_heavy) {
+__global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a) {
     using L = Layout<T, B, VPL>;
     using Acc = typename L::Acc;
+    const int32_t n = a.n;
     const int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
-    const uint4 *xp = reinterpret_cast<const uint4 *>(x_prev + slice_off);
-    uint4 *xn = reinterpret_cast<uint4 *>(x_next + slice_off);
+    const uint4 *xp = reinterpret_cast<const uint4 *>(a.x_prev + slice_off);
+    uint4 *xn = reinterpret_cast<uint4 *>(a.x_next + slice_off);
+    const int32_t *__restrict__ row_ptr = a.row_ptr;
+    const int32_t *__restrict__ col = a.col;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / L::LG, gl = lane % L::LG;
+    const int32_t cta = static_cast<int32_t>(blockIdx.x);
 
-    if (static_cast<int32_t>(blockIdx.x) < n_heavy) {
+    if (cta < a.n_heavy) {
         // ---------------- heavy row: chunks spread over the CTA ----------------
         constexpr int NGRP = kSpmmWarps * L::G;  // chunk slots per round
         __shared__ Acc part[NGRP][B];
-        const int32_t row = heavy_rows[blockIdx.x];
+        const int32_t row = a.row_order[cta];
         const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
         const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
         Acc total = Acc(0);  // thread t < B owns column t
@@ -107,7 +156,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32)
             const int32_t c = base + slot;
             Acc acc[L::NACC];
 #pragma unroll
-            for (int a = 0; a < L::NACC; ++a) acc[a] = Acc(0);
+            for (int q = 0; q < L::NACC; ++q) acc[q] = Acc(0);
             if (c < nchunks) {
                 const int32_t kb = rb + c * kChunk;
                 const int32_t ke = min(kb + kChunk, re);
@@ -145,22 +194,33 @@ __global__ void __launch_bounds__(kSpmmWarps * 32)
             __syncthreads();
         }
         if (threadIdx.x < B) {
-            T *out = x_next + slice_off + static_cast<int64_t>(row) * B;
-            out[threadIdx.x] = from_acc<T>(total * inv_deg[row]);
+            T *out = a.x_next + slice_off + static_cast<int64_t>(row) * B;
+            out[threadIdx.x] = from_acc<T>(total * a.inv_deg[row]);
+        }
+        return;
+    }
+
+    if (cta >= a.n_heavy + a.light_ctas) {
+        // ---------------- fused gather of X_{l-1} ----------------
+        const int32_t q = static_cast<int32_t>(blockIdx.y) * B + (cta - a.n_heavy - a.light_ctas) * kSpmmWarps + warp;
+        if (q < a.nsrc) {
+            const int32_t s = a.src[q];
+            if (s >= 0)
+                gather_source<T, B>(row_ptr, col, a.x_prev, n, s, q, a.tau, a.gather_ell, a.g, a.t1, a.t2, lane);
         }
         return;
     }
 
     // ---------------- light rows: one row per group of LG lanes ----------------
-    const int64_t row = (static_cast<int64_t>(blockIdx.x - n_heavy) * kSpmmWarps + warp) * L::G + grp;
-    if (row >= n) return;
+    const int64_t idx = (static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp) * L::G + grp;
+    if (idx >= n - a.n_heavy) return;
+    const int32_t row = a.row_order ? a.row_order[a.n_heavy + idx] : static_cast<int32_t>(idx);
     const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
-    if (re - rb > heavy_threshold) return;  // done by a heavy CTA
     Acc acc[L::NACC], chunk[L::NACC];
 #pragma unroll
-    for (int a = 0; a < L::NACC; ++a) {
-        acc[a] = Acc(0);
-        chunk[a] = Acc(0);
+    for (int q = 0; q < L::NACC; ++q) {
+        acc[q] = Acc(0);
+        chunk[q] = Acc(0);
     }
     int32_t k = rb;
     for (; k + L::U <= re; k += L::U) {
@@ -176,11 +236,11 @@ __global__ void __launch_bounds__(kSpmmWarps * 32)
         for (int u = 0; u < L::U; ++u)
 #pragma unroll
             for (int p = 0; p < VPL; ++p) vadd(chunk + p * L::E, v[u][p], T());
-        if (((k + L::U - rb) % kChunk) == 0) {  // chunk boundary reached
+        if (((k + L::U - rb) % kChunk) == 0) {  // a chunk of 32 positions is complete
 #pragma unroll
-            for (int a = 0; a < L::NACC; ++a) {
-                acc[a] += chunk[a];
-                chunk[a] = Acc(0);
+            for (int q = 0; q < L::NACC; ++q) {
+                acc[q] += chunk[q];
+                chunk[q] = Acc(0);
             }
         }
     }
@@ -191,12 +251,12 @@ __global__ void __launch_bounds__(kSpmmWarps * 32)
             vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
     }
 #pragma unroll
-    for (int a = 0; a < L::NACC; ++a) acc[a] += chunk[a];
-    const Acc s = inv_deg[row];
+    for (int q = 0; q < L::NACC; ++q) acc[q] += chunk[q];
+    const Acc sc = a.inv_deg[row];
 #pragma unroll
-    for (int a = 0; a < L::NACC; ++a) acc[a] *= s;
+    for (int q = 0; q < L::NACC; ++q) acc[q] *= sc;
 #pragma unroll
-    for (int p = 0; p < VPL; ++p) xn[row * L::V + gl + p * L::LG] = vpack(acc + p * L::E, T());
+    for (int p = 0; p < VPL; ++p) xn[static_cast<int64_t>(row) * L::V + gl + p * L::LG] = vpack(acc + p * L::E, T());
 }
 
 // X_1 = P e_s for each source s of the launch (Alg. 2 line 2 followed by the
@@ -217,10 +277,7 @@ __global__ void k_first_hop(const int32_t *__restrict__ row_ptr, const int32_t *
     }
 }
 
-// Alg. 2 lines 10-11 for hop `ell`: for source i = s_b and each entry k = (i -> j)
-// the unscaled half term p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while
-// ell <= tau[k]; the terms of hops tau[k]+1 and tau[k]+2 are stored in t1, t2.
-// (The 1/d(v_i) factor of Eq. 9 is applied once in the combine.)
+// stand-alone gather (the last hop of a block, and callers without fusion)
 template <typename T, int B>
 __global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                          const T *__restrict__ x, int32_t n, const int32_t *__restrict__ src, int32_t nsrc,
@@ -231,16 +288,17 @@ __global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__r
     if (q >= nsrc) return;
     const int32_t s = src[q];
     if (s < 0) return;
-    const T *xs = x + static_cast<int64_t>(q / B) * n * B + (q % B);
-    const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s) * B]));
-    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
-        const int32_t j = col[k];
-        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j) * B]));
-        const int32_t tk = tau[k];
-        if (ell <= tk) g[k] += term;
-        else if (ell == tk + 1) t1[k] = term;
-        else if (ell == tk + 2) t2[k] = term;
-    }
+    gather_source<T, B>(row_ptr, col, x, n, s, q, tau, ell, g, t1, t2, lane);
+}
+
+// launch helper: one hop over `slices` slices, optionally gathering X_{l-1}
+template <typename T, int B, int VPL>
+inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s) {
+    using L = Layout<T, B, VPL>;
+    a.light_ctas = ceil_div(a.n - a.n_heavy, kSpmmWarps * L::G);
+    const int gather_ctas = a.gather_ell > 0 ? ceil_div(B, kSpmmWarps) : 0;
+    dim3 grid(a.n_heavy + a.light_ctas + gather_ctas, slices);
+    k_spmm_hop<T, B, VPL><<<grid, kSpmmWarps * 32, 0, s>>>(a);
 }
 
 }  // namespace sc

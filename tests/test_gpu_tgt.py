@@ -153,7 +153,8 @@ def test_fp64_series_matches_oracle(cuda_lib, maker, tau):
 
 
 @pytest.mark.parametrize("B,vpl,heavy,slices", [(32, 1, 128, 0), (32, 2, 4, 1), (32, 4, 7, 2), (64, 1, 3, 0),
-                                                (64, 2, 128, 1), (128, 2, 5, 0), (128, 4, 128, 3)])
+                                                (64, 2, 128, 1), (128, 2, 5, 0), (128, 4, 128, 3),
+                                                (32, -1, 0, 0), (64, -1, 0, 2), (128, -1, 0, 1)])
 def test_fp64_every_kernel_variant(cuda_lib, B, vpl, heavy, slices):
     g = gg.barabasi_albert(700, 6, 5)  # hubs above the small heavy thresholds; 700 % B != 0
     ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, 7)
@@ -162,10 +163,14 @@ def test_fp64_every_kernel_variant(cuda_lib, B, vpl, heavy, slices):
                                 heavy_threshold=heavy, max_slices=slices)
     assert rep["block_width"] == B and rep["rows_split"] == vpl
     assert np.max(np.abs(s - ref)) < TOL64
+    if vpl == -1:  # the TMA-gather kernel sums in the same order as the SIMT kernel
+        with _graph(cuda_lib, g) as G:
+            s1, _, _ = G.all_edges(policy="fixed", ell_fixed=7, precision="fp64", block_width=B, rows_split=1 if B < 128 else 2)
+        assert np.array_equal(s, s1)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", TOL32), ("bf16", TOLBF16)])
-@pytest.mark.parametrize("B,vpl", [(32, 1), (64, 1), (64, 2), (128, 1), (128, 4)])
+@pytest.mark.parametrize("B,vpl", [(32, 1), (64, 1), (64, 2), (128, 1), (128, 4), (32, -1), (64, -1), (128, -1)])
 def test_low_precision_blocks(cuda_lib, prec, tol, B, vpl):
     g = gg.barabasi_albert(1100, 5, 7)
     ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, 7)
@@ -180,7 +185,8 @@ def test_bitwise_deterministic_and_independent_of_launch_shape(cuda_lib):
     g = gg.barabasi_albert(2000, 6, 11)
     outs = []
     with _graph(cuda_lib, g) as G:
-        for B, vpl, heavy, sl in [(64, 1, 128, 0), (64, 1, 128, 0), (32, 4, 9, 1), (128, 1, 40, 2), (128, 2, 1000, 0)]:
+        for B, vpl, heavy, sl in [(64, 1, 128, 0), (64, 1, 128, 0), (32, 4, 9, 1), (128, 1, 40, 2), (128, 2, 1000, 0),
+                                  (64, -1, 0, 0), (32, -1, 0, 3), (128, -1, 0, 0), (64, 0, 0, 0)]:
             s, _, rep = G.all_edges(policy="fixed", ell_fixed=9, precision="fp32", block_width=B, rows_split=vpl,
                                     heavy_threshold=heavy, max_slices=sl)
             outs.append((s, rep["foster_sum"]))
