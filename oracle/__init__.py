@@ -18,4 +18,4 @@ Modules:
   mlp         FP64 reference MLP (features, forward, backward, Adam) for the
               learned truncation length
 """
-from . import exact, philox, series, tgtplus, truncation  # noqa: F401
+from . import exact, learned, philox, series, tgtplus, truncation  # noqa: F401

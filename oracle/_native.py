@@ -42,6 +42,9 @@ def lib():
             L.oracle_cg.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, i32p,
                                     ctypes.c_double, ctypes.c_int32, f64p, i32p, ctypes.c_int32]
             L.oracle_cg.restype = ctypes.c_int
+            L.oracle_series_terms.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p,
+                                              ctypes.POINTER(ctypes.c_int64), f64p, ctypes.c_int32]
+            L.oracle_series_terms.restype = ctypes.c_int
             _lib = L
     return _lib
 

@@ -211,3 +211,64 @@ int oracle_cg(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t
     }
     return status;
 }
+
+/*
+ * Per-hop half terms of Algorithm 2 for the sources listed: for entry k = (i -> j)
+ * of a source row, out[k_local * (L + 1) + l] = (p_l(v_i,v_i) - p_l(v_j,v_i)) / d(v_i)
+ * for l = 0..L, where k_local = k - row_ptr[i] + row_off[si] (row_off: prefix of the
+ * sources' degrees). Used to find, per edge, the least odd length whose
+ * a-posteriori tail bound meets eps.
+ */
+int oracle_series_terms(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t L, int32_t nsrc,
+                        const int32_t *sources, const int64_t *row_off, double *out, int32_t nthreads)
+{
+    if (n <= 0 || !row_ptr || !col_idx || !sources || !row_off || !out || L < 0 || nsrc < 0)
+        return -1;
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double *p_prev = (double *)malloc(sizeof(double) * (size_t)n);
+        double *p_next = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!p_prev || !p_next) {
+#pragma omp atomic write
+            status = -1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int32_t si = 0; si < nsrc; ++si) {
+                const int32_t i = sources[si];
+                const int32_t k0 = row_ptr[i], k1 = row_ptr[i + 1];
+                const double d_i = (double)(k1 - k0);
+                double *o = out + row_off[si] * (int64_t)(L + 1);
+                memset(p_prev, 0, sizeof(double) * (size_t)n);
+                p_prev[i] = 1.0;
+                for (int32_t k = k0; k < k1; ++k) o[(int64_t)(k - k0) * (L + 1)] = 1.0 / d_i;
+                for (int32_t l = 1; l <= L; ++l) {
+                    memset(p_next, 0, sizeof(double) * (size_t)n);
+                    for (int32_t j = 0; j < n; ++j) {
+                        const double pj = p_prev[j];
+                        if (pj > 0.0) {
+                            for (int32_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+                                const int32_t x = col_idx[e];
+                                p_next[x] += pj / (double)(row_ptr[x + 1] - row_ptr[x]);
+                            }
+                        }
+                    }
+                    for (int32_t k = k0; k < k1; ++k)
+                        o[(int64_t)(k - k0) * (L + 1) + l] = p_next[i] / d_i - p_next[col_idx[k]] / d_i;
+                    double *tmp = p_prev;
+                    p_prev = p_next;
+                    p_next = tmp;
+                }
+            }
+        }
+        free(p_prev);
+        free(p_next);
+    }
+    return status;
+}

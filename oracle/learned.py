@@ -1,0 +1,190 @@
+"""Learned per-source truncation length (oracle for the MLP step).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the timed
+CPU baseline; the CUDA path never imports it.
+
+The paper truncates every edge at the a-priori length of Eq. (6). A source
+usually needs far fewer hops: for odd tau the tail of the series is
+sum_k c_k lambda_k^{tau+1} / (1 - lambda_k) with c_k >= 0 (proof of Theorem
+3.2), and writing each term as c_k (1 + lambda_k) lambda_k^{tau-1} *
+lambda_k^2 / (1 - lambda_k^2) gives the a-posteriori bound
+
+    tail(tau) <= lambda*^2 / (1 - lambda*^2) * (t_{tau-1}(e) + t_tau(e)),
+
+with t_l(e) the full hop-l term of Eq. (2): it uses only hops already
+traversed. An edge is certified at the least odd tau where the bound is at
+most eps. The label of source i is the largest certified length over its
+edges; a small MLP predicts it from six per-source features.
+
+Features (in this order):
+  0  log d_i
+  1  log min_{j in N(i)} d_j
+  2  local clustering c_i = triangles(i) / (d_i (d_i - 1) / 2) (0 for d_i < 2)
+  3  log(sum_{j in N(i)} d_j / (2m))      (share of the volume one hop reaches)
+  4  p_2(i, i) = (1/d_i) sum_{j in N(i)} 1/d_j
+  5  log(1 / (1 - lambda_plus))          (the graph's spectral gap)
+
+Network: inputs standardised with the training set's mean and standard
+deviation, then 6 -> 32 -> 32 -> 1 with ReLU after the two hidden layers; the
+output is log L. Loss: mean over sources of (y - log L*)^2 / 2. Optimiser:
+Adam (Kingma and Ba, ICLR 2015) with bias correction. Prediction: the
+smallest odd integer >= exp(y), clipped to [1, cap].
+
+Flat parameter layout (float32, 1313 entries): W1[32][6], b1[32], W2[32][32],
+b2[32], W3[32], b3[1].
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _native, series
+
+H = 32
+NF = 6
+NPARAM = H * NF + H + H * H + H + H + 1
+
+
+def features(n, row_ptr, col_idx, lam_plus):
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col_idx = np.asarray(col_idx, dtype=np.int64)
+    deg = np.diff(row_ptr).astype(np.float64)
+    two_m = deg.sum()
+    F = np.zeros((n, NF))
+    for i in range(n):
+        nb = col_idx[row_ptr[i]:row_ptr[i + 1]]
+        d = deg[i]
+        tri = 0
+        s = set(nb.tolist())
+        for j in nb:
+            for y in col_idx[row_ptr[j]:row_ptr[j + 1]]:
+                if y in s:
+                    tri += 1
+        tri //= 2  # each triangle at i is seen from both of its other corners
+        F[i, 0] = math.log(d)
+        F[i, 1] = math.log(deg[nb].min())
+        F[i, 2] = tri / (d * (d - 1) / 2.0) if d >= 2 else 0.0
+        F[i, 3] = math.log(deg[nb].sum() / two_m)
+        F[i, 4] = np.sum(1.0 / deg[nb]) / d
+        F[i, 5] = math.log(1.0 / (1.0 - lam_plus))
+    return F
+
+
+def hop_terms(n, row_ptr, col_idx, L, sources=None, threads=0):
+    """T[k, l] = (p_l(i,i) - p_l(j,i)) / d_i for l = 0..L and every entry k of
+    the requested sources' rows (other rows NaN)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    src = np.arange(n, dtype=np.int32) if sources is None else np.ascontiguousarray(np.unique(sources), dtype=np.int32)
+    deg = np.diff(rp.astype(np.int64))
+    off = np.zeros(src.size + 1, dtype=np.int64)
+    np.cumsum(deg[src], out=off[1:])
+    out = np.empty(int(off[-1]) * (L + 1))
+    lib = _native.lib()
+    rc = lib.oracle_series_terms(n, _native.ptr(rp, ctypes.c_int32), _native.ptr(ci, ctypes.c_int32), L, src.size,
+                                 _native.ptr(src, ctypes.c_int32), _native.ptr(off, ctypes.c_int64),
+                                 _native.ptr(out, ctypes.c_double), threads or _native.default_threads())
+    if rc != 0:
+        raise RuntimeError("oracle_series_terms failed")
+    T = np.full((ci.size, L + 1), np.nan)
+    out = out.reshape(-1, L + 1)
+    for t, i in enumerate(src):
+        T[rp[i]:rp[i + 1]] = out[off[t]:off[t + 1]]
+    return T
+
+
+def certified_lengths(n, row_ptr, col_idx, eps, lam_star, cap):
+    """Least odd tau <= cap per entry whose a-posteriori bound is <= eps (else cap)."""
+    T = hop_terms(n, row_ptr, col_idx, cap)
+    rev = series.reverse_entries(n, row_ptr, col_idx)
+    full = T + T[rev]  # t_l(e), l = 0..cap
+    factor = lam_star * lam_star / (1.0 - lam_star * lam_star)
+    tau = np.full(full.shape[0], cap, dtype=np.int64)
+    done = np.zeros(full.shape[0], dtype=bool)
+    for t in range(1, cap + 1, 2):
+        ok = (~done) & (factor * (full[:, t - 1] + full[:, t]) <= eps)
+        tau[ok] = t
+        done |= ok
+    return tau
+
+
+def source_labels(n, row_ptr, tau_entries):
+    out = np.zeros(n, dtype=np.int64)
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(row_ptr, dtype=np.int64)))
+    np.maximum.at(out, rows, tau_entries)
+    return out
+
+
+def unpack(theta):
+    theta = np.asarray(theta, dtype=np.float64)
+    o = 0
+
+    def take(shape):
+        nonlocal o
+        size = int(np.prod(shape))
+        v = theta[o:o + size].reshape(shape)
+        o += size
+        return v
+
+    W1 = take((H, NF))
+    b1 = take((H,))
+    W2 = take((H, H))
+    b2 = take((H,))
+    W3 = take((H,))
+    b3 = take((1,))
+    return W1, b1, W2, b2, W3, b3
+
+
+def forward(theta, X):
+    """X: standardised features (N, 6). Returns (y (N,), cache)."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    z1 = X @ W1.T + b1
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ W2.T + b2
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ W3 + b3[0]
+    return y, (X, z1, h1, z2, h2)
+
+
+def loss_and_grad(theta, X, target):
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    N = X.shape[0]
+    r = y - target
+    loss = 0.5 * np.mean(r * r)
+    dy = r / N
+    gW3 = h2.T @ dy
+    gb3 = np.array([dy.sum()])
+    dh2 = np.outer(dy, W3) * (z2 > 0)
+    gW2 = dh2.T @ h1
+    gb2 = dh2.sum(axis=0)
+    dh1 = (dh2 @ W2) * (z1 > 0)
+    gW1 = dh1.T @ X
+    gb1 = dh1.sum(axis=0)
+    grad = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, gb3])
+    return loss, grad
+
+
+def adam_step(theta, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step t (1-based); returns new (theta, m, v)."""
+    m = b1 * m + (1 - b1) * grad
+    v = b2 * v + (1 - b2) * grad * grad
+    mhat = m / (1 - b1 ** t)
+    vhat = v / (1 - b2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def standardise(F):
+    mu = F.mean(axis=0)
+    sd = F.std(axis=0)
+    sd = np.where(sd > 0, sd, 1.0)
+    return mu, sd
+
+
+def predict_lengths(theta, F, mu, sd, cap):
+    y, _ = forward(theta, (F - mu) / sd)
+    L = np.ceil(np.exp(y) - 1e-9).astype(np.int64)
+    L = np.clip(L, 1, cap)
+    return np.where(L % 2 == 0, np.minimum(L + 1, cap if cap % 2 == 1 else cap + 1), L)

@@ -1,0 +1,132 @@
+"""Pins for the learned-length oracle: features, certified lengths, MLP and Adam.
+
+  * features against their definitions on named graphs and against P^2;
+  * per-hop terms against the series oracle and exact matrix powers;
+  * certified lengths: the bound holds at tau_e, fails at tau_e - 2, and the
+    truncated series at tau_e is within eps of the exact value;
+  * the MLP gradient against central finite differences; Adam's first step
+    against its closed form.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+from oracle import exact, learned, series, truncation
+
+
+def _P(g):
+    P = np.zeros((g.n, g.n))
+    for r in range(g.n):
+        nb = g.col_idx[g.row_ptr[r]:g.row_ptr[r + 1]]
+        P[r, nb] = 1.0 / len(nb)
+    return P
+
+
+def test_features_on_named_graphs():
+    F = learned.features(*_csr(gg.complete(6)), 0.3)
+    assert np.allclose(F[:, 2], 1.0) and np.allclose(F[:, 0], np.log(5)) and np.allclose(F[:, 1], np.log(5))
+    F = learned.features(*_csr(gg.star(5)), 0.3)
+    assert F[0, 2] == 0.0 and np.allclose(F[1:, 2], 0.0)  # no triangles; leaves have d = 1
+    assert np.isclose(F[0, 3], np.log(5 / 10)) and np.allclose(F[1:, 3], np.log(5 / 10))
+    g = gg.barbell(4, 1)  # K4 - K4 joined by one edge: corner nodes lose clustering
+    F = learned.features(*_csr(g), 0.5)
+    assert np.isclose(F[0, 2], 1.0) and np.isclose(F[3, 2], 3 / 6)
+    assert np.allclose(F[:, 5], np.log(1 / (1 - 0.5)))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_p2_feature_is_two_step_return_probability(seed):
+    g = gg.tree_plus_gnp(50, 5.0, seed)
+    F = learned.features(*_csr(g), 0.2)
+    P = _P(g)
+    assert np.allclose(F[:, 4], np.diag(P @ P), atol=1e-14)
+
+
+def test_hop_terms_match_series_and_powers():
+    g = gg.tree_plus_gnp(40, 4.0, 3)
+    L = 6
+    T = learned.hop_terms(*_csr(g), L)
+    P = _P(g)
+    d = g.degree
+    rows = g.entry_rows()
+    Pl = [np.linalg.matrix_power(P, l) for l in range(L + 1)]
+    for k in range(0, g.nnz, 7):
+        i, j = rows[k], g.col_idx[k]
+        for l in range(L + 1):
+            assert abs(T[k, l] - (Pl[l][i, i] - Pl[l][j, i]) / d[i]) < 1e-14
+    gsum, t1, t2 = series.half_sums(*_csr(g), 3, extra_steps=2)
+    assert np.allclose(gsum, T[:, :4].sum(axis=1), atol=1e-14)
+    assert np.allclose(t1, T[:, 4], atol=1e-15) and np.allclose(t2, T[:, 5], atol=1e-15)
+
+
+@pytest.mark.parametrize("maker", [lambda: gg.barabasi_albert(600, 5, 1), lambda: gg.tree_plus_gnp(500, 8.0, 2),
+                                   lambda: gg.gnp_lcc(500, 6.0, 3)])
+@pytest.mark.parametrize("eps", [1e-2, 1e-3])
+def test_certified_lengths(maker, eps):
+    g = maker()
+    _, _, lam = truncation.spectrum_extremes(*_csr(g))
+    cap = int(truncation.tau_entries(*_csr(g), eps, lam).max())
+    tau = learned.certified_lengths(*_csr(g), eps, lam, cap)
+    assert np.all(tau % 2 == 1) and np.all(tau <= cap)
+    rev = series.reverse_entries(*_csr(g))
+    assert np.array_equal(tau, tau[rev])
+    T = learned.hop_terms(*_csr(g), cap)
+    full = T + T[rev]
+    f = lam * lam / (1 - lam * lam)
+    idx = np.arange(g.nnz)
+    below = tau < cap
+    assert np.all(f * (full[idx, tau - 1] + full[idx, tau])[below] <= eps)
+    prev = tau - 2
+    has_prev = prev >= 1
+    assert np.all(f * (full[idx, prev - 1] + full[idx, prev])[has_prev] > eps)
+    s, _ = series.series_entries(*_csr(g), tau)
+    r = exact.exact_dense(*_csr(g))
+    assert np.max(np.abs(s - r)) <= eps
+    labels = learned.source_labels(g.n, g.row_ptr, tau)
+    assert labels.max() <= cap and labels.mean() < cap  # the certified lengths are shorter on average
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    theta = rng.normal(0, 0.3, learned.NPARAM)
+    X = rng.normal(size=(40, learned.NF))
+    t = rng.normal(size=40)
+    loss, grad = learned.loss_and_grad(theta, X, t)
+    h = 1e-6
+    for p in rng.choice(learned.NPARAM, size=60, replace=False):
+        e = np.zeros_like(theta)
+        e[p] = h
+        fd = (learned.loss_and_grad(theta + e, X, t)[0] - learned.loss_and_grad(theta - e, X, t)[0]) / (2 * h)
+        assert abs(fd - grad[p]) <= 1e-7 + 1e-5 * abs(fd)
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    theta, m, v = learned.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.1)
+    assert np.allclose(theta, -0.1 * g / (np.abs(g) + 1e-8))
+
+
+def test_training_reduces_loss_and_predictions_are_odd():
+    g = gg.barabasi_albert(800, 5, 4)
+    lp, _, lam = truncation.spectrum_extremes(*_csr(g))
+    cap = int(truncation.tau_entries(*_csr(g), 1e-3, lam).max())
+    labels = learned.source_labels(g.n, g.row_ptr, learned.certified_lengths(*_csr(g), 1e-3, lam, cap))
+    F = learned.features(*_csr(g), lp)
+    mu, sd = learned.standardise(F)
+    X = (F - mu) / sd
+    y = np.log(labels)
+    rng = np.random.default_rng(1)
+    theta = rng.normal(0, 0.2, learned.NPARAM)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    l0 = learned.loss_and_grad(theta, X, y)[0]
+    for t in range(1, 301):
+        loss, grad = learned.loss_and_grad(theta, X, y)
+        theta, m, v = learned.adam_step(theta, grad, m, v, t, lr=1e-2)
+    assert loss < 0.2 * l0
+    L = learned.predict_lengths(theta, F, mu, sd, cap)
+    assert np.all(L % 2 == 1) and L.min() >= 1 and L.max() <= cap
+
+
+def _csr(g):
+    return g.n, g.row_ptr, g.col_idx
