@@ -158,8 +158,9 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
 #define SC_ELL_GLOBAL 0     /* one length for every edge: max of Eq. (6) over all edges */
 #define SC_ELL_PER_EDGE 1   /* tau_ij of Eq. (6) per edge; sources run tau_p (Alg. 2 line 4) */
 #define SC_ELL_FIXED 2      /* opts.ell_fixed for every edge (no eigenvalue needed) */
-#define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP, extended until the
-                               a-posteriori tail bound meets eps (needs a loaded model) */
+#define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP (sc_mlp_load); every edge
+                               is then certified by the bound of sc_certified_lengths and, if it
+                               fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed */
 
 /* storage precision of the propagated probability block */
 #define SC_PREC_FP64 0
@@ -194,9 +195,14 @@ typedef struct sc_options {
     uint32_t flags;           /* SC_OUT_DEVICE | SC_OPT_RECORD_TAIL */
     uint64_t seed;            /* Philox key for TGT+ walks */
     double delta;             /* TGT+ failure probability (0 = 1/n, Section 5.1) */
-    int32_t gamma;            /* CalChi candidates (Alg. 3), default 10 when < 0 */
-    int32_t reserved[7];
+    int32_t gamma;            /* CalChi candidates (Alg. 3), 0..16; default 10 when < 0 */
+    int32_t switch_rule;      /* TGT+: SC_SWITCH_COST (default) or SC_SWITCH_PAPER (Eq. 14 as printed) */
+    int32_t reserved[6];
 } sc_options;
+
+/* TGT+ switch rules (when to stop the traversal and draw walks) */
+#define SC_SWITCH_COST 0   /* measured cost: walks once their time is below the remaining hops' time */
+#define SC_SWITCH_PAPER 1  /* Eq. 14: frontier volume above the sum of walk counts */
 
 /* fills *opts with defaults: eps 1e-3, TGT, FP32, global length, plain estimator, auto B */
 void sc_options_default(sc_options *opts);
@@ -220,9 +226,15 @@ typedef struct sc_report {
     double hop_ms;             /* with SC_OPT_TIME_KERNELS: summed duration of the propagation launches */
     int64_t hop_launches;      /* propagation (SpMM hop) launches */
     double hop_bytes;          /* algorithmic bytes of those launches (part of algorithmic_bytes) */
-    int64_t walks;             /* TGT+: random walks drawn */
+    int64_t walks;             /* TGT+: random walk pairs drawn */
     int32_t edges_extended;    /* learned policy: edges whose length was extended */
-    int32_t reserved[5];
+    int32_t tt_min, tt_max;    /* TGT+: shortest / longest traversal before switching to walks */
+    int32_t switch_tests;      /* TGT+: switch tests run */
+    double switch_ms;          /* TGT+: wall time in switch tests (kernels, copies, host work) */
+    double walk_ms;            /* TGT+: wall time drawing walks (planning, kernels) */
+    int64_t source_hops;       /* sum over sources of hops traversed (the traversal's work) */
+    int32_t extension_rounds;  /* learned policy: rerun rounds for edges that failed their bound */
+    int32_t reserved;
 } sc_report;
 
 /*
@@ -246,6 +258,71 @@ typedef struct sc_report {
  */
 sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                        sc_report *report);
+
+/* ---- learned per-source length (step A8; the paper has no learned part) --- */
+
+#define SC_MLP_FEATURES 6
+#define SC_MLP_HIDDEN 32
+/* flat float parameters: W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3[1] */
+#define SC_MLP_PARAMS 1313
+/* a model = the parameters followed by the 6 feature means and 6 standard deviations */
+#define SC_MLP_MODEL_FLOATS (SC_MLP_PARAMS + 2 * SC_MLP_FEATURES)
+
+/*
+ * sc_source_features -- the model's inputs for every node, host float[n * 6]:
+ * log d_i, log min_{j in N(i)} d_j, local clustering, log(sum_{j in N(i)} d_j / 2m),
+ * p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j, log(1 / (1 - lambda_plus)).
+ * Runs sc_estimate_lambda first if needed.
+ */
+sc_status sc_source_features(sc_graph *g, float *features);
+
+/*
+ * sc_certified_lengths -- per entry the least odd tau whose a-posteriori bound
+ * lambda*^2 / (1 - lambda*^2) * (t_{tau-1}(e) + t_tau(e)) is at most eps, where
+ * t_l(e) is the hop-l term of Eq. (2) (the bound follows from the mode
+ * expansion in the proof of Theorem 3.2); the a-priori length of Eq. (6) when
+ * none below it passes. per_entry: host int32[nnz]; per_source (nullable):
+ * host int32[n], the maximum over the row (the training label); cap
+ * (nullable): the a-priori length. Traverses every source to the cap with all
+ * hop terms recorded (8 (cap + 1) nnz bytes of device scratch).
+ */
+sc_status sc_certified_lengths(sc_graph *g, double eps, int32_t precision, int32_t *per_entry, int32_t *per_source,
+                               int32_t *cap);
+
+typedef struct sc_mlp_train_opts {
+    int32_t epochs;       /* full-batch Adam steps */
+    float lr;             /* learning rate */
+    float beta1, beta2, adam_eps;  /* 0 = 0.9, 0.999, 1e-8 */
+    int32_t precision;    /* block precision used for the labels */
+    double eps;           /* accuracy the labels certify */
+} sc_mlp_train_opts;
+
+/*
+ * sc_mlp_train -- builds the training set from `graphs` (features and log of
+ * the certified per-source lengths), standardises the features, and trains
+ * the MLP on the device (loss: mean (y - log L*)^2 / 2; full-batch Adam).
+ *   init_params : host float[SC_MLP_PARAMS], the starting weights (caller's choice)
+ *   model_out   : host float[SC_MLP_MODEL_FLOATS]
+ *   loss_curve  : host float[epochs], nullable: the loss before each step
+ * Work runs on the stream of graphs[0].
+ */
+sc_status sc_mlp_train(sc_graph *const *graphs, int32_t count, const sc_mlp_train_opts *opts,
+                       const float *init_params, float *model_out, float *loss_curve);
+
+/* sc_mlp_load -- copies a model (host float[SC_MLP_MODEL_FLOATS]) into the graph for SC_ELL_LEARNED */
+sc_status sc_mlp_load(sc_graph *g, const float *model);
+
+/* sc_mlp_predict -- the per-source lengths the loaded model gives (host int32[n]),
+ * the smallest odd integer >= exp(output), clipped to [1, cap] */
+sc_status sc_mlp_predict(sc_graph *g, int32_t cap, int32_t *lengths);
+
+/*
+ * sc_mlp_loss_grad -- one evaluation of the training loss and its gradient on
+ * host data (features host float[count * 6], targets host float[count]);
+ * model as for sc_mlp_load. loss: host float; grad: host float[SC_MLP_PARAMS].
+ */
+sc_status sc_mlp_loss_grad(const float *model, const float *features, const float *targets, int32_t count,
+                           float *loss, float *grad, void *stream);
 
 /* ---- allocation-free variant ---------------------------------------------- */
 

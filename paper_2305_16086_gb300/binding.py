@@ -34,8 +34,11 @@ SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
 EXPORTS = [
     "sc_graph_create", "sc_graph_get_info", "sc_graph_destroy", "sc_estimate_lambda",
     "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
-    "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc",
+    "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
+    "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
 ]
+MLP_PARAMS, MLP_FEATURES = 1313, 6
+MLP_MODEL_FLOATS = MLP_PARAMS + 2 * MLP_FEATURES
 
 
 class GraphInfo(ctypes.Structure):
@@ -62,7 +65,7 @@ class Options(ctypes.Structure):
                 ("rows_split", ctypes.c_int32), ("heavy_threshold", ctypes.c_int32),
                 ("max_slices", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("delta", ctypes.c_double), ("gamma", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("switch_rule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Report(ctypes.Structure):
@@ -75,10 +78,18 @@ class Report(ctypes.Structure):
                 ("propagate_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("hop_ms", ctypes.c_double), ("hop_launches", ctypes.c_int64), ("hop_bytes", ctypes.c_double),
                 ("walks", ctypes.c_int64), ("edges_extended", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("tt_min", ctypes.c_int32), ("tt_max", ctypes.c_int32),
+                ("switch_tests", ctypes.c_int32), ("switch_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
+                ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class MlpTrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("precision", ctypes.c_int32),
+                ("eps", ctypes.c_double)]
 
 
 class ScError(RuntimeError):
@@ -124,6 +135,19 @@ def load(path: str = LIB_PATH):
     L.sc_abi_version.restype = ctypes.c_int32
     L.sc_all_edges_noalloc.argtypes = [i32, i64, vp, vp, i32, vp, vp]
     L.sc_all_edges_noalloc.restype = ctypes.c_int
+    f32p = ctypes.POINTER(ctypes.c_float)
+    L.sc_source_features.argtypes = [vp, f32p]
+    L.sc_source_features.restype = ctypes.c_int
+    L.sc_certified_lengths.argtypes = [vp, f64, i32, i32p, i32p, i32p]
+    L.sc_certified_lengths.restype = ctypes.c_int
+    L.sc_mlp_train.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(MlpTrainOpts), f32p, f32p, f32p]
+    L.sc_mlp_train.restype = ctypes.c_int
+    L.sc_mlp_load.argtypes = [vp, f32p]
+    L.sc_mlp_load.restype = ctypes.c_int
+    L.sc_mlp_predict.argtypes = [vp, i32, i32p]
+    L.sc_mlp_predict.restype = ctypes.c_int
+    L.sc_mlp_loss_grad.argtypes = [f32p, f32p, f32p, i32, f32p, f32p, vp]
+    L.sc_mlp_loss_grad.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -227,7 +251,8 @@ class Graph:
     @staticmethod
     def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
-                record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None) -> Options:
+                record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
+                switch="cost") -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
         o.eps = eps
@@ -246,6 +271,7 @@ class Graph:
         o.delta = delta
         if gamma is not None:
             o.gamma = gamma
+        o.switch_rule = {"cost": 0, "paper": 1}[switch]
         return o
 
     def all_edges(self, out=None, tail_bound=None, **kw):
@@ -285,3 +311,65 @@ def all_edges_noalloc(row_ptr, col_idx, ell: int, out, stream=None):
                                        ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
            "sc_all_edges_noalloc")
     return out
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def source_features(graph) -> np.ndarray:
+    out = np.empty((graph.n, MLP_FEATURES), dtype=np.float32)
+    _check(load().sc_source_features(graph._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "sc_source_features")
+    return out
+
+
+def certified_lengths(graph, eps: float, precision: str = "fp64"):
+    """(per_entry int32[nnz], per_source int32[n], cap)"""
+    pe = np.empty(graph.nnz, dtype=np.int32)
+    ps = np.empty(graph.n, dtype=np.int32)
+    cap = ctypes.c_int32()
+    _check(load().sc_certified_lengths(graph._h, eps, PREC[precision], _i32p(pe), _i32p(ps), ctypes.byref(cap)),
+           "sc_certified_lengths")
+    return pe, ps, int(cap.value)
+
+
+def mlp_train(graphs, init_params, epochs=300, lr=1e-2, eps=1e-3, precision="fp32"):
+    """Train on the GPU. Returns (model float32[MLP_MODEL_FLOATS], loss curve float32[epochs])."""
+    hs = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
+    opts = MlpTrainOpts(epochs, lr, 0.0, 0.0, 0.0, PREC[precision], eps)
+    p, pp = _f32(init_params)
+    model = np.empty(MLP_MODEL_FLOATS, dtype=np.float32)
+    curve = np.empty(epochs, dtype=np.float32)
+    _check(load().sc_mlp_train(hs, len(graphs), ctypes.byref(opts), pp,
+                               model.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                               curve.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "sc_mlp_train")
+    return model, curve
+
+
+def mlp_load(graph, model):
+    m, mp = _f32(model)
+    _check(load().sc_mlp_load(graph._h, mp), "sc_mlp_load")
+
+
+def mlp_predict(graph, cap: int) -> np.ndarray:
+    out = np.empty(graph.n, dtype=np.int32)
+    _check(load().sc_mlp_predict(graph._h, cap, _i32p(out)), "sc_mlp_predict")
+    return out
+
+
+def mlp_loss_grad(model, features, targets):
+    m, mp = _f32(model)
+    f, fp = _f32(features)
+    t, tp = _f32(targets)
+    loss = ctypes.c_float()
+    grad = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(load().sc_mlp_loss_grad(mp, fp, tp, t.size, ctypes.byref(loss),
+                                   grad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_handle(None)),
+           "sc_mlp_loss_grad")
+    return float(loss.value), grad

@@ -147,8 +147,15 @@ struct sc_graph {
     sc::DevBuf<int32_t> part;
     int32_t nparts = 0;
     int32_t part_target = -1;
-    // autotuned (block width, lane split) per request key
+    // autotuned (block width, lane split) per request key, and its measured ms per source-hop
     std::map<long long, std::pair<int, int>> tuned;
+    std::map<long long, double> tuned_cost;
+    double walk_step_ns = 0.5;  // TGT+ cost rule: measured device time per walk step (running estimate)
+    long long last_walk_steps = 0;
+
+    // learned length: features (n x 6) and the loaded model
+    sc::DevBuf<float> features, mlp;
+    bool features_ready = false, mlp_loaded = false;
 
     // cached eigenvalue estimate
     bool has_lambda = false;
@@ -159,6 +166,12 @@ struct sc_graph {
     sc::DevBuf<double> acc_g, acc_t1, acc_t2;
     sc::DevBuf<int32_t> tau_entry, src_list, status;
     sc::DevBuf<double> scratch_d;
+    // TGT+ work buffers: CalChi partial and per-column statistics, walk counts
+    sc::DevBuf<double> tp_pval, tp_pmin, tp_pmax, tp_cval, tp_cmin, tp_cmax;
+    sc::DevBuf<int32_t> tp_pid, tp_cid;
+    sc::DevBuf<long long> tp_pvol, tp_cvol, tp_walks, tp_counters, tp_packed, tp_chunk_w0;
+    sc::DevBuf<int32_t> tp_eq, tp_ek, tp_chunk_entry, tp_entry_chunk0;
+    sc::DevBuf<double> tp_chunk_sum;
     std::vector<cudaEvent_t> hop_events;  // pairs bracketing timed propagation launches
     ~sc_graph() {
         for (cudaEvent_t e : hop_events) cudaEventDestroy(e);

@@ -56,6 +56,7 @@ struct TmaHopArgs {
     const int32_t *tau;
     int32_t gather_ell;
     double *g, *t1, *t2;
+    GatherRec rec;
     int32_t *status;       // bit 0: an mbarrier wait expired
 };
 
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_hop_tma(const __grid_constan
             const int32_t s = a.src[q];
             if (s >= 0)
                 gather_source<T, B>(a.row_ptr, a.col, static_cast<const T *>(a.x_prev), n, s, q, a.tau, a.gather_ell,
-                                    a.g, a.t1, a.t2, lane);
+                                    a.g, a.t1, a.t2, lane, a.rec);
         }
         return;
     }

@@ -213,11 +213,12 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
             ha.g = acc;
             ha.t1 = nullptr;
             ha.t2 = nullptr;
+            ha.rec = GatherRec{0, nullptr, 0};
             launch_spmm_hop<double, B, 1>(ha, 1, s);
             std::swap(a, b);
         }
         k_gather<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,
-                                                            nullptr);
+                                                            nullptr, GatherRec{0, nullptr, 0});
         SC_LAUNCH_CHECK();
     }
     k_na_combine<<<ceil_div(n, 8), 256, 0, s>>>(row_ptr, col_idx, rev, inv_deg, acc, n, s_hat);

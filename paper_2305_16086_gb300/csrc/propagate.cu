@@ -2,6 +2,7 @@
 // blocks of sources, the per-edge combine of Alg. 2 line 12, the
 // end-corrected estimator and the a-posteriori tail bound.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -9,11 +10,20 @@
 #include <cudaTypedefs.h>
 
 #include "hop_tma.cuh"
+#include "tgtplus.cuh"
 #include "propagate.cuh"
 
 namespace sc {
 
 sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
+void tgtplus_reserve(sc_graph *g, int slices, int B);
+void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, const int32_t *src, const int32_t *h_src,
+                   int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
+                   long long *rhs, long long *steps, cudaStream_t s);
+long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32_t *src, const int32_t *h_src,
+                        int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s);
+long long tgtplus_last_steps(sc_graph *g);
+constexpr int kCostRuleHops = 4;  // the cost rule tests the last hops only
 void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_entry, int32_t *tau_src,
                         int32_t *ell_global_host);
 
@@ -126,6 +136,7 @@ struct HopLaunch {
     int gather_ell;  // 0: no fused gather
     double *g, *t1, *t2;
     int32_t *status;  // TMA kernel: bounded-wait expiry flag
+    GatherRec rec;
 };
 
 // ---- TMA-gather variant (lane split value 0) --------------------------------
@@ -190,6 +201,7 @@ static void hop_tma_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.g = h.g;
     a.t1 = h.t1;
     a.t2 = h.t2;
+    a.rec = h.rec;
     a.status = h.status;
     const int gather_ctas = h.gather_ell > 0 ? ceil_div(B, kTmaWarps) : 0;
     dim3 grid(a.part_ctas + gather_ctas, h.slices);
@@ -214,6 +226,7 @@ static void hop_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.g = h.g;
     a.t1 = h.t1;
     a.t2 = h.t2;
+    a.rec = h.rec;
     launch_spmm_hop<T, B, VPL>(a, h.slices, s);
 }
 
@@ -274,7 +287,7 @@ void launch_hop(const sc_graph *g, int prec, int B, int vpl, const HopLaunch &h,
 template <typename T, int B>
 static void first_gather_t(const sc_graph *g, bool first, const void *x, const int32_t *src, int nsrc,
                            const int32_t *tau, int ell, double *acc_g, double *acc_t1, double *acc_t2,
-                           cudaStream_t s) {
+                           const GatherRec &rec, cudaStream_t s) {
     const int warps = 8;
     const int blocks = ceil_div(nsrc, warps);
     if (first)
@@ -282,27 +295,28 @@ static void first_gather_t(const sc_graph *g, bool first, const void *x, const i
                                                          nsrc, static_cast<T *>(const_cast<void *>(x)), g->n);
     else
         k_gather<T, B><<<blocks, warps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), static_cast<const T *>(x),
-                                                      g->n, src, nsrc, tau, ell, acc_g, acc_t1, acc_t2);
+                                                      g->n, src, nsrc, tau, ell, acc_g, acc_t1, acc_t2, rec);
 }
 
 template <typename T>
 static void first_gather_p(const sc_graph *g, int B, bool first, const void *x, const int32_t *src, int nsrc,
-                           const int32_t *tau, int ell, double *a, double *b, double *c, cudaStream_t s) {
+                           const int32_t *tau, int ell, double *a, double *b, double *c, const GatherRec &rec,
+                           cudaStream_t s) {
     switch (B) {
-    case 32: first_gather_t<T, 32>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
-    case 64: first_gather_t<T, 64>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
-    case 128: first_gather_t<T, 128>(g, first, x, src, nsrc, tau, ell, a, b, c, s); break;
+    case 32: first_gather_t<T, 32>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
+    case 64: first_gather_t<T, 64>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
+    case 128: first_gather_t<T, 128>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
     default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
     }
 }
 
 void launch_first_or_gather(const sc_graph *g, int prec, int B, bool first, const void *x, const int32_t *src,
                             int nsrc, const int32_t *tau, int ell, double *a, double *b, double *cc,
-                            cudaStream_t s) {
+                            const GatherRec &rec, cudaStream_t s) {
     switch (prec) {
-    case SC_PREC_FP64: first_gather_p<double>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
-    case SC_PREC_FP32: first_gather_p<float>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
-    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, s); break;
+    case SC_PREC_FP64: first_gather_p<double>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
+    case SC_PREC_FP32: first_gather_p<float>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
+    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
     }
     SC_LAUNCH_CHECK();
 }
@@ -324,6 +338,7 @@ static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
 // keep the fastest per source-hop. Cached per graph, precision and request.
 struct TuneResult {
     int B, vpl;
+    double ms_per_source_hop;  // measured by the autotuner (0 if it did not time)
 };
 
 static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_slices, cudaStream_t s) {
@@ -331,16 +346,13 @@ static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_sl
                           (static_cast<long long>(fixV) << 16) ^ static_cast<long long>(max_slices & 0xffff) ^
                           (static_cast<long long>(g->n_heavy) << 44);
     auto it = g->tuned.find(key);
-    if (it != g->tuned.end()) return TuneResult{it->second.first, it->second.second};
+    if (it != g->tuned.end()) return TuneResult{it->second.first, it->second.second, g->tuned_cost[key]};
     std::vector<std::pair<int, int>> cands;
     for (int B : {32, 64, 128})
         for (int v : {0, 1, 2, 4})
             if ((fixB == 0 || fixB == B) && (fixV < 0 || fixV == v) && cfg_valid(prec, B, v)) cands.push_back({B, v});
     if (cands.empty()) SC_FAIL(SC_ERR_INVALID_ARG, "no admissible kernel for B=%d split=%d", fixB, fixV);
-    if (cands.size() == 1) {
-        g->tuned[key] = cands[0];
-        return TuneResult{cands[0].first, cands[0].second};
-    }
+
     const size_t elem = elem_size(prec);
     size_t need = 0;
     for (auto &c : cands) need = std::max(need, slices_for(g, c.first, elem, max_slices) * static_cast<size_t>(g->n) * c.first * elem);
@@ -354,7 +366,8 @@ static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_sl
     std::pair<int, int> pick = cands[0];
     for (auto &c : cands) {
         const int sl = slices_for(g, c.first, elem, max_slices);
-        HopLaunch h{g->xa.get(), g->xb.get(), sl, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr, g->status.get()};
+        HopLaunch h{g->xa.get(), g->xb.get(), sl, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr, g->status.get(),
+                    GatherRec{0, nullptr, 0}};
         launch_hop(g, prec, c.first, c.second, h, s);  // warm-up
         SC_CUDA(cudaEventRecord(e0, s));
         const int reps = 3;
@@ -372,28 +385,254 @@ static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_sl
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->tuned[key] = pick;
-    return TuneResult{pick.first, pick.second};
+    g->tuned_cost[key] = best;
+    return TuneResult{pick.first, pick.second, best};
+}
+
+// ---------------------------------------------------------------------------
+// accumulator reset for a set of source rows (all rows when rows == nullptr):
+// the hop-0 term of Eq. (9) is 1 (unscaled); with record mode 1 the hop-0 term
+// is also the "tau - 1" record of a length-1 entry
+// ---------------------------------------------------------------------------
+__global__ void k_reset_rows(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rows, int32_t nrows,
+                             const int32_t *__restrict__ tau, int mode, double *__restrict__ g, double *__restrict__ t1,
+                             double *__restrict__ t2, double *__restrict__ rec_all, int rec_stride) {
+    const int32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= nrows) return;
+    const int32_t r = rows ? rows[t] : t;
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        g[k] = 1.0;
+        const int32_t tk = tau[k];
+        t1[k] = (mode == 1 && tk == 1) ? 1.0 : 0.0;
+        t2[k] = (mode == 1 && tk == 0) ? 1.0 : 0.0;
+        if (rec_all) rec_all[static_cast<int64_t>(k) * rec_stride] = 1.0;
+    }
+}
+
+// tau_e = min(L_i, L_j) for every entry (one length per edge for both halves)
+__global__ void k_tau_min_of_sources(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                     const int32_t *__restrict__ L, int32_t n, int32_t *__restrict__ tau) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int32_t Lr = L[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) tau[k] = min(Lr, L[col[k]]);
+}
+
+// Extension step of the learned policy: an entry whose bound exceeds eps and
+// whose length is below the a-priori cap gets tau <- min(2 tau + 1, cap);
+// its row is marked for a rerun. Both directions of an edge carry the same
+// bound, so both endpoints are marked.
+__global__ void k_extend_failing(const int32_t *__restrict__ row_ptr, const double *__restrict__ bound, int32_t n,
+                                 double eps, int32_t cap, int32_t *__restrict__ tau, int32_t *__restrict__ row_flag,
+                                 unsigned long long *count) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int any = 0;
+    unsigned long long c = 0;
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        if (bound[k] > eps && tau[k] < cap) {
+            tau[k] = min(2 * tau[k] + 1, cap);
+            any = 1;
+            ++c;
+        }
+    }
+    any = __any_sync(0xffffffffu, any);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        row_flag[r] = any;
+        if (c) atomicAdd(count, c);
+    }
+}
+
+// per-source maximum of tau over its row
+__global__ void k_row_max(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ tau, int32_t n,
+                          int32_t *__restrict__ out) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int32_t m = 0;
+    for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) m = max(m, tau[k]);
+    out[r] = m;
+}
+
+void learned_lengths(sc_graph *g, int32_t cap, int32_t *L_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// the block loop: propagates the given sources in blocks, longest first
+// ---------------------------------------------------------------------------
+struct Run {
+    sc_graph *g;
+    const sc_options *o;
+    cudaStream_t s;
+    int prec, B, vpl, slices;
+    size_t slice_bytes;
+    bool plus, time_kernels;
+    int gamma;
+    double log2md;
+    int extra;  // hops beyond the per-source length (records of tau+1, tau+2)
+    GatherRec rec;
+    double ms_per_source_hop;
+    // statistics
+    int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0;
+    double alg_bytes = 0.0, switch_ms = 0.0, walk_ms = 0.0;
+    int32_t ell_min_src = INT32_MAX, ell_max_src = 0, tt_min = INT32_MAX, tt_max = 0, switch_tests = 0;
+};
+
+static double wall_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// sources: the node ids to propagate; len[v]: hops source v needs
+static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<int32_t> &len) {
+    sc_graph *g = R.g;
+    cudaStream_t s = R.s;
+    const int32_t n = g->n;
+    const int64_t nnz = g->nnz;
+    const int B = R.B;
+    const int S = R.slices * B;
+    if (sources.empty()) return;
+    std::stable_sort(sources.begin(), sources.end(), [&](int32_t a, int32_t b) { return len[a] > len[b]; });
+    const int64_t ns = static_cast<int64_t>(sources.size());
+    const int64_t nsuper = (ns + S - 1) / S;
+    std::vector<int32_t> h_src(nsuper * S, -1);
+    std::copy(sources.begin(), sources.end(), h_src.begin());
+    g->src_list.reserve(h_src.size());
+    SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (R.time_kernels) {
+        int64_t total_hops = 0;
+        for (int64_t sb = 0; sb < nsuper; ++sb) total_hops += std::max(len[sources[sb * S]] + R.extra - 1, 0);
+        while (static_cast<int64_t>(g->hop_events.size()) < 2 * (R.hop_launches + total_hops)) {
+            cudaEvent_t e;
+            SC_CUDA(cudaEventCreate(&e));
+            g->hop_events.push_back(e);
+        }
+    }
+    cudaEvent_t ev_w0, ev_w1;
+    SC_CUDA(cudaEventCreate(&ev_w0));
+    SC_CUDA(cudaEventCreate(&ev_w1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{ev_w0, ev_w1};
+    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
+                                       2.0 * static_cast<double>(R.slice_bytes);
+    for (int64_t sb = 0; sb < nsuper; ++sb) {
+        const int64_t first = sb * S;
+        const int nsrc = static_cast<int>(std::min<int64_t>(S, ns - first));
+        const int used_slices = (nsrc + B - 1) / B;
+        int32_t L = len[sources[first]];  // longest first
+        for (int q = 0; q < nsrc; ++q) {
+            R.ell_min_src = std::min(R.ell_min_src, len[sources[first + q]] + R.extra);
+            R.ell_max_src = std::max(R.ell_max_src, len[sources[first + q]] + R.extra);
+        }
+        L += R.extra;
+        if (L == 0) continue;
+        const int32_t *src = g->src_list.get() + first;
+        void *xa = g->xa.get(), *xb = g->xb.get();
+        SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * R.slice_bytes, s));
+        launch_first_or_gather(g, R.prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, R.rec, s);
+        R.launches += 1;  // the memset is not a kernel of ours
+        int32_t tt = L;   // hops traversed; TGT+ may switch to walks earlier
+        for (int ell = 2; ell <= L; ++ell) {
+            const bool paper_rule = R.o->switch_rule == SC_SWITCH_PAPER;
+            if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
+                // switch test after hop ell-1. Paper rule (Eq. 14): frontier volume against the
+                // sum of walk counts. Cost rule: predicted walk time against the time of the
+                // L - (ell-1) hops the walks would replace (hop time measured by the autotuner,
+                // walk-step time measured on earlier walk launches).
+                long long lhs = 0, rhs = 0, steps = 0;
+                const double t0 = wall_ms();
+                tgtplus_check(g, R.prec, B, xa, used_slices, src, h_src.data() + first, nsrc, g->tau_entry.get(),
+                              ell - 1, R.gamma, R.o->eps, R.log2md, &lhs, &rhs, &steps, s);
+                R.switch_ms += wall_ms() - t0;
+                ++R.switch_tests;
+                R.launches += 3;
+                const double hop_ms = R.ms_per_source_hop * used_slices * B;
+                const bool go = paper_rule ? (lhs > rhs)
+                                           : (static_cast<double>(steps) * g->walk_step_ns * 1e-6 <
+                                              static_cast<double>(L - (ell - 1)) * hop_ms);
+                if (go) {
+                    tt = ell - 1;
+                    break;
+                }
+            }
+            // hop ell computes X_ell and, in its tail CTAs, gathers X_{ell-1}
+            HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
+                        g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
+            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
+            launch_hop(g, R.prec, B, R.vpl, h, s);
+            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], s));
+            ++R.hop_launches;
+            std::swap(xa, xb);
+            R.launches += 1;
+            R.alg_bytes += used_slices * hop_bytes_per_slice;
+        }
+        launch_first_or_gather(g, R.prec, B, false, xa, src, nsrc, g->tau_entry.get(), tt, g->acc_g.get(),
+                               g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+        R.launches += 1;
+        R.hops += tt;
+        R.source_hops += static_cast<int64_t>(tt) * nsrc;
+        if (R.plus) {
+            R.tt_min = std::min(R.tt_min, tt);
+            R.tt_max = std::max(R.tt_max, tt);
+            if (tt < L) {
+                // Alg. 4 lines 12-17: walk tails from X_tt with the counts of the last check
+                const double t0 = wall_ms();
+                SC_CUDA(cudaEventRecord(ev_w0, s));
+                const long long pairs = tgtplus_walks(g, R.prec, B, xa, src, h_src.data() + first, nsrc,
+                                                      g->tau_entry.get(), tt, R.o->seed, g->acc_g.get(), s);
+                SC_CUDA(cudaEventRecord(ev_w1, s));
+                SC_CUDA(cudaEventSynchronize(ev_w1));
+                R.walk_ms += wall_ms() - t0;
+                R.launches += 3;
+                R.walks += pairs;
+                float wms = 0.f;
+                SC_CUDA(cudaEventElapsedTime(&wms, ev_w0, ev_w1));
+                const long long st = tgtplus_last_steps(g);
+                if (st > 1000) g->walk_step_ns = 0.5 * g->walk_step_ns + 0.5 * (1e6 * wms / static_cast<double>(st));
+            }
+        }
+    }
+    int32_t h_status = 0;
+    SC_CUDA(cudaMemcpyAsync(&h_status, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    if (h_status & 1) SC_FAIL(SC_ERR_TIMEOUT, "a bounded mbarrier wait expired in the TMA hop kernel");
 }
 
 // ---------------------------------------------------------------------------
 // the driver
 // ---------------------------------------------------------------------------
-static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep) {
+static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep,
+                           double *rec_all = nullptr, int rec_stride = 0) {
     if (!g || !s_hat) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or output");
     sc_options o;
     if (o_in) o = *o_in;
     else sc_options_default(&o);
     if (!(o.eps > 0.0 && o.eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1), got %g", o.eps);
     if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
-    if (o.mode != SC_MODE_TGT) SC_FAIL(SC_ERR_UNSUPPORTED, "mode %d is not available in sc_all_edges yet", o.mode);
-    if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_PER_EDGE && o.ell_policy != SC_ELL_FIXED)
-        SC_FAIL(SC_ERR_UNSUPPORTED, "length policy %d", o.ell_policy);
+    if (o.mode != SC_MODE_TGT && o.mode != SC_MODE_TGT_PLUS) SC_FAIL(SC_ERR_INVALID_ARG, "mode %d", o.mode);
+    const bool plus = o.mode == SC_MODE_TGT_PLUS;
+    if (plus && (o.estimator != SC_EST_PLAIN || (o.flags & SC_OPT_RECORD_TAIL) || o.ell_policy == SC_ELL_LEARNED))
+        SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ takes the plain estimator, no tail records and an Eq. 6 length");
+    const int gamma = o.gamma < 0 ? 10 : o.gamma;
+    if (plus && gamma > kGammaMax) SC_FAIL(SC_ERR_UNSUPPORTED, "gamma %d above %d", gamma, kGammaMax);
+    if (o.ell_policy < SC_ELL_GLOBAL || o.ell_policy > SC_ELL_LEARNED) SC_FAIL(SC_ERR_INVALID_ARG, "length policy %d", o.ell_policy);
     if (o.ell_policy == SC_ELL_FIXED && o.ell_fixed < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_fixed < 0");
     if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
+    const bool learned = o.ell_policy == SC_ELL_LEARNED;
+    if (learned && !g->mlp_loaded) SC_FAIL(SC_ERR_INVALID_ARG, "no model loaded: call sc_mlp_load first");
+    if (learned && o.estimator != SC_EST_PLAIN)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "the learned length certifies the plain estimator");
     const bool out_dev = (o.flags & SC_OUT_DEVICE) != 0;
     const bool time_kernels = (o.flags & SC_OPT_TIME_KERNELS) != 0;
-    const bool record_tail = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
-    const bool need_lambda = o.ell_policy != SC_ELL_FIXED || record_tail;
+    const bool record_after = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
+    const bool need_lambda = o.ell_policy != SC_ELL_FIXED || record_after;
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
     const int64_t nnz = g->nnz;
@@ -418,30 +657,39 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
     }
     if (o.ell_policy != SC_ELL_FIXED && (g->bipartite || g->lam.lambda_star >= 1.0))
-        SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1 (bipartite graph): no finite length meets eps; use a fixed or "
-                                    "learned length with the end-corrected estimator");
+        SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1 (bipartite graph): no finite length meets eps; use a fixed "
+                                    "length with the end-corrected estimator");
+    const double lam_star = g->lam.lambda_star;
 
     // ---- truncation lengths --------------------------------------------------
     g->tau_entry.reserve(nnz);
     DevBuf<int32_t> tau_src;
     tau_src.reserve(n);
-    std::vector<int32_t> h_tau_src(n);
+    std::vector<int32_t> len(n);
     int32_t ell_global = 0;
     if (o.ell_policy == SC_ELL_FIXED) {
         ell_global = o.ell_fixed;
-        std::fill(h_tau_src.begin(), h_tau_src.end(), o.ell_fixed);
+        std::fill(len.begin(), len.end(), o.ell_fixed);
         fill_i32(g->tau_entry.get(), nnz, o.ell_fixed, s);
     } else {
-        tau_entries_device(g, o.eps, g->lam.lambda_star, g->tau_entry.get(), tau_src.get(), &ell_global);
+        // TGT+ asks for a tail of at most eps/2 and leaves eps/2 to the walks (Alg. 4 line 2)
+        tau_entries_device(g, plus ? 0.5 * o.eps : o.eps, lam_star, g->tau_entry.get(), tau_src.get(), &ell_global);
         if (o.ell_policy == SC_ELL_GLOBAL) {
-            std::fill(h_tau_src.begin(), h_tau_src.end(), ell_global);
+            std::fill(len.begin(), len.end(), ell_global);
             fill_i32(g->tau_entry.get(), nnz, ell_global, s);
+        } else if (o.ell_policy == SC_ELL_LEARNED) {
+            // per-source lengths from the model, capped by the a-priori length of Eq. 6
+            learned_lengths(g, ell_global, tau_src.get(), s);
+            k_tau_min_of_sources<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), tau_src.get(), n,
+                                                                  g->tau_entry.get());
+            k_row_max<<<ceil_div(n, 256), 256, 0, s>>>(g->row_ptr.get(), g->tau_entry.get(), n, tau_src.get());
+            SC_LAUNCH_CHECK();
+            SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         } else {
-            SC_CUDA(cudaMemcpyAsync(h_tau_src.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         }
         SC_CUDA(cudaStreamSynchronize(s));
     }
-    const int extra = record_tail ? 2 : 0;
 
     // ---- block configuration -------------------------------------------------
     const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 256;
@@ -456,138 +704,132 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     // rows_split: 0 = automatic, -1 = the TMA-gather kernel, 1/2/4 = SIMT lane split
     const int fixV = o.rows_split == 0 ? -1 : (o.rows_split < 0 ? 0 : o.rows_split);
     const TuneResult tr = autotune(g, o.precision, o.block_width, fixV, o.max_slices, s);
-    const int prec = o.precision, B = tr.B, vpl = tr.vpl;
-    const size_t elem = elem_size(prec);
-    const size_t slice_bytes = static_cast<size_t>(n) * B * elem;
-    const int64_t nblocks_total = (static_cast<int64_t>(n) + B - 1) / B;
-    const int slices = slices_for(g, B, elem, o.max_slices);
-    const int S = slices * B;
+    Run R;
+    R.g = g;
+    R.o = &o;
+    R.s = s;
+    R.prec = o.precision;
+    R.B = tr.B;
+    R.vpl = tr.vpl;
+    const size_t elem = elem_size(R.prec);
+    R.slice_bytes = static_cast<size_t>(n) * R.B * elem;
+    R.slices = slices_for(g, R.B, elem, o.max_slices);
+    R.plus = plus;
+    R.time_kernels = time_kernels;
+    R.gamma = gamma;
+    const double delta = o.delta > 0.0 ? o.delta : 1.0 / static_cast<double>(n);  // Section 5.1: delta = 1/n
+    R.log2md = std::log(2.0 * static_cast<double>(nnz / 2) / delta);
+    R.extra = record_after ? 2 : 0;
+    R.rec = GatherRec{learned ? 1 : 0, rec_all, rec_stride};
+    R.ms_per_source_hop = tr.ms_per_source_hop;
+    const int64_t nblocks_total = (static_cast<int64_t>(n) + R.B - 1) / R.B;
 
-    // source order: longest runs first so a launch holds similar lengths
-    std::vector<int32_t> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    if (o.ell_policy == SC_ELL_PER_EDGE)
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return h_tau_src[a] > h_tau_src[b]; });
-    const int64_t nsuper = (n + S - 1) / S;
-    std::vector<int32_t> h_src(nsuper * S, -1);
-    std::copy(order.begin(), order.end(), h_src.begin());
-
-    g->src_list.reserve(h_src.size());
-    SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    g->xa.reserve(slices * slice_bytes);
-    g->xb.reserve(slices * slice_bytes);
+    g->xa.reserve(R.slices * R.slice_bytes);
+    g->xb.reserve(R.slices * R.slice_bytes);
     g->acc_g.reserve(nnz);
     g->acc_t1.reserve(nnz);
     g->acc_t2.reserve(nnz);
-    k_init_acc<<<ceil_div(nnz, 256), 256, 0, s>>>(g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), nnz);
+    k_reset_rows<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), nullptr, n, g->tau_entry.get(), R.rec.mode,
+                                                g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
     SC_LAUNCH_CHECK();
-    int64_t launches = 1 + (o.ell_policy == SC_ELL_FIXED ? 1 : (o.ell_policy == SC_ELL_GLOBAL ? 2 : 1));
-
-    // events for the timed propagation launches (grow-only pool of pairs)
-    int64_t total_hops = 0;
-    if (time_kernels) {
-        for (int64_t sb = 0; sb < nsuper; ++sb) {
-            int32_t L = 0;
-            const int64_t first = sb * S;
-            const int nsrc = static_cast<int>(std::min<int64_t>(S, n - first));
-            for (int q = 0; q < nsrc; ++q) L = std::max(L, h_tau_src[order[first + q]]);
-            L += extra;
-            total_hops += std::max(L - 1, 0);
-        }
-        while (static_cast<int64_t>(g->hop_events.size()) < 2 * total_hops) {
-            cudaEvent_t e;
-            SC_CUDA(cudaEventCreate(&e));
-            g->hop_events.push_back(e);
-        }
-    }
-    int64_t hop_launches = 0;
+    R.launches = 2 + (o.ell_policy == SC_ELL_FIXED ? 0 : 1) + (learned ? 4 : 0);
+    if (plus) tgtplus_reserve(g, R.slices, R.B);
 
     // ---- propagation ----------------------------------------------------------
     SC_CUDA(cudaEventRecord(ev1, s));
-    int64_t hops = 0;
-    double alg_bytes = 0.0;
-    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
-                                       2.0 * static_cast<double>(slice_bytes);
-    int32_t ell_min_src = INT32_MAX, ell_max_src = 0;
-    for (int64_t sb = 0; sb < nsuper; ++sb) {
-        const int64_t first = sb * S;
-        const int nsrc = static_cast<int>(std::min<int64_t>(S, n - first));
-        const int used_slices = (nsrc + B - 1) / B;
-        int32_t L = 0;
-        for (int q = 0; q < nsrc; ++q) L = std::max(L, h_tau_src[order[first + q]]);
-        for (int q = 0; q < nsrc; ++q) {
-            ell_min_src = std::min(ell_min_src, h_tau_src[order[first + q]] + extra);
-            ell_max_src = std::max(ell_max_src, h_tau_src[order[first + q]] + extra);
-        }
-        L += extra;
-        if (L == 0) continue;
-        const int32_t *src = g->src_list.get() + first;
-        void *xa = g->xa.get(), *xb = g->xb.get();
-        SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * slice_bytes, s));
-        launch_first_or_gather(g, prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, s);
-        launches += 1;  // the memset is not a kernel of ours
-        for (int ell = 2; ell <= L; ++ell) {
-            // hop ell computes X_ell and, in its tail CTAs, gathers X_{ell-1}
-            HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
-                        g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get()};
-            if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches], s));
-            launch_hop(g, prec, B, vpl, h, s);
-            if (time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * hop_launches + 1], s));
-            ++hop_launches;
-            std::swap(xa, xb);
-            launches += 1;
-            alg_bytes += used_slices * hop_bytes_per_slice;
-        }
-        launch_first_or_gather(g, prec, B, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(),
-                               g->acc_t1.get(), g->acc_t2.get(), s);
-        launches += 1;
-        hops += L;
-    }
-    SC_CUDA(cudaEventRecord(ev2, s));
-    {
-        int32_t h_status = 0;
-        SC_CUDA(cudaMemcpyAsync(&h_status, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SC_CUDA(cudaStreamSynchronize(s));
-        if (h_status & 1) SC_FAIL(SC_ERR_TIMEOUT, "a bounded mbarrier wait expired in the TMA hop kernel");
-    }
+    std::vector<int32_t> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    run_blocks(R, all, len);
 
-    // ---- combine ----------------------------------------------------------------
+    // ---- combine, and for the learned lengths the check / extension loop ------
     DevBuf<double> tmp_s, tmp_b;
     double *d_s = s_hat;
     double *d_b = tail_bound;
     if (!out_dev) {
         tmp_s.reserve(nnz);
         d_s = tmp_s.get();
-        if (tail_bound) {
+        if (tail_bound || learned) {
             tmp_b.reserve(nnz);
             d_b = tmp_b.get();
         }
+    } else if (learned && !d_b) {
+        tmp_b.reserve(nnz);
+        d_b = tmp_b.get();
     }
-    if (!record_tail) d_b = nullptr;
-    const double lam_plus = g->lam.lambda_plus;
-    const double lam_star = g->lam.lambda_star;
-    // q / (2 (1 - lambda_plus)) for the end-corrected estimator, q / (1 - lambda_star^2) otherwise;
-    // lambda_plus carries its Ritz residual as a safety margin
+    const bool have_tail = record_after || learned;
+    if (!have_tail) d_b = nullptr;
+    // bound scales: after-records q = t_{tau+1} + t_{tau+2}: q / (2 (1 - lambda_plus)) (end-corrected) or
+    // q / (1 - lambda*^2); learned (records of hops tau-1, tau): lambda*^2 / (1 - lambda*^2) (t_{tau-1} + t_tau).
+    // lambda_plus carries its Ritz residual as a safety margin.
     double bound_scale = 0.0;
-    if (record_tail) {
-        const double lp = lam_plus + std::max(g->lam.residual_plus, 0.0);
+    if (learned) {
+        bound_scale = lam_star * lam_star / (1.0 - lam_star * lam_star);
+    } else if (record_after) {
+        const double lp = g->lam.lambda_plus + std::max(g->lam.residual_plus, 0.0);
         if (o.estimator == SC_EST_END_CORRECTED) bound_scale = lp < 1.0 ? 1.0 / (2.0 * (1.0 - lp)) : INFINITY;
         else bound_scale = lam_star < 1.0 ? 1.0 / (1.0 - lam_star * lam_star) : INFINITY;
     }
-    k_combine<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(),
-                                             g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), n,
-                                             o.estimator == SC_EST_END_CORRECTED, record_tail ? 1 : 0, bound_scale,
-                                             d_s, d_b);
-    SC_LAUNCH_CHECK();
+    auto combine = [&] {
+        k_combine<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(),
+                                                 g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), n,
+                                                 o.estimator == SC_EST_END_CORRECTED, have_tail ? 1 : 0, bound_scale,
+                                                 d_s, d_b);
+        SC_LAUNCH_CHECK();
+        R.launches += 1;
+    };
+    combine();
+    int64_t extended = 0;
+    int32_t rounds = 0;
+    if (learned) {
+        DevBuf<int32_t> row_flag, rows;
+        row_flag.reserve(n);
+        g->tp_counters.reserve(4);
+        std::vector<int32_t> h_flag(n);
+        while (true) {
+            SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, sizeof(long long), s));
+            k_extend_failing<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), d_b, n, o.eps, ell_global,
+                                                            g->tau_entry.get(), row_flag.get(),
+                                                            reinterpret_cast<unsigned long long *>(g->tp_counters.get()));
+            SC_LAUNCH_CHECK();
+            R.launches += 1;
+            long long failing = 0;
+            SC_CUDA(cudaMemcpyAsync(&failing, g->tp_counters.get(), sizeof(long long), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            if (failing == 0) break;
+            extended += failing / 2;
+            ++rounds;
+            // rerun the marked sources with their extended lengths
+            SC_CUDA(cudaMemcpyAsync(h_flag.data(), row_flag.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            k_row_max<<<ceil_div(n, 256), 256, 0, s>>>(g->row_ptr.get(), g->tau_entry.get(), n, tau_src.get());
+            SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            std::vector<int32_t> redo;
+            for (int32_t v = 0; v < n; ++v)
+                if (h_flag[v]) redo.push_back(v);
+            rows.reserve(redo.size());
+            SC_CUDA(cudaMemcpyAsync(rows.get(), redo.data(), redo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            k_reset_rows<<<ceil_div(static_cast<int64_t>(redo.size()), 8), 256, 0, s>>>(
+                g->row_ptr.get(), rows.get(), static_cast<int32_t>(redo.size()), g->tau_entry.get(), 1, g->acc_g.get(),
+                g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
+            SC_LAUNCH_CHECK();
+            R.launches += 2;
+            run_blocks(R, redo, len);
+            combine();
+        }
+    }
+    SC_CUDA(cudaEventRecord(ev2, s));
+
     g->scratch_d.reserve(kRedBlocks + 8);
     const double foster2 = device_reduce(d_s, nnz, false, g->scratch_d.get(), s);
     double max_bound = 0.0;
     if (d_b) max_bound = device_reduce(d_b, nnz, true, g->scratch_d.get(), s);
-    launches += 1 + 2 + (d_b ? 2 : 0);
+    R.launches += 2 + (d_b ? 2 : 0);
     if (!out_dev) {
         SC_CUDA(cudaMemcpyAsync(s_hat, d_s, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (tail_bound && d_b)
             SC_CUDA(cudaMemcpyAsync(tail_bound, d_b, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    } else if (tail_bound && d_b && d_b != tail_bound) {
+        SC_CUDA(cudaMemcpyAsync(tail_bound, d_b, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     SC_CUDA(cudaStreamSynchronize(s));
     float prop_ms = 0.f, total_ms = 0.f;
@@ -597,7 +839,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaEventElapsedTime(&total_ms, ev0, ev2));
     double hop_ms = 0.0;
     if (time_kernels) {
-        for (int64_t i = 0; i < hop_launches; ++i) {
+        for (int64_t i = 0; i < R.hop_launches; ++i) {
             float ms = 0.f;
             SC_CUDA(cudaEventElapsedTime(&ms, g->hop_events[2 * i], g->hop_events[2 * i + 1]));
             hop_ms += ms;
@@ -606,24 +848,99 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));
         rep->ell_global = ell_global;
-        rep->ell_min_source = ell_min_src == INT32_MAX ? 0 : ell_min_src;
-        rep->ell_max_source = ell_max_src;
-        rep->block_width = B;
-        rep->rows_split = vpl == 0 ? -1 : vpl;
-        rep->slices = slices;
+        rep->ell_min_source = R.ell_min_src == INT32_MAX ? 0 : R.ell_min_src;
+        rep->ell_max_source = R.ell_max_src;
+        rep->block_width = R.B;
+        rep->rows_split = R.vpl == 0 ? -1 : R.vpl;
+        rep->slices = R.slices;
         rep->blocks = nblocks_total;
-        rep->launches = launches;
-        rep->hops = hops;
-        rep->algorithmic_bytes = alg_bytes;
+        rep->launches = R.launches;
+        rep->hops = R.hops;
+        rep->source_hops = R.source_hops;
+        rep->algorithmic_bytes = R.alg_bytes;
         rep->foster_sum = 0.5 * foster2;
         rep->max_tail_bound = max_bound;
         rep->lambda_star = need_lambda ? lam_star : 0.0;
         rep->propagate_ms = prop_ms;
         rep->total_ms = total_ms;
         rep->hop_ms = hop_ms;
-        rep->hop_launches = hop_launches;
-        rep->hop_bytes = alg_bytes;
+        rep->hop_launches = R.hop_launches;
+        rep->hop_bytes = R.alg_bytes;
+        rep->walks = R.walks;
+        rep->edges_extended = static_cast<int32_t>(extended);
+        rep->extension_rounds = rounds;
+        rep->tt_min = plus ? (R.tt_min == INT32_MAX ? 0 : R.tt_min) : 0;
+        rep->tt_max = plus ? R.tt_max : 0;
+        rep->switch_tests = R.switch_tests;
+        rep->switch_ms = R.switch_ms;
+        rep->walk_ms = R.walk_ms;
     }
+}
+
+// certified per-entry lengths for training labels: all sources run the
+// a-priori length with every hop's half term recorded, then each edge takes
+// the least odd tau whose bound lambda*^2/(1-lambda*^2) (t_{tau-1} + t_tau)
+// is within eps (else the cap)
+__global__ void k_certify(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                          const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                          const double *__restrict__ rec, int stride, int32_t n, int32_t cap, double factor, double eps,
+                          int32_t *__restrict__ tau_out) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const double ir = inv_d[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t kr = rev[k];
+        const double ij = inv_d[col[k]];
+        auto full = [&](int l) {
+            return __dadd_rn(__dmul_rn(rec[static_cast<int64_t>(k) * stride + l], ir),
+                             __dmul_rn(rec[static_cast<int64_t>(kr) * stride + l], ij));
+        };
+        int32_t t = cap;
+        for (int32_t c = 1; c <= cap; c += 2) {
+            if (__dmul_rn(factor, __dadd_rn(full(c - 1), full(c))) <= eps) {
+                t = c;
+                break;
+            }
+        }
+        tau_out[k] = t;
+    }
+}
+
+void certified_lengths_impl(sc_graph *g, double eps, int precision, int32_t *per_entry_dev, int32_t *cap_out) {
+    cudaStream_t s = g->stream;
+    if (!g->has_lambda) {
+        sc_lambda lam;
+        sc_status st = estimate_lambda_impl(g, nullptr, &lam);
+        if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
+    }
+    const double lam = g->lam.lambda_star;
+    if (!(lam < 1.0)) SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1: no finite length");
+    int32_t cap = 0;
+    {
+        DevBuf<int32_t> te, ts;
+        te.reserve(g->nnz);
+        ts.reserve(g->n);
+        tau_entries_device(g, eps, lam, te.get(), ts.get(), &cap);
+    }
+    DevBuf<double> rec, sh;
+    const int stride = cap + 1;
+    rec.reserve(static_cast<size_t>(g->nnz) * stride);
+    sh.reserve(g->nnz);
+    sc_options o;
+    sc_options_default(&o);
+    o.eps = eps;
+    o.precision = precision;
+    o.ell_policy = SC_ELL_FIXED;
+    o.ell_fixed = cap;
+    o.flags = SC_OUT_DEVICE;
+    all_edges_impl(g, &o, sh.get(), nullptr, nullptr, rec.get(), stride);
+    k_certify<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(),
+                                                rec.get(), stride, g->n, cap, lam * lam / (1.0 - lam * lam), eps,
+                                                per_entry_dev);
+    SC_LAUNCH_CHECK();
+    SC_CUDA(cudaStreamSynchronize(s));
+    *cap_out = cap;
 }
 
 }  // namespace sc

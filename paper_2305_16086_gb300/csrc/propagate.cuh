@@ -76,6 +76,13 @@ __device__ __forceinline__ uint4 vpack(const float *a, __nv_bfloat16) {
 
 __device__ __forceinline__ uint4 ld_x(const uint4 *p) { return __ldg(p); }
 
+// What the gather records besides the half sums.
+struct GatherRec {
+    int mode;       // 0: t1, t2 = terms of hops tau+1, tau+2; 1: terms of hops tau-1, tau
+    double *all;    // nullable: all[k * stride + ell] = term of hop ell (every hop)
+    int stride;
+};
+
 // Arguments of one hop launch.
 template <typename T>
 struct HopArgs {
@@ -99,27 +106,37 @@ struct HopArgs {
     const int32_t *tau;
     int32_t gather_ell;
     double *g, *t1, *t2;
+    GatherRec rec;
 };
 
 // Alg. 2 lines 10-11 for hop `ell` and launch source q (slice q / B, column
 // q % B): for source i = s_b and each entry k = (i -> j) the unscaled half term
-// p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while ell <= tau[k]; the terms
-// of hops tau[k]+1 and tau[k]+2 are stored in t1, t2. (The 1/d(v_i) factor of
-// Eq. 9 is applied once in the combine.) One warp per source.
+// p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while ell <= tau[k]; t1, t2
+// keep the terms of hops tau+1, tau+2 (mode 0) or tau-1, tau (mode 1). (The
+// 1/d(v_i) factor of Eq. 9 is applied once in the combine.) One warp per source.
 template <typename T, int B>
 __device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                               const T *__restrict__ x, int32_t n, int32_t s, int32_t q,
                                               const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
-                                              double *__restrict__ t1, double *__restrict__ t2, int lane) {
+                                              double *__restrict__ t1, double *__restrict__ t2, int lane,
+                                              const GatherRec rec) {
     const T *xs = x + static_cast<int64_t>(q / B) * n * B + (q % B);
     const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s) * B]));
     for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
         const int32_t j = col[k];
         const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j) * B]));
         const int32_t tk = tau[k];
-        if (ell <= tk) g[k] += term;
-        else if (ell == tk + 1) t1[k] = term;
-        else if (ell == tk + 2) t2[k] = term;
+        if (ell <= tk) {
+            g[k] += term;
+            if (rec.mode == 1) {
+                if (ell == tk - 1) t1[k] = term;
+                else if (ell == tk) t2[k] = term;
+            }
+        } else if (rec.mode == 0) {
+            if (ell == tk + 1) t1[k] = term;
+            else if (ell == tk + 2) t2[k] = term;
+        }
+        if (rec.all) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
     }
 }
 
@@ -206,7 +223,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         if (q < a.nsrc) {
             const int32_t s = a.src[q];
             if (s >= 0)
-                gather_source<T, B>(row_ptr, col, a.x_prev, n, s, q, a.tau, a.gather_ell, a.g, a.t1, a.t2, lane);
+                gather_source<T, B>(row_ptr, col, a.x_prev, n, s, q, a.tau, a.gather_ell, a.g, a.t1, a.t2, lane, a.rec);
         }
         return;
     }
@@ -282,13 +299,13 @@ template <typename T, int B>
 __global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                          const T *__restrict__ x, int32_t n, const int32_t *__restrict__ src, int32_t nsrc,
                          const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
-                         double *__restrict__ t1, double *__restrict__ t2) {
+                         double *__restrict__ t1, double *__restrict__ t2, const GatherRec rec) {
     const int32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (q >= nsrc) return;
     const int32_t s = src[q];
     if (s < 0) return;
-    gather_source<T, B>(row_ptr, col, x, n, s, q, tau, ell, g, t1, t2, lane);
+    gather_source<T, B>(row_ptr, col, x, n, s, q, tau, ell, g, t1, t2, lane, rec);
 }
 
 // launch helper: one hop over `slices` slices, optionally gathering X_{l-1}

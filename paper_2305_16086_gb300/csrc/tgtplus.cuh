@@ -1,0 +1,433 @@
+// TGT+ (Algorithm 4) kernels: column statistics for CalChi (Alg. 3), the
+// per-entry range chi (Eq. 17 / Eq. 15) and walk count R (Eq. 13), the
+// switch rule (Eq. 14) and the random-walk tail (Eq. 11).
+//
+// Notation: X = p_tt(., s_b) for the sources s_b of a launch (the block after
+// tt hops), L = tau_k - tt the walk length of entry k = (i -> j).
+#pragma once
+
+#include "philox.cuh"
+#include "propagate.cuh"
+
+namespace sc {
+
+constexpr int kGammaMax = 16;        // largest supported candidate count (Alg. 3)
+constexpr int kChiScanThreads = 128;
+constexpr int kChiRowsPerCta = 256;
+constexpr uint32_t kWalkTag = 0x57414C4Bu;
+constexpr long long kWalkCountCap = 1ll << 40;
+
+// strict total order of (value, node): larger value first, then smaller id
+__device__ __forceinline__ bool better(double v, int32_t x, double w, int32_t y) {
+    return v > w || (v == w && x < y);
+}
+
+// insert (v, x) into the descending list (val, id) of length kGammaMax
+__device__ __forceinline__ void top_insert(double *val, int32_t *id, double v, int32_t x) {
+    if (!better(v, x, val[kGammaMax - 1], id[kGammaMax - 1])) return;
+#pragma unroll
+    for (int s = 0; s < kGammaMax; ++s) {
+        if (better(v, x, val[s], id[s])) {
+            const double tv = val[s];
+            const int32_t ti = id[s];
+            val[s] = v;
+            id[s] = x;
+            v = tv;
+            x = ti;
+        }
+    }
+}
+
+// a := the kGammaMax best of the two sorted (descending) lists a and b; list
+// element s of a sits at av[s * as] (strided, so that the lists of the threads
+// of a warp interleave across shared-memory banks)
+__device__ __forceinline__ void merge_sorted(double *av, int32_t *ai, int as, const double *bv, const int32_t *bi,
+                                             int bs) {
+    double ov[kGammaMax];
+    int32_t oi[kGammaMax];
+    int x = 0, y = 0;
+#pragma unroll
+    for (int s = 0; s < kGammaMax; ++s) {
+        const double xa = av[x * as], yb = bv[y * bs];
+        const int32_t ia = ai[x * as], ib = bi[y * bs];
+        const bool ta = better(xa, ia, yb, ib);
+        ov[s] = ta ? xa : yb;
+        oi[s] = ta ? ia : ib;
+        x += ta ? 1 : 0;
+        y += ta ? 0 : 1;
+    }
+#pragma unroll
+    for (int s = 0; s < kGammaMax; ++s) {
+        av[s * as] = ov[s];
+        ai[s * as] = oi[s];
+    }
+}
+
+// Per CTA and column: the kGammaMax largest (value, node), min, max and the
+// frontier volume sum_{x: X[x,b] != 0} d_x over kChiRowsPerCta rows.
+// partial layout: [slice][cta][B] entries, lists of kGammaMax.
+template <typename T, int B>
+__global__ void __launch_bounds__(kChiScanThreads)
+    k_chi_scan(const int32_t *__restrict__ row_ptr, const T *__restrict__ x, int32_t n, double *__restrict__ pval,
+               int32_t *__restrict__ pid, double *__restrict__ pmin, double *__restrict__ pmax,
+               long long *__restrict__ pvol) {
+    constexpr int TPC = kChiScanThreads / B;  // threads per column
+    constexpr int BATCH = 8;                 // rows in flight per thread
+    const int c = threadIdx.x % B, sub = threadIdx.x / B;
+    const int32_t r0 = blockIdx.x * kChiRowsPerCta;
+    const int32_t r1 = min(n, r0 + kChiRowsPerCta);
+    const T *xs = x + static_cast<int64_t>(blockIdx.y) * n * B;
+    constexpr int NT = kChiScanThreads;  // list element s of thread t at [s * NT + t]
+    __shared__ double sv[kGammaMax * NT];
+    __shared__ int32_t si[kGammaMax * NT];
+    __shared__ double smin[NT], smax[NT];
+    __shared__ long long svol[NT];
+    double *val = sv + threadIdx.x;
+    int32_t *id = si + threadIdx.x;
+    for (int s = 0; s < kGammaMax; ++s) {
+        val[s * NT] = -INFINITY;
+        id[s * NT] = INT32_MAX;
+    }
+    double vmin = INFINITY, vmax = -INFINITY;
+    long long vol = 0;
+    for (int32_t rb = r0 + sub; rb < r1; rb += TPC * BATCH) {
+        double v[BATCH];
+        int32_t d[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int32_t r = rb + u * TPC;
+            v[u] = r < r1 ? static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B + c])) : -INFINITY;
+            d[u] = r < r1 ? row_ptr[r + 1] - row_ptr[r] : 0;
+        }
+#pragma unroll 1
+        for (int u = 0; u < BATCH; ++u) {
+            const int32_t r = rb + u * TPC;
+            if (r < r1) {
+                vmin = fmin(vmin, v[u]);
+                vmax = fmax(vmax, v[u]);
+                if (v[u] != 0.0) vol += d[u];
+                // rows arrive in increasing order: a tie never beats the last slot
+                if (v[u] > val[(kGammaMax - 1) * NT]) {
+                    double cv = v[u];
+                    int32_t ci = r;
+#pragma unroll 1
+                    for (int s = 0; s < kGammaMax; ++s) {
+                        if (better(cv, ci, val[s * NT], id[s * NT])) {
+                            const double tv = val[s * NT];
+                            const int32_t ti = id[s * NT];
+                            val[s * NT] = cv;
+                            id[s * NT] = ci;
+                            cv = tv;
+                            ci = ti;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    smin[threadIdx.x] = vmin;
+    smax[threadIdx.x] = vmax;
+    svol[threadIdx.x] = vol;
+    __syncthreads();
+    for (int half = TPC / 2; half > 0; half >>= 1) {  // tree of sorted merges over the column's threads
+        if (sub < half) {
+            const int o = threadIdx.x + half * B;
+            merge_sorted(val, id, NT, sv + o, si + o, NT);
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[o]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[o]);
+            svol[threadIdx.x] += svol[o];
+        }
+        __syncthreads();
+    }
+    if (sub == 0) {
+        const int64_t base = (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * B + c;
+        for (int s = 0; s < kGammaMax; ++s) {
+            pval[base * kGammaMax + s] = val[s * NT];
+            pid[base * kGammaMax + s] = id[s * NT];
+        }
+        pmin[base] = smin[threadIdx.x];
+        pmax[base] = smax[threadIdx.x];
+        pvol[base] = svol[threadIdx.x];
+    }
+}
+
+// One CTA per column (slice * B + b): threads merge strided CTA partials, then
+// a tree of sorted merges in shared memory. The order is total, so the result
+// does not depend on the merge order.
+template <int B>
+__global__ void __launch_bounds__(kChiScanThreads)
+    k_chi_merge(int nct, int ncols, const double *__restrict__ pval, const int32_t *__restrict__ pid,
+                const double *__restrict__ pmin, const double *__restrict__ pmax,
+                const long long *__restrict__ pvol, double *__restrict__ cval, int32_t *__restrict__ cid,
+                double *__restrict__ cmin, double *__restrict__ cmax, long long *__restrict__ cvol) {
+    const int q = blockIdx.x;
+    if (q >= ncols) return;
+    const int slice = q / B, c = q % B, t = threadIdx.x;
+    constexpr int NT = kChiScanThreads;
+    __shared__ double sv[kGammaMax * NT];
+    __shared__ int32_t si[kGammaMax * NT];
+    __shared__ double smin[NT], smax[NT];
+    __shared__ long long svol[NT];
+    double *val = sv + t;
+    int32_t *id = si + t;
+    for (int s = 0; s < kGammaMax; ++s) {
+        val[s * NT] = -INFINITY;
+        id[s * NT] = INT32_MAX;
+    }
+    double vmin = INFINITY, vmax = -INFINITY;
+    long long vol = 0;
+    double bv[kGammaMax];
+    int32_t bi[kGammaMax];
+    for (int p = t; p < nct; p += kChiScanThreads) {
+        const int64_t base = (static_cast<int64_t>(slice) * nct + p) * B + c;
+#pragma unroll
+        for (int s = 0; s < kGammaMax; ++s) {
+            bv[s] = pval[base * kGammaMax + s];
+            bi[s] = pid[base * kGammaMax + s];
+        }
+        merge_sorted(val, id, NT, bv, bi, 1);
+        vmin = fmin(vmin, pmin[base]);
+        vmax = fmax(vmax, pmax[base]);
+        vol += pvol[base];
+    }
+    smin[t] = vmin;
+    smax[t] = vmax;
+    svol[t] = vol;
+    __syncthreads();
+    for (int half = kChiScanThreads / 2; half > 0; half >>= 1) {
+        if (t < half) {
+            merge_sorted(val, id, NT, sv + t + half, si + t + half, NT);
+            smin[t] = fmin(smin[t], smin[t + half]);
+            smax[t] = fmax(smax[t], smax[t + half]);
+            svol[t] += svol[t + half];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int s = 0; s < kGammaMax; ++s) {
+            cval[static_cast<int64_t>(q) * kGammaMax + s] = val[s * NT];
+            cid[static_cast<int64_t>(q) * kGammaMax + s] = id[s * NT];
+        }
+        cmin[q] = smin[0];
+        cmax[q] = smax[0];
+        cvol[q] = svol[0];
+    }
+}
+
+__device__ __forceinline__ bool has_edge(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                         int32_t a, int32_t b) {
+    int32_t lo = row_ptr[a], hi = row_ptr[a + 1];
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        const int32_t c = col[mid];
+        if (c == b) return true;
+        if (c < b) lo = mid + 1;
+        else hi = mid;
+    }
+    return false;
+}
+
+struct ChiArgs {
+    const int32_t *row_ptr, *col, *src, *tau;
+    int32_t n, nsrc, ell, gamma;
+    const double *cval, *cmin, *cmax;
+    const int32_t *cid;
+    double eps, log_2m_delta;
+    long long *walk_count;   // per CSR entry (0 = no walks)
+    long long *rhs;          // [0] sum of the launch's walk counts (Eq. 14 right side), [2] walk steps
+};
+
+// One CTA per source: warp 0 finds rho_hat (Alg. 3) and min / max of p over
+// N(i); then one warp per entry k = (i -> j), its lanes striding over N(j),
+// gives chi (Eq. 17, or Eq. 15 for gamma = 0) and R (Eq. 13) for the walk
+// length L = tau_k - ell. The floating-point expressions follow the oracle's
+// evaluation order (no FMA contraction).
+template <typename T, int B>
+__global__ void k_chi_entries(const T *__restrict__ x, const ChiArgs a) {
+    const int32_t q = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (q >= a.nsrc) return;
+    const int32_t s = a.src[q];
+    if (s < 0) return;
+    const T *xs = x + static_cast<int64_t>(q / B) * a.n * B + (q % B);
+    auto px = [&](int32_t v) { return static_cast<double>(to_acc(xs[static_cast<int64_t>(v) * B])); };
+    const double *cv = a.cval + static_cast<int64_t>(q) * kGammaMax;
+    const int32_t *ci = a.cid + static_cast<int64_t>(q) * kGammaMax;
+    const double vmin = a.cmin[q], vmax = a.cmax[q];
+    const int g = a.gamma;
+    const int32_t rb = a.row_ptr[s], re = a.row_ptr[s + 1];
+    __shared__ double sh_rho, sh_nmin, sh_nmax;
+    __shared__ unsigned long long sh_cnt[2];
+    if (warp == 0) {
+        // rho_hat = max(max over edges inside C of p(c_a) + p(c_b), p(c_1) + p(c_gamma))
+        double best = -INFINITY;
+        if (g > 0) {
+            for (int t = lane; t < g * g; t += 32) {
+                const int u = t / g, v = t % g;
+                if (u < v && has_edge(a.row_ptr, a.col, ci[u], ci[v])) best = fmax(best, __dadd_rn(cv[u], cv[v]));
+            }
+        }
+        double nmin = INFINITY, nmax = -INFINITY;
+        for (int32_t k = rb + lane; k < re; k += 32) {
+            const double v = px(a.col[k]);
+            nmin = fmin(nmin, v);
+            nmax = fmax(nmax, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+            nmin = fmin(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
+            nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        }
+        if (lane == 0) {
+            sh_rho = g > 0 ? fmax(best, __dadd_rn(cv[0], cv[g - 1])) : 0.0;
+            sh_nmin = nmin;
+            sh_nmax = nmax;
+            sh_cnt[0] = 0;
+            sh_cnt[1] = 0;
+        }
+    }
+    __syncthreads();
+    const double rho = sh_rho, nmin_i = sh_nmin, nmax_i = sh_nmax;
+    const double d_i = static_cast<double>(re - rb);
+    const double denom = __dmul_rn(__dmul_rn(__dmul_rn(d_i, d_i), a.eps), a.eps);
+    unsigned long long local = 0, steps = 0;
+    for (int32_t k = rb + warp; k < re; k += nw) {
+        const int32_t L = a.tau[k] - a.ell;
+        if (L <= 0) {
+            if (lane == 0) a.walk_count[k] = 0;
+            continue;
+        }
+        const int32_t j = a.col[k];
+        double chi;
+        if (g == 0) {
+            chi = __dmul_rn(__dmul_rn(2.0, static_cast<double>(L)), __dsub_rn(vmax, vmin));  // Eq. 15
+        } else {
+            double nmin_j = INFINITY, nmax_j = -INFINITY;
+            for (int32_t e = a.row_ptr[j] + lane; e < a.row_ptr[j + 1]; e += 32) {
+                const double v = px(a.col[e]);
+                nmin_j = fmin(nmin_j, v);
+                nmax_j = fmax(nmax_j, v);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                nmin_j = fmin(nmin_j, __shfl_xor_sync(0xffffffffu, nmin_j, o));
+                nmax_j = fmax(nmax_j, __shfl_xor_sync(0xffffffffu, nmax_j, o));
+            }
+            const double Lm1 = static_cast<double>(L - 1);
+            const double lb_i = __dadd_rn(nmin_i, __dmul_rn(Lm1, vmin));
+            const double lb_j = __dadd_rn(nmin_j, __dmul_rn(Lm1, vmin));
+            const double tail = __ddiv_rn(__dmul_rn(Lm1, rho), 2.0);
+            const double ub_i = __dadd_rn(__dadd_rn(__ddiv_rn(nmax_i, 2.0), __ddiv_rn(vmax, 2.0)), tail);
+            const double ub_j = __dadd_rn(__dadd_rn(__ddiv_rn(nmax_j, 2.0), __ddiv_rn(vmax, 2.0)), tail);
+            chi = __dsub_rn(__dsub_rn(__dadd_rn(ub_i, ub_j), lb_i), lb_j);  // Eq. 17
+        }
+        const double r = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(8.0, chi), chi), a.log_2m_delta), denom);
+        const double rc = ceil(r);
+        const long long R =
+            rc < 1.0 ? 1 : (rc > static_cast<double>(kWalkCountCap) ? kWalkCountCap : static_cast<long long>(rc));
+        if (lane == 0) {
+            a.walk_count[k] = R;
+            local += static_cast<unsigned long long>(R);
+            steps += static_cast<unsigned long long>(R) * 2ull * static_cast<unsigned long long>(L);
+        }
+    }
+    if (lane == 0 && local) {
+        atomicAdd(&sh_cnt[0], local);
+        atomicAdd(&sh_cnt[1], steps);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sh_cnt[0]) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.rhs), sh_cnt[0]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.rhs + 2), sh_cnt[1]);
+    }
+}
+
+struct WalkArgs {
+    const int32_t *row_ptr, *col, *src, *tau;
+    int32_t n, nsrc, tt;
+    const long long *walk_count;
+    double *g;             // unscaled half sums; the walk mean of X d_i is added
+    uint32_t key0, key1;
+};
+
+// sum_{t=1..L} X[W[t]] for walk w of entry k on one side (Eq. 11)
+template <typename T, int B>
+__device__ __forceinline__ double walk_sum(const WalkArgs &a, const T *__restrict__ xs, int32_t start, int32_t L,
+                                           uint32_t k, uint32_t w, uint32_t side) {
+    int32_t cur = start;
+    double sum = 0.0;
+    Philox4 words{};
+    for (int32_t t = 1; t <= L; ++t) {
+        const int r = (t - 1) & 3;
+        if (r == 0)
+            words = philox4x32_10(k, w, (side << 31) | static_cast<uint32_t>((t - 1) >> 2), kWalkTag, a.key0, a.key1);
+        const int32_t b = a.row_ptr[cur];
+        const uint32_t d = static_cast<uint32_t>(a.row_ptr[cur + 1] - b);
+        const uint32_t idx = static_cast<uint32_t>((static_cast<uint64_t>(words.v[r]) * d) >> 32);
+        cur = a.col[b + idx];
+        sum += static_cast<double>(to_acc(xs[static_cast<int64_t>(cur) * B]));
+    }
+    return sum;
+}
+
+constexpr int kWalkChunk = 128;  // walk pairs per warp-sized chunk
+
+struct WalkChunkArgs {
+    const int32_t *entry_q;     // per planned entry: launch source index q
+    const int32_t *entry_k;     // per planned entry: CSR entry k
+    const int32_t *chunk_entry; // per chunk: planned entry index
+    const long long *chunk_w0;  // per chunk: first walk index
+    int32_t nchunks;
+    double *chunk_sum;          // per chunk: sum over its walks of (S_i - S_j)
+};
+
+// One warp per chunk of walk pairs of one entry; lanes take walks w0 + lane,
+// w0 + lane + 32, ... in the chunk; the chunk sum is reduced by a fixed tree.
+template <typename T, int B>
+__global__ void k_walk_chunks(const T *__restrict__ x, const WalkArgs a, const WalkChunkArgs c) {
+    const int32_t ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (ch >= c.nchunks) return;
+    const int32_t e = c.chunk_entry[ch];
+    const int32_t q = c.entry_q[e], k = c.entry_k[e];
+    const int32_t s = a.src[q];
+    const T *xs = x + static_cast<int64_t>(q / B) * a.n * B + (q % B);
+    const long long R = a.walk_count[k];
+    const long long w0 = c.chunk_w0[ch];
+    const long long w1 = min(R, w0 + kWalkChunk);
+    const int32_t L = a.tau[k] - a.tt;
+    const int32_t j = a.col[k];
+    double acc = 0.0;
+    for (long long w = w0 + lane; w < w1; w += 32) {
+        const double si = walk_sum<T, B>(a, xs, s, L, static_cast<uint32_t>(k), static_cast<uint32_t>(w), 0u);
+        const double sj = walk_sum<T, B>(a, xs, j, L, static_cast<uint32_t>(k), static_cast<uint32_t>(w), 1u);
+        acc += si - sj;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c.chunk_sum[ch] = acc;
+}
+
+// g[k] += (sum of the entry's chunk sums, in chunk order) / R_k  (Alg. 4 line 17)
+static __global__ void k_walk_finish(const int32_t *__restrict__ entry_k, const int32_t *__restrict__ entry_chunk0,
+                              int32_t nentries, const double *__restrict__ chunk_sum,
+                              const long long *__restrict__ walk_count, double *__restrict__ g) {
+    const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nentries) return;
+    const int32_t k = entry_k[e];
+    const long long R = walk_count[k];
+    if (R <= 0) return;
+    double t = 0.0;
+    for (int32_t ch = entry_chunk0[e]; ch < entry_chunk0[e + 1]; ++ch) t += chunk_sum[ch];
+    g[k] += t / static_cast<double>(R);
+}
+
+// packs the walk counts of the planned entries
+static __global__ void k_pack_counts(const int32_t *__restrict__ entry_k, int32_t nentries,
+                              const long long *__restrict__ walk_count, long long *__restrict__ out) {
+    const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nentries) out[e] = walk_count[entry_k[e]];
+}
+
+}  // namespace sc
