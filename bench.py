@@ -3,11 +3,15 @@
 
 Workload (default): Barabasi-Albert graph, n = 200,000, 10 edges per new node
 (m = 1,999,900), seed 1; FP32 probability blocks with FP64 edge accumulation;
-eps = 1e-3; truncation length from Eq. (6) with the Lanczos eigenvalue bound.
+eps = 1e-3; per-source lengths from the MLP (trained beforehand on another
+Barabasi-Albert graph, n = 50,000, seed 101), every edge certified by the
+a-posteriori bound and extended when it fails, capped by the length of Eq. (6).
 
 A step is one full sc_all_edges call: every edge's s_hat, all sources. The
-eigenvalue bound is preprocessing (computed once per graph, outside the timed
-region, as the paper separates preprocessing from the run).
+eigenvalue bound, the features and the model are preprocessing (computed once
+per graph or graph family, outside the timed region, as the paper separates
+preprocessing from the run). The plain global-length arms (FP32 and FP64) are
+timed beside it for comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -31,7 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "AESC edges/sec at eps=1e-3 (learned-l FP32 batched vs plain global-l); HBM GB/s"
+METRIC = "AESC edges/sec at \u03b5=1e-3 (learned-\u2113 FP32 batched vs plain global-\u2113); HBM GB/s"
 UNIT = "edges/s"
 WORKLOADS = {
     "ba_200k": dict(desc="Barabasi-Albert n=200000, 10 edges per new node (m=1,999,900), seed 1",
@@ -153,6 +157,20 @@ def cpu_baseline(g, ell: int, target_s: float = 10.0):
                       f"full-job rate = m / (n * seconds per source)", "seconds": round(elapsed, 2)}
 
 
+def train_model(eps, stream):
+    """The MLP for the learned length, trained on the GPU on a separate graph of
+    the same family (untimed preprocessing)."""
+    import graphgen as gg
+    from paper_2305_16086_gb300 import Graph, binding
+
+    tg = gg.barabasi_albert(50_000, 10, 101)
+    with Graph(tg.row_ptr, tg.col_idx, stream=stream) as Gt:
+        Gt.estimate_lambda(allow_unconverged=True)
+        init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
+        model, _ = binding.mlp_train([Gt], init, epochs=400, lr=1e-2, eps=eps, precision="fp32")
+    return model
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -197,7 +215,8 @@ def main():
     ap.add_argument("--workload", default="ba_200k", choices=sorted(WORKLOADS))
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--policy", default="global", choices=["global", "per_edge"])
+    ap.add_argument("--policy", default="learned", choices=["learned", "global", "per_edge"])
+    ap.add_argument("--no-arms", action="store_true")
     ap.add_argument("--block-width", type=int, default=0)
     ap.add_argument("--rows-split", type=int, default=0)
     ap.add_argument("--heavy-threshold", type=int, default=0)
@@ -216,7 +235,7 @@ def main():
     import torch
 
     import graphgen as gg
-    from paper_2305_16086_gb300 import Graph
+    from paper_2305_16086_gb300 import Graph, binding
 
     torch.cuda.set_device(local)
     pg = None
@@ -232,6 +251,10 @@ def main():
 
     G = Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), stream=stream)
     lam = G.estimate_lambda(allow_unconverged=True)
+    model = None
+    if args.policy == "learned":
+        model = train_model(args.eps, stream)
+        binding.mlp_load(G, model)
     out = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2: evict between steps
 
@@ -250,9 +273,11 @@ def main():
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("timed_step")
             e0.record(stream)
             _, _, rep = G.all_edges(out=out, time_kernels=True, **run_kw)
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             reports.append(rep)
@@ -292,6 +317,8 @@ def main():
             t0 = time.perf_counter()
             with Graph(rp_h, ci_h, stream=stream) as Gh:
                 Gh.estimate_lambda(allow_unconverged=True)
+                if model is not None:
+                    binding.mlp_load(Gh, model)
                 Gh.all_edges(out=out_h, **run_kw)
             torch.cuda.synchronize()
             if i >= 2:
@@ -303,7 +330,25 @@ def main():
             e2e_step = float(t.item())
         e2e = {"value": world * g.m / (e2e_step / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz), "d2h_bytes_per_step": int(8 * g.nnz),
-               "ms_per_step": e2e_step, "includes": "graph create + validation + Lanczos + all edges + D2H"}
+               "ms_per_step": e2e_step,
+               "includes": "graph create + validation + Lanczos + model load + features + all edges + D2H"}
+
+    # comparison arms: the plain global length in FP32 and FP64 (one warm-up, one timed step each)
+    arms = {}
+    if not args.no_arms:
+        for name, prec in (("global_fp32", "fp32"), ("global_fp64", "fp64")):
+            kw = dict(run_kw, policy="global", precision=prec)
+            G.all_edges(out=out, **kw)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, r = G.all_edges(out=out, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            arms[name] = {"value": world * g.m / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                          "ms_per_step": e0.elapsed_time(e1), "source_hops": r["source_hops"],
+                          "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m}
 
     if rank != 0:
         return
@@ -317,11 +362,17 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "m": g.m, "eps": args.eps,
                    "policy": args.policy, "precision": f"{args.precision} blocks, fp64 accumulation",
+                   "batching": f"{rep0['slices']} block(s) of {rep0['block_width']} sources per launch, "
+                               f"{rep0['blocks']} blocks",
                    "ell_global": rep0["ell_global"], "lambda_star": lam["lambda_star"],
                    "block_width": rep0["block_width"], "rows_split": rep0["rows_split"],
                    "slices": rep0["slices"], "l2": "working set > L2 and a 512 MB write between steps",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "arms": arms,
+        "learned": {"source_hops": rep0["source_hops"], "extension_rounds": rep0["extension_rounds"],
+                    "edges_extended": rep0["edges_extended"], "max_tail_bound": rep0["max_tail_bound"],
+                    "model": "trained on Barabasi-Albert n=50000 m0=10 seed 101, 400 Adam steps"}
+        if args.policy == "learned" else None,
         "clocks": clk.summary(), "gpu_launches": int(sum(r["launches"] for r in reports)),
         "foster_mean_abs_error": ((g.n - 1) - rep0["foster_sum"]) / g.m,
     }

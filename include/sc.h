@@ -180,6 +180,14 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
 #define SC_OUT_DEVICE 1u        /* s_hat (and aux outputs) are device pointers (else host) */
 #define SC_OPT_RECORD_TAIL 2u   /* run 2 extra hops per source and report the tail bound */
 #define SC_OPT_TIME_KERNELS 4u  /* bracket every propagation launch with CUDA events (report.hop_ms) */
+/* Windowed blocks: Algorithm 2 visits only nodes with p_{l-1} > 0; a block of
+   consecutive sources on a graph of bandwidth beta = max |i - j| reaches at
+   hop l only rows within l * beta of its sources, so each block stores and
+   computes that interval alone. Chosen automatically when a block's last
+   window is under half the graph (grid-like numbering); the values are the
+   same either way. Not with TGT+ or the TMA-gather kernel. */
+#define SC_OPT_WINDOWS_OFF 8u
+#define SC_OPT_WINDOWS_FORCE 16u
 
 typedef struct sc_options {
     double eps;               /* absolute error target of Definition 2.2, 0 < eps < 1 */

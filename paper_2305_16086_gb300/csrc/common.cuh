@@ -143,6 +143,13 @@ struct sc_graph {
     sc::DevBuf<int32_t> row_order;
     int32_t heavy_threshold_cached = -1;
     int32_t n_heavy = 0;
+    // the heavy rows again, sorted by id (windowed launches), and on the host
+    sc::DevBuf<int32_t> heavy_ids;
+    std::vector<int32_t> h_heavy_ids;
+    // bandwidth max |i - j| over the entries (i -> j); -1 until computed
+    int32_t bandwidth = -1;
+    // per-slice windows of windowed launches
+    sc::DevBuf<unsigned char> win_list;
     // row runs of about equal CSR entries, one per warp, for the TMA kernel
     sc::DevBuf<int32_t> part;
     int32_t nparts = 0;
@@ -180,6 +187,7 @@ struct sc_graph {
 
 namespace sc {
 void ensure_row_order(sc_graph *g, int32_t heavy_threshold);
+int32_t ensure_bandwidth(sc_graph *g);
 void ensure_partition(sc_graph *g, int32_t target);
 void fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s);
 }

@@ -159,7 +159,41 @@ void ensure_row_order(sc_graph *g, int32_t heavy_threshold) {
                             g->stream));
     SC_CUDA(cudaStreamSynchronize(g->stream));
     g->n_heavy = static_cast<int32_t>(heavy.size());
+    g->h_heavy_ids = heavy;
+    std::sort(g->h_heavy_ids.begin(), g->h_heavy_ids.end());
+    g->heavy_ids.reserve(std::max<size_t>(heavy.size(), 1));
+    if (!heavy.empty())
+        SC_CUDA(cudaMemcpyAsync(g->heavy_ids.get(), g->h_heavy_ids.data(), heavy.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, g->stream));
+    SC_CUDA(cudaStreamSynchronize(g->stream));
     g->heavy_threshold_cached = heavy_threshold;
+}
+
+// largest |i - j| over the rows' entries: one warp per row, maximum by atomics
+__global__ void k_bandwidth(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                            int32_t *out) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int32_t m = 0;
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) m = max(m, abs(col[k] - r));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0) atomicMax(out, m);
+}
+
+int32_t ensure_bandwidth(sc_graph *g) {
+    if (g->bandwidth >= 0) return g->bandwidth;
+    DevBuf<int32_t> d;
+    d.reserve(1);
+    SC_CUDA(cudaMemsetAsync(d.get(), 0, sizeof(int32_t), g->stream));
+    k_bandwidth<<<ceil_div(g->n, 8), 256, 0, g->stream>>>(g->row_ptr.get(), g->col_idx.get(), g->n, d.get());
+    SC_LAUNCH_CHECK();
+    int32_t h = 0;
+    SC_CUDA(cudaMemcpyAsync(&h, d.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+    g->bandwidth = h;
+    return h;
 }
 
 void ensure_partition(sc_graph *g, int32_t target) {

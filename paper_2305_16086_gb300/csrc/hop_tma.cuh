@@ -49,7 +49,7 @@ struct TmaHopArgs {
     const int32_t *part;   // warp w owns rows [part[w], part[w+1])
     int32_t nparts;
     int32_t part_ctas;
-    // fused gather of X_{l-1} (tail CTAs), as in HopArgs
+    int32_t gather_ctas;   // fused gather of X_{l-1} (first CTAs, one per source), as in HopArgs
     const void *x_prev;
     const int32_t *src;
     int32_t nsrc;
@@ -174,17 +174,20 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_hop_tma(const __grid_constan
     const int32_t cta = static_cast<int32_t>(blockIdx.x);
     const int32_t n = a.n;
 
-    if (cta >= a.part_ctas) {  // fused gather of X_{l-1}
-        const int32_t q = static_cast<int32_t>(blockIdx.y) * B + (cta - a.part_ctas) * kTmaWarps + warp;
+    if (cta < a.gather_ctas) {  // fused gather of X_{l-1}, one CTA per source, first in the grid
+        const int32_t q = static_cast<int32_t>(blockIdx.y) * B + cta;
         if (q < a.nsrc) {
             const int32_t s = a.src[q];
-            if (s >= 0)
-                gather_source<T, B>(a.row_ptr, a.col, static_cast<const T *>(a.x_prev), n, s, q, a.tau, a.gather_ell,
-                                    a.g, a.t1, a.t2, lane, a.rec);
+            if (s >= 0) {
+                int32_t sb;
+                const T *xs = slice_column<T, B>(static_cast<const T *>(a.x_prev), n, nullptr, q, &sb);
+                gather_source<T, B>(a.row_ptr, a.col, xs, sb, s, a.tau, a.gather_ell, a.g, a.t1, a.t2, threadIdx.x,
+                                    kTmaWarps * 32, a.rec);
+            }
         }
         return;
     }
-    const int32_t w = cta * kTmaWarps + warp;
+    const int32_t w = (cta - a.gather_ctas) * kTmaWarps + warp;
     if (w >= a.nparts) return;
     if (*reinterpret_cast<volatile int32_t *>(a.status) != 0) return;  // an earlier wait expired: stop early
 

@@ -192,7 +192,7 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
         const int32_t *bsrc = src + first;
         double *a = xa, *b = xb;
         SC_CUDA(cudaMemsetAsync(a, 0, 8 * static_cast<size_t>(B) * n, s));
-        k_first_hop<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, inv_deg, bsrc, nb, a, n);
+        k_first_hop<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, inv_deg, bsrc, nb, a, n, nullptr);
         for (int hop = 2; hop <= ell; ++hop) {
             // natural row order, every row on the light path (no schedule array
             // without allocation); the tail CTAs gather X_{hop-1}. hop - 1 <= ell
@@ -217,8 +217,8 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
             launch_spmm_hop<double, B, 1>(ha, 1, s);
             std::swap(a, b);
         }
-        k_gather<double, B><<<ceil_div(nb, 8), 256, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,
-                                                            nullptr, GatherRec{0, nullptr, 0});
+        k_gather<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,
+                                                            nullptr, GatherRec{0, nullptr, 0}, nullptr);
         SC_LAUNCH_CHECK();
     }
     k_na_combine<<<ceil_div(n, 8), 256, 0, s>>>(row_ptr, col_idx, rev, inv_deg, acc, n, s_hat);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -137,6 +138,11 @@ struct HopLaunch {
     double *g, *t1, *t2;
     int32_t *status;  // TMA kernel: bounded-wait expiry flag
     GatherRec rec;
+    // windowed launch: per slice windows, the hop computed, the bandwidth and
+    // the largest heavy + light CTA count over the slices
+    const SliceWin *win = nullptr;
+    int32_t ell = 0, beta = 0;
+    int win_ctas = 0;
 };
 
 // ---- TMA-gather variant (lane split value 0) --------------------------------
@@ -203,8 +209,9 @@ static void hop_tma_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.t2 = h.t2;
     a.rec = h.rec;
     a.status = h.status;
-    const int gather_ctas = h.gather_ell > 0 ? ceil_div(B, kTmaWarps) : 0;
-    dim3 grid(a.part_ctas + gather_ctas, h.slices);
+    if (h.win) SC_FAIL(SC_ERR_UNSUPPORTED, "the TMA-gather hop has no windowed form");
+    a.gather_ctas = h.gather_ell > 0 ? B : 0;
+    dim3 grid(a.gather_ctas + a.part_ctas, h.slices);
     k_hop_tma<T, B><<<grid, kTmaWarps * 32, TL::SMEM, s>>>(m, a);
 }
 
@@ -227,7 +234,12 @@ static void hop_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.t1 = h.t1;
     a.t2 = h.t2;
     a.rec = h.rec;
-    launch_spmm_hop<T, B, VPL>(a, h.slices, s);
+    a.win = h.win;
+    a.ell = h.ell;
+    a.beta = h.beta;
+    a.heavy_ids = g->heavy_ids.get();
+    a.heavy_t = g->heavy_threshold_cached;
+    launch_spmm_hop<T, B, VPL>(a, h.slices, s, h.win_ctas);
 }
 
 // lane split 0 = the TMA-gather kernel; 1, 2, 4 = 16-byte vectors per lane of the SIMT kernel
@@ -287,38 +299,43 @@ void launch_hop(const sc_graph *g, int prec, int B, int vpl, const HopLaunch &h,
 template <typename T, int B>
 static void first_gather_t(const sc_graph *g, bool first, const void *x, const int32_t *src, int nsrc,
                            const int32_t *tau, int ell, double *acc_g, double *acc_t1, double *acc_t2,
-                           const GatherRec &rec, cudaStream_t s) {
-    const int warps = 8;
-    const int blocks = ceil_div(nsrc, warps);
+                           const GatherRec &rec, const SliceWin *win, cudaStream_t s) {
+    if (nsrc <= 0) return;
     if (first)
-        k_first_hop<T, B><<<blocks, warps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g), src,
-                                                         nsrc, static_cast<T *>(const_cast<void *>(x)), g->n);
+        k_first_hop<T, B><<<nsrc, 128, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g), src, nsrc,
+                                               static_cast<T *>(const_cast<void *>(x)), g->n, win);
     else
-        k_gather<T, B><<<blocks, warps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), static_cast<const T *>(x),
-                                                      g->n, src, nsrc, tau, ell, acc_g, acc_t1, acc_t2, rec);
+        k_gather<T, B><<<nsrc, 128, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), static_cast<const T *>(x), g->n, src,
+                                            nsrc, tau, ell, acc_g, acc_t1, acc_t2, rec, win);
 }
 
 template <typename T>
 static void first_gather_p(const sc_graph *g, int B, bool first, const void *x, const int32_t *src, int nsrc,
                            const int32_t *tau, int ell, double *a, double *b, double *c, const GatherRec &rec,
-                           cudaStream_t s) {
+                           const SliceWin *win, cudaStream_t s) {
     switch (B) {
-    case 32: first_gather_t<T, 32>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
-    case 64: first_gather_t<T, 64>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
-    case 128: first_gather_t<T, 128>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, s); break;
+    case 32: first_gather_t<T, 32>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, win, s); break;
+    case 64: first_gather_t<T, 64>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, win, s); break;
+    case 128: first_gather_t<T, 128>(g, first, x, src, nsrc, tau, ell, a, b, c, rec, win, s); break;
     default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
     }
 }
 
 void launch_first_or_gather(const sc_graph *g, int prec, int B, bool first, const void *x, const int32_t *src,
                             int nsrc, const int32_t *tau, int ell, double *a, double *b, double *cc,
-                            const GatherRec &rec, cudaStream_t s) {
+                            const GatherRec &rec, cudaStream_t s, const SliceWin *win = nullptr) {
     switch (prec) {
-    case SC_PREC_FP64: first_gather_p<double>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
-    case SC_PREC_FP32: first_gather_p<float>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
-    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, s); break;
+    case SC_PREC_FP64: first_gather_p<double>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, win, s); break;
+    case SC_PREC_FP32: first_gather_p<float>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, win, s); break;
+    case SC_PREC_BF16: first_gather_p<__nv_bfloat16>(g, B, first, x, src, nsrc, tau, ell, a, b, cc, rec, win, s); break;
     }
     SC_LAUNCH_CHECK();
+}
+
+// rows one CTA of the SIMT hop kernel takes on the light path
+static int light_rows_per_cta(int prec, int B, int vpl) {
+    const int V = B * static_cast<int>(elem_size(prec)) / 16;  // 16-byte vectors per row
+    return kSpmmWarps * (32 / (V / vpl));
 }
 
 // blocks propagated per launch: both ping-pong blocks within ~60% of L2
@@ -333,60 +350,107 @@ static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
     return static_cast<int>(std::min<int64_t>(std::min<int64_t>(slices, nblocks), 65535));
 }
 
-// Autotuner: time a few hops of every admissible (B, lane split) on this
-// graph (values do not change the kernel's cost, so zero blocks are used) and
-// keep the fastest per source-hop. Cached per graph, precision and request.
+// Autotuner: for every admissible (B, lane split) time what one block of
+// sources costs on this graph: the zeroing of X_1, the first hop, a hop with
+// the fused gather (taken L - 1 times) and the final gather, over a strided
+// sample of sources (values do not change the cost). Keeps the least time per
+// source; cached per graph, precision, request and length. The gathers write
+// the accumulators, which the caller resets afterwards.
 struct TuneResult {
     int B, vpl;
-    double ms_per_source_hop;  // measured by the autotuner (0 if it did not time)
+    double ms_per_source_hop;  // one hop with gather, per source
 };
 
-static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_slices, cudaStream_t s) {
+static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_slices, int32_t L, const GatherRec &rec,
+                           bool allow_tma, cudaStream_t s) {
+    L = std::max(L, 1);
     const long long key = (static_cast<long long>(prec) << 40) ^ (static_cast<long long>(fixB) << 24) ^
                           (static_cast<long long>(fixV) << 16) ^ static_cast<long long>(max_slices & 0xffff) ^
-                          (static_cast<long long>(g->n_heavy) << 44);
+                          (static_cast<long long>(g->n_heavy) << 44) ^ (static_cast<long long>(L) << 52) ^
+                          (static_cast<long long>(allow_tma) << 62);
     auto it = g->tuned.find(key);
     if (it != g->tuned.end()) return TuneResult{it->second.first, it->second.second, g->tuned_cost[key]};
     std::vector<std::pair<int, int>> cands;
     for (int B : {32, 64, 128})
         for (int v : {0, 1, 2, 4})
-            if ((fixB == 0 || fixB == B) && (fixV < 0 || fixV == v) && cfg_valid(prec, B, v)) cands.push_back({B, v});
+            if ((fixB == 0 || fixB == B) && (fixV < 0 || fixV == v) && (v != 0 || allow_tma) && cfg_valid(prec, B, v))
+                cands.push_back({B, v});
     if (cands.empty()) SC_FAIL(SC_ERR_INVALID_ARG, "no admissible kernel for B=%d split=%d", fixB, fixV);
 
     const size_t elem = elem_size(prec);
     size_t need = 0;
-    for (auto &c : cands) need = std::max(need, slices_for(g, c.first, elem, max_slices) * static_cast<size_t>(g->n) * c.first * elem);
-    g->xa.reserve(need);
-    g->xb.reserve(need);
-    SC_CUDA(cudaMemsetAsync(g->xa.get(), 0, need, s));
-    cudaEvent_t e0, e1;
-    SC_CUDA(cudaEventCreate(&e0));
-    SC_CUDA(cudaEventCreate(&e1));
-    double best = INFINITY;
-    std::pair<int, int> pick = cands[0];
+    int smax = 0;
     for (auto &c : cands) {
         const int sl = slices_for(g, c.first, elem, max_slices);
-        HopLaunch h{g->xa.get(), g->xb.get(), sl, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr, g->status.get(),
-                    GatherRec{0, nullptr, 0}};
-        launch_hop(g, prec, c.first, c.second, h, s);  // warm-up
-        SC_CUDA(cudaEventRecord(e0, s));
-        const int reps = 3;
-        for (int r = 0; r < reps; ++r) launch_hop(g, prec, c.first, c.second, h, s);
-        SC_CUDA(cudaEventRecord(e1, s));
-        SC_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        const double per_source_hop = ms / (reps * static_cast<double>(sl) * c.first);
-        if (per_source_hop < best) {
-            best = per_source_hop;
-            pick = c;
+        need = std::max(need, sl * static_cast<size_t>(g->n) * c.first * elem);
+        smax = std::max(smax, sl * c.first);
+    }
+    g->xa.reserve(need);
+    g->xb.reserve(need);
+    SC_CUDA(cudaMemsetAsync(g->xb.get(), 0, need, s));
+    std::vector<int32_t> h_src(smax);
+    for (int q = 0; q < smax; ++q) h_src[q] = static_cast<int32_t>((static_cast<int64_t>(q) * g->n) / smax);
+    g->src_list.reserve(smax);
+    SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), smax * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev[4];
+    for (auto &e : ev) SC_CUDA(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int q = 0; q < 4; ++q) cudaEventDestroy(e[q]);
+        }
+    } evg{ev};
+    double *acc_g = g->acc_g.get(), *acc_t1 = g->acc_t1.get(), *acc_t2 = g->acc_t2.get();
+    const int32_t *tau = g->tau_entry.get();
+    // three interleaved rounds over the candidates (so that clock or cache drift
+    // affects all of them alike), best round kept per candidate
+    std::vector<double> best_block(cands.size(), INFINITY), best_hop(cands.size(), INFINITY);
+    for (int round = 0; round < 3; ++round) {
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
+            const auto &c = cands[ci];
+            const int sl = slices_for(g, c.first, elem, max_slices);
+            const int nsrc = sl * c.first;
+            const int32_t *src = g->src_list.get();
+            HopLaunch h{g->xa.get(), g->xb.get(), sl, src, nsrc, tau, 1, acc_g, acc_t1, acc_t2, g->status.get(), rec};
+            if (round == 0) launch_hop(g, prec, c.first, c.second, h, s);  // warm-up
+            const int reps = 4;
+            SC_CUDA(cudaEventRecord(ev[0], s));
+            SC_CUDA(cudaMemsetAsync(g->xa.get(), 0, static_cast<size_t>(nsrc) * g->n * elem, s));
+            launch_first_or_gather(g, prec, c.first, true, g->xa.get(), src, nsrc, nullptr, 1, nullptr, nullptr,
+                                   nullptr, rec, s);
+            SC_CUDA(cudaEventRecord(ev[1], s));
+            for (int r = 0; r < reps; ++r) launch_hop(g, prec, c.first, c.second, h, s);
+            SC_CUDA(cudaEventRecord(ev[2], s));
+            launch_first_or_gather(g, prec, c.first, false, g->xb.get(), src, nsrc, tau, 1, acc_g, acc_t1, acc_t2,
+                                   rec, s);
+            SC_CUDA(cudaEventRecord(ev[3], s));
+            SC_CUDA(cudaEventSynchronize(ev[3]));
+            float a = 0.f, b = 0.f, c2 = 0.f;
+            SC_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+            SC_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+            SC_CUDA(cudaEventElapsedTime(&c2, ev[2], ev[3]));
+            const double hop = b / reps;
+            const double block = a + c2 + (L - 1) * hop;
+            best_block[ci] = std::min(best_block[ci], block / nsrc);
+            best_hop[ci] = std::min(best_hop[ci], hop / nsrc);
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    g->tuned[key] = pick;
-    g->tuned_cost[key] = best;
-    return TuneResult{pick.first, pick.second, best};
+    double best = INFINITY;
+    size_t pick = 0;
+    const bool log = std::getenv("SC_AUTOTUNE_LOG") != nullptr;
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        if (log)
+            std::fprintf(stderr, "sc autotune: prec %d L %d B %d split %d: %.4f us per source-hop (%.4f per hop alone)\n",
+                         prec, L, cands[ci].first, cands[ci].second == 0 ? -1 : cands[ci].second,
+                         1e3 * best_block[ci] / L, 1e3 * best_hop[ci]);
+        if (best_block[ci] < best) {
+            best = best_block[ci];
+            pick = ci;
+        }
+    }
+    g->tuned[key] = cands[pick];
+    g->tuned_cost[key] = best_hop[pick];
+    return TuneResult{cands[pick].first, cands[pick].second, best_hop[pick]};
 }
 
 // ---------------------------------------------------------------------------
@@ -606,6 +670,166 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
 }
 
 // ---------------------------------------------------------------------------
+// the windowed block loop (the frontier as an interval, K1w): blocks never
+// cross a segment (one graph of a batch, or the whole graph) and hold sources
+// of one length; each slice stores and computes only its window, so a slice
+// costs what its window holds instead of n rows. seg_start: segment
+// boundaries (nseg + 1 entries); beta: bandwidth bound of every segment (0:
+// the window is the whole segment).
+// ---------------------------------------------------------------------------
+struct WinBlock {
+    int64_t first;  // first entry in the padded source list (multiple of B)
+    int32_t L;      // hops (length + records)
+    SliceWin w;
+};
+
+static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vector<int32_t> &len,
+                           const std::vector<int32_t> &seg_start, int32_t beta) {
+    sc_graph *g = R.g;
+    cudaStream_t s = R.s;
+    const int B = R.B;
+    const size_t elem = elem_size(R.prec);
+    if (sources.empty()) return;
+    if (R.plus) SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ has no windowed form");
+    std::sort(sources.begin(), sources.end(), [&](int32_t a, int32_t b) {
+        return len[a] != len[b] ? len[a] > len[b] : a < b;
+    });
+    auto seg_of = [&](int32_t v) {
+        return static_cast<int32_t>(std::upper_bound(seg_start.begin(), seg_start.end(), v) - seg_start.begin()) - 1;
+    };
+    // blocks: up to B sources of one segment and one length
+    std::vector<int32_t> h_src;
+    std::vector<WinBlock> blocks;
+    for (size_t i = 0; i < sources.size();) {
+        const int32_t v0 = sources[i], sg = seg_of(v0), l0 = len[v0];
+        size_t j = i;
+        int32_t lo = v0, hi = v0;
+        while (j < sources.size() && static_cast<int>(j - i) < B && len[sources[j]] == l0 && seg_of(sources[j]) == sg) {
+            lo = std::min(lo, sources[j]);
+            hi = std::max(hi, sources[j]);
+            ++j;
+        }
+        WinBlock b{};
+        b.first = static_cast<int64_t>(h_src.size());
+        b.L = l0 + R.extra;
+        for (size_t q = i; q < j; ++q) h_src.push_back(sources[q]);
+        h_src.resize(h_src.size() + (B - (j - i)), -1);
+        SliceWin &w = b.w;
+        w.seg_lo = seg_start[sg];
+        w.seg_hi = seg_start[sg + 1];
+        w.src_lo = lo;
+        w.src_hi = hi + 1;
+        // storage: every row hop L + 1 may read (the neighbours of hop L's window)
+        int32_t a, e;
+        window_rows(w, beta, b.L + 1, &a, &e);
+        w.base = a;
+        w.rows = e - a;
+        const auto &H = g->h_heavy_ids;
+        w.heavy_begin = static_cast<int32_t>(std::lower_bound(H.begin(), H.end(), w.seg_lo) - H.begin());
+        w.heavy_cnt = static_cast<int32_t>(std::lower_bound(H.begin(), H.end(), w.seg_hi) - H.begin()) - w.heavy_begin;
+        blocks.push_back(b);
+        i = j;
+    }
+    // super-blocks: consecutive blocks of one length whose two ping-pong
+    // windows fit ~60% of L2 (at least one block)
+    const double budget = 0.6 * static_cast<double>(g->l2_bytes ? g->l2_bytes : (64u << 20));
+    const int max_sl = R.o->max_slices > 0 ? std::min(R.o->max_slices, 65535) : 65535;
+    std::vector<size_t> sb_begin;
+    size_t need = 0;
+    {
+        size_t i = 0;
+        while (i < blocks.size()) {
+            sb_begin.push_back(i);
+            double bytes = 0.0;
+            int64_t off = 0;
+            size_t j = i;
+            while (j < blocks.size() && static_cast<int>(j - i) < max_sl && blocks[j].L == blocks[i].L) {
+                const double add = 2.0 * static_cast<double>(blocks[j].w.rows) * B * elem;
+                if (j > i && bytes + add > budget) break;
+                bytes += add;
+                blocks[j].w.xoff = off;
+                off += static_cast<int64_t>(blocks[j].w.rows) * B;
+                ++j;
+            }
+            need = std::max(need, static_cast<size_t>(off) * elem);
+            i = j;
+        }
+        sb_begin.push_back(blocks.size());
+    }
+    std::vector<SliceWin> h_win(blocks.size());
+    for (size_t i = 0; i < blocks.size(); ++i) h_win[i] = blocks[i].w;
+    g->src_list.reserve(h_src.size());
+    g->win_list.reserve(h_win.size() * sizeof(SliceWin));
+    g->xa.reserve(need);
+    g->xb.reserve(need);
+    SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(g->win_list.get(), h_win.data(), h_win.size() * sizeof(SliceWin), cudaMemcpyHostToDevice, s));
+    const SliceWin *d_win = reinterpret_cast<const SliceWin *>(g->win_list.get());
+    if (R.time_kernels) {
+        int64_t total_hops = 0;
+        for (size_t q = 0; q + 1 < sb_begin.size(); ++q) total_hops += std::max(blocks[sb_begin[q]].L - 1, 0);
+        while (static_cast<int64_t>(g->hop_events.size()) < 2 * (R.hop_launches + total_hops)) {
+            cudaEvent_t e;
+            SC_CUDA(cudaEventCreate(&e));
+            g->hop_events.push_back(e);
+        }
+    }
+    const int rpc = light_rows_per_cta(R.prec, B, R.vpl);
+    const auto &hrp = g->h_row_ptr;
+    for (size_t q = 0; q + 1 < sb_begin.size(); ++q) {
+        const size_t b0 = sb_begin[q], b1 = sb_begin[q + 1];
+        const int used = static_cast<int>(b1 - b0);
+        const int32_t L = blocks[b0].L;
+        const int nsrc = used * B;
+        const int32_t *src = g->src_list.get() + blocks[b0].first;
+        const SliceWin *win = d_win + b0;
+        size_t bytes = 0;
+        for (size_t b = b0; b < b1; ++b) {
+            bytes += static_cast<size_t>(blocks[b].w.rows) * B * elem;
+            int32_t cnt = 0;
+            for (int64_t t = blocks[b].first; t < blocks[b].first + B; ++t) cnt += h_src[t] >= 0;
+            R.ell_min_src = std::min(R.ell_min_src, L);
+            R.ell_max_src = std::max(R.ell_max_src, L);
+            R.source_hops += static_cast<int64_t>(L) * cnt;
+        }
+        if (L == 0) continue;
+        void *xa = g->xa.get(), *xb = g->xb.get();
+        SC_CUDA(cudaMemsetAsync(xa, 0, bytes, s));
+        SC_CUDA(cudaMemsetAsync(xb, 0, bytes, s));
+        launch_first_or_gather(g, R.prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, R.rec, s, win);
+        R.launches += 1;
+        for (int32_t ell = 2; ell <= L; ++ell) {
+            int ctas = 0;
+            double hop_bytes = 0.0;
+            for (size_t b = b0; b < b1; ++b) {
+                int32_t lo, hi;
+                window_rows(blocks[b].w, beta, ell, &lo, &hi);
+                ctas = std::max(ctas, blocks[b].w.heavy_cnt + ceil_div(hi - lo, rpc));
+                hop_bytes += 4.0 * (hrp[hi] - hrp[lo]) + 4.0 * (hi - lo + 1) +
+                             (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * (hi - lo) + 2.0 * (hi - lo) * B * elem;
+            }
+            HopLaunch h{xa, xb, used, src, nsrc, g->tau_entry.get(), ell - 1,
+                        g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
+            h.win = win;
+            h.ell = ell;
+            h.beta = beta;
+            h.win_ctas = ctas;
+            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
+            launch_hop(g, R.prec, B, R.vpl, h, s);
+            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], s));
+            ++R.hop_launches;
+            std::swap(xa, xb);
+            R.launches += 1;
+            R.alg_bytes += hop_bytes;
+        }
+        launch_first_or_gather(g, R.prec, B, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(),
+                               g->acc_t1.get(), g->acc_t2.get(), R.rec, s, win);
+        R.launches += 1;
+        R.hops += L;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // the driver
 // ---------------------------------------------------------------------------
 static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep,
@@ -703,7 +927,19 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaMemsetAsync(g->status.get(), 0, 4 * sizeof(int32_t), s));
     // rows_split: 0 = automatic, -1 = the TMA-gather kernel, 1/2/4 = SIMT lane split
     const int fixV = o.rows_split == 0 ? -1 : (o.rows_split < 0 ? 0 : o.rows_split);
-    const TuneResult tr = autotune(g, o.precision, o.block_width, fixV, o.max_slices, s);
+    const GatherRec rec{learned ? 1 : 0, rec_all, rec_stride};
+    g->acc_g.reserve(nnz);
+    g->acc_t1.reserve(nnz);
+    g->acc_t2.reserve(nnz);
+    // windowed blocks (the frontier as an interval) when the graph's bandwidth
+    // keeps a block's last window under half the graph, or when asked for
+    const int32_t beta = ensure_bandwidth(g);
+    const int32_t Lmax = ell_global + (record_after ? 2 : 0);
+    const bool use_win = !plus && o.rows_split != -1 && !(o.flags & SC_OPT_WINDOWS_OFF) &&
+                         ((o.flags & SC_OPT_WINDOWS_FORCE) ||
+                          2.0 * (Lmax + 1.0) * static_cast<double>(beta) + 128.0 < 0.5 * static_cast<double>(n));
+    const TuneResult tr = autotune(g, o.precision, o.block_width, fixV, o.max_slices, Lmax,
+                                   GatherRec{rec.mode, nullptr, 0}, !use_win, s);
     Run R;
     R.g = g;
     R.o = &o;
@@ -720,15 +956,12 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     const double delta = o.delta > 0.0 ? o.delta : 1.0 / static_cast<double>(n);  // Section 5.1: delta = 1/n
     R.log2md = std::log(2.0 * static_cast<double>(nnz / 2) / delta);
     R.extra = record_after ? 2 : 0;
-    R.rec = GatherRec{learned ? 1 : 0, rec_all, rec_stride};
+    R.rec = rec;
     R.ms_per_source_hop = tr.ms_per_source_hop;
     const int64_t nblocks_total = (static_cast<int64_t>(n) + R.B - 1) / R.B;
 
     g->xa.reserve(R.slices * R.slice_bytes);
     g->xb.reserve(R.slices * R.slice_bytes);
-    g->acc_g.reserve(nnz);
-    g->acc_t1.reserve(nnz);
-    g->acc_t2.reserve(nnz);
     k_reset_rows<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), nullptr, n, g->tau_entry.get(), R.rec.mode,
                                                 g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
     SC_LAUNCH_CHECK();
@@ -739,7 +972,12 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaEventRecord(ev1, s));
     std::vector<int32_t> all(n);
     std::iota(all.begin(), all.end(), 0);
-    run_blocks(R, all, len);
+    const std::vector<int32_t> seg_whole{0, n};
+    auto run = [&](const std::vector<int32_t> &src, const std::vector<int32_t> &l) {
+        if (use_win) run_blocks_win(R, src, l, seg_whole, beta);
+        else run_blocks(R, src, l);
+    };
+    run(all, len);
 
     // ---- combine, and for the learned lengths the check / extension loop ------
     DevBuf<double> tmp_s, tmp_b;
@@ -813,7 +1051,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
                 g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
             SC_LAUNCH_CHECK();
             R.launches += 2;
-            run_blocks(R, redo, len);
+            run(redo, len);
             combine();
         }
     }

@@ -83,6 +83,33 @@ struct GatherRec {
     int stride;
 };
 
+// The rows one slice of a launch covers (the frontier of Algorithm 2, which
+// only visits nodes with p_{l-1} > 0, kept as an interval). The slice stores
+// rows [base, base + rows) at element offset xoff of the block buffer; hop l
+// computes rows [lo_l, hi_l) = [max(seg_lo, src_lo - l beta), min(seg_hi,
+// src_hi + l beta)) with beta the graph's bandwidth (beta = 0: the whole
+// segment). A segment is one graph of a batch (or the whole graph). The
+// support of X_l lies in [lo_l, hi_l) and rows outside it stay zero, so the
+// result is the one of the full hop.
+struct SliceWin {
+    int64_t xoff;
+    int32_t base, rows;
+    int32_t seg_lo, seg_hi;
+    int32_t src_lo, src_hi;
+    int32_t heavy_begin, heavy_cnt;  // the segment's heavy rows in the id-sorted heavy list
+};
+
+__host__ __device__ __forceinline__ void window_rows(const SliceWin &w, int32_t beta, int32_t ell, int32_t *lo,
+                                                     int32_t *hi) {
+    int64_t a = w.seg_lo, b = w.seg_hi;
+    if (beta > 0) {
+        a = max(a, static_cast<int64_t>(w.src_lo) - static_cast<int64_t>(ell) * beta);
+        b = min(b, static_cast<int64_t>(w.src_hi) + static_cast<int64_t>(ell) * beta);
+    }
+    *lo = static_cast<int32_t>(a);
+    *hi = static_cast<int32_t>(b);
+}
+
 // Arguments of one hop launch.
 template <typename T>
 struct HopArgs {
@@ -99,32 +126,42 @@ struct HopArgs {
     const int32_t *row_order;
     int32_t n_heavy;
     int32_t light_ctas;
-    // fused gather of X_{l-1} for the launch's sources (gather_ell > 0):
-    // see gather_source
+    // fused gather of X_{l-1} for the launch's sources (gather_ell > 0), one
+    // CTA per source of the slice, placed first in the grid: see gather_source
+    int32_t gather_ctas;
     const int32_t *src;
     int32_t nsrc;
     const int32_t *tau;
     int32_t gather_ell;
     double *g, *t1, *t2;
     GatherRec rec;
+    // windowed launch (win != nullptr): per slice (blockIdx.y) window, the hop
+    // index, the bandwidth, the id-sorted heavy rows and the heavy threshold
+    const SliceWin *win;
+    int32_t ell, beta;
+    const int32_t *heavy_ids;
+    int32_t heavy_t;
 };
 
 // Alg. 2 lines 10-11 for hop `ell` and launch source q (slice q / B, column
 // q % B): for source i = s_b and each entry k = (i -> j) the unscaled half term
 // p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while ell <= tau[k]; t1, t2
 // keep the terms of hops tau+1, tau+2 (mode 0) or tau-1, tau (mode 1). (The
-// 1/d(v_i) factor of Eq. 9 is applied once in the combine.) One warp per source.
+// 1/d(v_i) factor of Eq. 9 is applied once in the combine.) Threads tid of
+// nthr take the entries of the source's row in turn (one CTA per source, so a
+// hub's row does not serialise on one warp).
+// xs points at the source's column of its slice, whose first stored row is
+// `base`.
 template <typename T, int B>
 __device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                              const T *__restrict__ x, int32_t n, int32_t s, int32_t q,
+                                              const T *__restrict__ xs, int32_t base, int32_t s,
                                               const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
-                                              double *__restrict__ t1, double *__restrict__ t2, int lane,
+                                              double *__restrict__ t1, double *__restrict__ t2, int tid, int nthr,
                                               const GatherRec rec) {
-    const T *xs = x + static_cast<int64_t>(q / B) * n * B + (q % B);
-    const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s) * B]));
-    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
+    const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s - base) * B]));
+    for (int32_t k = row_ptr[s] + tid; k < row_ptr[s + 1]; k += nthr) {
         const int32_t j = col[k];
-        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j) * B]));
+        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j - base) * B]));
         const int32_t tk = tau[k];
         if (ell <= tk) {
             g[k] += term;
@@ -140,31 +177,70 @@ __device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_pt
     }
 }
 
+// column q % B of slice q / B: pointer and first stored row
+template <typename T, int B>
+__device__ __forceinline__ const T *slice_column(const T *x, int32_t n, const SliceWin *win, int32_t q,
+                                                 int32_t *base) {
+    if (win) {
+        *base = win[q / B].base;
+        return x + win[q / B].xoff + (q % B);
+    }
+    *base = 0;
+    return x + static_cast<int64_t>(q / B) * n * B + (q % B);
+}
+
 // ---------------------------------------------------------------------------
-// One hop for S = gridDim.y slices. CTAs [0, n_heavy) each take one heavy row
-// and split its chunks over all warps; the next light_ctas CTAs give each row
-// group of LG lanes one light row; the remaining CTAs (if any) gather X_{l-1}
-// for the launch's sources.
+// One hop for S = gridDim.y slices. CTAs [0, gather_ctas) gather X_{l-1} for
+// the slice's sources (first, so that a hub source's long row overlaps the
+// hop instead of trailing it); the next n_heavy CTAs each take one heavy row
+// and split its chunks over all warps; the last light_ctas CTAs give each row
+// group of LG lanes one light row. A windowed launch takes its slice's
+// heavy rows from the id-sorted list and its light rows in natural order over
+// the window, skipping the heavy ones; rows are stored from the slice's base.
 // ---------------------------------------------------------------------------
 template <typename T, int B, int VPL>
 __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a) {
     using L = Layout<T, B, VPL>;
     using Acc = typename L::Acc;
     const int32_t n = a.n;
-    const int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
-    const uint4 *xp = reinterpret_cast<const uint4 *>(a.x_prev + slice_off);
-    uint4 *xn = reinterpret_cast<uint4 *>(a.x_next + slice_off);
+    int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
+    int32_t base = 0, lo = 0, hi = n, n_heavy = a.n_heavy;
+    if (a.win) {
+        const SliceWin w = a.win[blockIdx.y];
+        slice_off = w.xoff;
+        base = w.base;
+        window_rows(w, a.beta, a.ell, &lo, &hi);
+        n_heavy = w.heavy_cnt;
+    }
+    // rows are addressed as (row - base) within the slice
+    const uint4 *xp = reinterpret_cast<const uint4 *>(a.x_prev + slice_off) - static_cast<int64_t>(base) * L::V;
+    uint4 *xn = reinterpret_cast<uint4 *>(a.x_next + slice_off) - static_cast<int64_t>(base) * L::V;
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / L::LG, gl = lane % L::LG;
-    const int32_t cta = static_cast<int32_t>(blockIdx.x);
+    if (static_cast<int32_t>(blockIdx.x) < a.gather_ctas) {
+        // ---------------- fused gather of X_{l-1} ----------------
+        const int32_t q = static_cast<int32_t>(blockIdx.y) * B + static_cast<int32_t>(blockIdx.x);
+        if (q < a.nsrc) {
+            const int32_t s = a.src[q];
+            if (s >= 0) {
+                int32_t sb;
+                const T *xs = slice_column<T, B>(a.x_prev, n, a.win, q, &sb);
+                gather_source<T, B>(row_ptr, col, xs, sb, s, a.tau, a.gather_ell, a.g, a.t1, a.t2, threadIdx.x,
+                                    kSpmmWarps * 32, a.rec);
+            }
+        }
+        return;
+    }
+    const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;
 
-    if (cta < a.n_heavy) {
+    if (cta < n_heavy) {
         // ---------------- heavy row: chunks spread over the CTA ----------------
         constexpr int NGRP = kSpmmWarps * L::G;  // chunk slots per round
         __shared__ Acc part[NGRP][B];
-        const int32_t row = a.row_order[cta];
+        const int32_t row = a.win ? a.heavy_ids[a.win[blockIdx.y].heavy_begin + cta] : a.row_order[cta];
+        if (row < lo || row >= hi) return;  // outside the window: X_l is zero there
         const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
         const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
         Acc total = Acc(0);  // thread t < B owns column t
@@ -211,28 +287,24 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
             __syncthreads();
         }
         if (threadIdx.x < B) {
-            T *out = a.x_next + slice_off + static_cast<int64_t>(row) * B;
+            T *out = a.x_next + slice_off + static_cast<int64_t>(row - base) * B;
             out[threadIdx.x] = from_acc<T>(total * a.inv_deg[row]);
         }
         return;
     }
 
-    if (cta >= a.n_heavy + a.light_ctas) {
-        // ---------------- fused gather of X_{l-1} ----------------
-        const int32_t q = static_cast<int32_t>(blockIdx.y) * B + (cta - a.n_heavy - a.light_ctas) * kSpmmWarps + warp;
-        if (q < a.nsrc) {
-            const int32_t s = a.src[q];
-            if (s >= 0)
-                gather_source<T, B>(row_ptr, col, a.x_prev, n, s, q, a.tau, a.gather_ell, a.g, a.t1, a.t2, lane, a.rec);
-        }
-        return;
-    }
-
     // ---------------- light rows: one row per group of LG lanes ----------------
-    const int64_t idx = (static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp) * L::G + grp;
-    if (idx >= n - a.n_heavy) return;
-    const int32_t row = a.row_order ? a.row_order[a.n_heavy + idx] : static_cast<int32_t>(idx);
+    const int64_t idx = (static_cast<int64_t>(cta - n_heavy) * kSpmmWarps + warp) * L::G + grp;
+    int32_t row;
+    if (a.win) {
+        if (idx >= hi - lo) return;
+        row = lo + static_cast<int32_t>(idx);
+    } else {
+        if (idx >= n - a.n_heavy) return;
+        row = a.row_order ? a.row_order[a.n_heavy + idx] : static_cast<int32_t>(idx);
+    }
     const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
+    if (a.win && re - rb > a.heavy_t) return;  // a heavy row: its own CTA computes it
     Acc acc[L::NACC], chunk[L::NACC];
 #pragma unroll
     for (int q = 0; q < L::NACC; ++q) {
@@ -278,43 +350,54 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
 
 // X_1 = P e_s for each source s of the launch (Alg. 2 line 2 followed by the
 // first hop): X_1[j, b] = 1/d_j for j in N(s_b). X_1 must be zero on entry.
+// One CTA per source.
 template <typename T, int B>
 __global__ void k_first_hop(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                             const typename AccOf<T>::type *__restrict__ inv_deg, const int32_t *__restrict__ src,
-                            int32_t nsrc, T *__restrict__ x1, int32_t n) {
-    const int32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+                            int32_t nsrc, T *__restrict__ x1, int32_t n, const SliceWin *__restrict__ win) {
+    const int32_t q = blockIdx.x;
     if (q >= nsrc) return;
     const int32_t s = src[q];
     if (s < 0) return;
-    T *xs = x1 + static_cast<int64_t>(q / B) * n * B + (q % B);
-    for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) {
+    int32_t base;
+    T *xs = const_cast<T *>(slice_column<T, B>(x1, n, win, q, &base));
+    for (int32_t k = row_ptr[s] + threadIdx.x; k < row_ptr[s + 1]; k += blockDim.x) {
         const int32_t j = col[k];
-        xs[static_cast<int64_t>(j) * B] = from_acc<T>(inv_deg[j]);
+        xs[static_cast<int64_t>(j - base) * B] = from_acc<T>(inv_deg[j]);
     }
 }
 
-// stand-alone gather (the last hop of a block, and callers without fusion)
+// stand-alone gather (the last hop of a block, and callers without fusion):
+// one CTA per source
 template <typename T, int B>
 __global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                          const T *__restrict__ x, int32_t n, const int32_t *__restrict__ src, int32_t nsrc,
                          const int32_t *__restrict__ tau, int32_t ell, double *__restrict__ g,
-                         double *__restrict__ t1, double *__restrict__ t2, const GatherRec rec) {
-    const int32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+                         double *__restrict__ t1, double *__restrict__ t2, const GatherRec rec,
+                         const SliceWin *__restrict__ win) {
+    const int32_t q = blockIdx.x;
     if (q >= nsrc) return;
     const int32_t s = src[q];
     if (s < 0) return;
-    gather_source<T, B>(row_ptr, col, x, n, s, q, tau, ell, g, t1, t2, lane, rec);
+    int32_t base;
+    const T *xs = slice_column<T, B>(x, n, win, q, &base);
+    gather_source<T, B>(row_ptr, col, xs, base, s, tau, ell, g, t1, t2, threadIdx.x, blockDim.x, rec);
 }
 
-// launch helper: one hop over `slices` slices, optionally gathering X_{l-1}
+// rows one CTA of the SIMT hop kernel computes on the light path
 template <typename T, int B, int VPL>
-inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s) {
+constexpr int light_rows_per_cta() {
+    return kSpmmWarps * Layout<T, B, VPL>::G;
+}
+
+// launch helper: one hop over `slices` slices, optionally gathering X_{l-1};
+// a windowed launch passes the largest heavy + light CTA count of its slices
+template <typename T, int B, int VPL>
+inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s, int win_ctas = 0) {
     using L = Layout<T, B, VPL>;
     a.light_ctas = ceil_div(a.n - a.n_heavy, kSpmmWarps * L::G);
-    const int gather_ctas = a.gather_ell > 0 ? ceil_div(B, kSpmmWarps) : 0;
-    dim3 grid(a.n_heavy + a.light_ctas + gather_ctas, slices);
+    a.gather_ctas = a.gather_ell > 0 ? B : 0;
+    dim3 grid(a.gather_ctas + (a.win ? win_ctas : a.n_heavy + a.light_ctas), slices);
     k_spmm_hop<T, B, VPL><<<grid, kSpmmWarps * 32, 0, s>>>(a);
 }
 

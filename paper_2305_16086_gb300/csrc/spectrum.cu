@@ -22,16 +22,18 @@ namespace sc {
 // ---------------------------------------------------------------------------
 // A3: truncation length per CSR entry
 // ---------------------------------------------------------------------------
+// one warp per row: the lanes take the row's entries (hub rows are long)
 __global__ void k_tau_entries(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
                               double eps, double lam, int32_t *__restrict__ tau, int32_t *__restrict__ tau_src,
                               int32_t *ell_global) {
-    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const double di = static_cast<double>(row_ptr[r + 1] - row_ptr[r]);
     const double denom = __dmul_rn(eps, __dsub_rn(1.0, __dmul_rn(lam, lam)));
     const double log_inv_lam = log(__ddiv_rn(1.0, lam));
     int32_t best = 0;
-    for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
         const int32_t j = col[k];
         const double dj = static_cast<double>(row_ptr[j + 1] - row_ptr[j]);
         // X_e = 1/d_i + 1/d_j - 2/(d_i d_j), evaluated left to right without contraction
@@ -46,8 +48,12 @@ __global__ void k_tau_entries(const int32_t *__restrict__ row_ptr, const int32_t
         tau[k] = t;
         best = max(best, t);
     }
-    tau_src[r] = best;
-    atomicMax(ell_global, best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) {
+        tau_src[r] = best;
+        atomicMax(ell_global, best);
+    }
 }
 
 void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_entry, int32_t *tau_src,
@@ -56,7 +62,7 @@ void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_e
     g->status.reserve(4);
     cudaStream_t s = g->stream;
     SC_CUDA(cudaMemsetAsync(g->status.get(), 0, sizeof(int32_t), s));
-    k_tau_entries<<<ceil_div(g->n, 256), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->n, eps,
+    k_tau_entries<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->n, eps,
                                                        std::max(lam_star, 0.0), tau_entry, tau_src, g->status.get());
     SC_LAUNCH_CHECK();
     SC_CUDA(cudaMemcpyAsync(ell_global_host, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
