@@ -178,6 +178,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(pg, x: float, device) -> float:
+    """The slowest rank's value (the job ends when the last replica does)."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, m: int, ms_per_step: float) -> float:
+    """Whole-job edges/s: every replica processes all m edges of its own copy
+    of the workload per step (weak scaling, no exchange between replicas)."""
+    return world * m / (ms_per_step / 1e3)
+
+
 def run_reference(args, world, rank):
     """The oracle on the host cores: each step a bounded sample of the workload."""
     if rank != 0:
@@ -282,13 +299,9 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             reports.append(rep)
         barrier()
-    total_ms = float(sum(step_ms))
-    if pg is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(pg, float(sum(step_ms)), "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * g.m / (ms_per_step / 1e3)
+    value = replica_value(world, g.m, ms_per_step)
 
     hop_ms = sum(r["hop_ms"] for r in reports)
     hop_bytes = sum(r["hop_bytes"] for r in reports)
@@ -323,12 +336,8 @@ def main():
             torch.cuda.synchronize()
             if i >= 2:
                 e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_step = statistics.mean(e2e_ms)
-        if pg is not None:
-            t = torch.tensor([e2e_step], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_step = float(t.item())
-        e2e = {"value": world * g.m / (e2e_step / 1e3), "unit": UNIT,
+        e2e_step = max_over_ranks(pg, statistics.mean(e2e_ms), "cuda")
+        e2e = {"value": replica_value(world, g.m, e2e_step), "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz), "d2h_bytes_per_step": int(8 * g.nnz),
                "ms_per_step": e2e_step,
                "includes": "graph create + validation + Lanczos + model load + features + all edges + D2H"}
@@ -351,6 +360,8 @@ def main():
                           "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m}
 
     if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:

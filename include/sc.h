@@ -242,7 +242,7 @@ typedef struct sc_report {
     double walk_ms;            /* TGT+: wall time drawing walks (planning, kernels) */
     int64_t source_hops;       /* sum over sources of hops traversed (the traversal's work) */
     int32_t extension_rounds;  /* learned policy: rerun rounds for edges that failed their bound */
-    int32_t reserved;
+    int32_t windowed;          /* 1 if the blocks ran windowed (SC_OPT_WINDOWS_*) */
 } sc_report;
 
 /*
@@ -266,6 +266,40 @@ typedef struct sc_report {
  */
 sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                        sc_report *report);
+
+/*
+ * sc_batch_all_edges -- sc_all_edges over many independent graphs in one
+ * pass (Definition 2.2 for each). The paper treats one graph at a time;
+ * Algorithm 2's source loop is independent across graphs as much as across
+ * sources, so the graphs' disjoint union is propagated in windowed blocks
+ * (SC_OPT_WINDOWS_*): a block holds sources of one graph and one length and
+ * stores and computes that graph's rows only. The launches of the whole
+ * batch are recorded into one CUDA graph and replayed as one launch.
+ *
+ *   graphs        : count >= 1 graphs created on one device. The batch runs
+ *                   on graphs[0]'s stream after waiting for every graph's
+ *                   stream; each graph's lambda estimate is computed if the
+ *                   Eq. 6 length needs it and none is cached.
+ *   opts          : as sc_all_edges, for every graph; mode SC_MODE_TGT,
+ *                   policy SC_ELL_GLOBAL (each graph its own Eq. 6 length)
+ *                   or SC_ELL_FIXED; no TMA-gather split.
+ *   ell_per_graph : nullable; count entries; > 0 overrides graph i's length
+ *                   (e.g. an empirical length for a bipartite lattice, whose
+ *                   Eq. 6 length does not exist), 0 keeps the policy.
+ *   s_hat         : count pointers; s_hat[i] holds graphs[i]'s nnz values,
+ *                   host or device per SC_OUT_DEVICE (caller-owned).
+ *   reports       : nullable; count reports. Per graph: ell_global,
+ *                   ell_min/max_source, blocks, source_hops, foster_sum,
+ *                   lambda_star; launches, hops, hop_launches, bytes and
+ *                   times hold the batch totals in every report.
+ * Errors: SC_ERR_UNSUPPORTED for TGT+, the learned policy, or a bipartite
+ * graph under SC_ELL_GLOBAL without an override; SC_ERR_INVALID_ARG for
+ * NULL inputs, mixed devices, negative lengths or a union of 2^31 nodes or
+ * entries; SC_ERR_OOM / SC_ERR_CUDA as elsewhere. Outputs are unspecified
+ * on error.
+ */
+sc_status sc_batch_all_edges(sc_graph *const *graphs, int32_t count, const sc_options *opts,
+                             const int32_t *ell_per_graph, double *const *s_hat, sc_report *reports);
 
 /* ---- learned per-source length (step A8; the paper has no learned part) --- */
 

@@ -29,6 +29,7 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 EST = {"plain": 0, "end_corrected": 1}
 MODE = {"tgt": 0, "tgt_plus": 1}
 SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
+SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE = 8, 16
 
 # every symbol include/sc.h declares
 EXPORTS = [
@@ -36,6 +37,7 @@ EXPORTS = [
     "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
+    "sc_batch_all_edges",
 ]
 MLP_PARAMS, MLP_FEATURES = 1313, 6
 MLP_MODEL_FLOATS = MLP_PARAMS + 2 * MLP_FEATURES
@@ -80,10 +82,10 @@ class Report(ctypes.Structure):
                 ("walks", ctypes.c_int64), ("edges_extended", ctypes.c_int32),
                 ("tt_min", ctypes.c_int32), ("tt_max", ctypes.c_int32),
                 ("switch_tests", ctypes.c_int32), ("switch_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
-                ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class MlpTrainOpts(ctypes.Structure):
@@ -127,6 +129,9 @@ def load(path: str = LIB_PATH):
     L.sc_options_default.restype = None
     L.sc_all_edges.argtypes = [vp, ctypes.POINTER(Options), vp, vp, ctypes.POINTER(Report)]
     L.sc_all_edges.restype = ctypes.c_int
+    L.sc_batch_all_edges.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Options), ctypes.POINTER(i32),
+                                     ctypes.POINTER(vp), ctypes.POINTER(Report)]
+    L.sc_batch_all_edges.restype = ctypes.c_int
     L.sc_status_string.argtypes = [ctypes.c_int]
     L.sc_status_string.restype = ctypes.c_char_p
     L.sc_last_error_detail.argtypes = []
@@ -252,7 +257,7 @@ class Graph:
     def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
                 record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
-                switch="cost") -> Options:
+                switch="cost", windows=None) -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
         o.eps = eps
@@ -266,6 +271,8 @@ class Graph:
         o.heavy_threshold = heavy_threshold
         o.max_slices = max_slices
         o.flags = (SC_OPT_RECORD_TAIL if record_tail else 0) | (SC_OPT_TIME_KERNELS if time_kernels else 0)
+        if windows is not None:  # None: automatic; True / False: force on / off
+            o.flags |= SC_OPT_WINDOWS_FORCE if windows else SC_OPT_WINDOWS_OFF
         if seed is not None:
             o.seed = seed
         o.delta = delta
@@ -298,6 +305,31 @@ class Graph:
                                    ctypes.c_void_p(b.ctypes.data) if b is not None else None,
                                    ctypes.byref(rep)), "sc_all_edges")
         return s, b, rep.as_dict()
+
+
+def batch_all_edges(graphs, ell_per_graph=None, outs=None, **kw):
+    """sc_batch_all_edges over a list of Graph objects. ``ell_per_graph``:
+    None or one length per graph (0 keeps the policy). ``outs``: None (host
+    numpy outputs) or one torch CUDA float64 tensor per graph. Returns
+    (list of s_hat, list of report dicts)."""
+    count = len(graphs)
+    o = Graph.options(**kw)
+    hs = (ctypes.c_void_p * count)(*[g._h.value for g in graphs])
+    if outs is None:
+        res = [np.empty(g.nnz, dtype=np.float64) for g in graphs]
+        ptrs = (ctypes.c_void_p * count)(*[r.ctypes.data for r in res])
+    else:
+        res = list(outs)
+        o.flags |= SC_OUT_DEVICE
+        ptrs = (ctypes.c_void_p * count)(*[r.data_ptr() for r in res])
+    ells = None
+    if ell_per_graph is not None:
+        ells = (ctypes.c_int32 * count)(*[int(x) for x in ell_per_graph])
+    reps = (Report * count)()
+    _check(load().sc_batch_all_edges(ctypes.cast(hs, ctypes.POINTER(ctypes.c_void_p)), count, ctypes.byref(o),
+                                     ells, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), reps),
+           "sc_batch_all_edges")
+    return res, [r.as_dict() for r in reps]
 
 
 def all_edges_noalloc(row_ptr, col_idx, ell: int, out, stream=None):

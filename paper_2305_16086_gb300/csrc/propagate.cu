@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <numeric>
 
 #include <cudaTypedefs.h>
@@ -31,15 +32,6 @@ void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_e
 // ---------------------------------------------------------------------------
 // accumulator initialisation and combine
 // ---------------------------------------------------------------------------
-// hop 0 of Eq. (9): p_0(v_i,v_i) - p_0(v_j,v_i) = 1 for every entry (Alg. 2 line 3, unscaled)
-__global__ void k_init_acc(double *g, double *t1, double *t2, int64_t nnz) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= nnz) return;
-    g[k] = 1.0;
-    t1[k] = 0.0;
-    t2[k] = 0.0;
-}
-
 // s_hat(e_ij) = g(v_i,v_j) + g(v_j,v_i) (Alg. 2 line 12) with g = unscaled / d,
 // optionally + t_{tau+1}/2; tail bound from q = t_{tau+1} + t_{tau+2}.
 __global__ void k_combine(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -539,8 +531,9 @@ struct Run {
     int extra;  // hops beyond the per-source length (records of tau+1, tau+2)
     GatherRec rec;
     double ms_per_source_hop;
+    bool capture = false;  // windowed loop: record into one CUDA graph
     // statistics
-    int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0;
+    int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0, graph_launches = 0;
     double alg_bytes = 0.0, switch_ms = 0.0, walk_ms = 0.0;
     int32_t ell_min_src = INT32_MAX, ell_max_src = 0, tt_min = INT32_MAX, tt_max = 0, switch_tests = 0;
 };
@@ -676,11 +669,31 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
 // costs what its window holds instead of n rows. seg_start: segment
 // boundaries (nseg + 1 entries); beta: bandwidth bound of every segment (0:
 // the window is the whole segment).
+//
+// Launches: blocks are ordered by window size class (powers of two) and by
+// length, longest first; a launch (super-block) takes consecutive blocks of
+// one class up to a memory budget. Hop l of a super-block runs over its
+// leading blocks with L >= l - 1 (the others are done): blocks with L >= l
+// compute X_l, and all of them gather X_{l-1} (Alg. 2 lines 10-11), which
+// is the final gather of the blocks with L = l - 1. With R.capture the whole
+// loop is recorded into one CUDA graph and replayed as one launch.
 // ---------------------------------------------------------------------------
 struct WinBlock {
     int64_t first;  // first entry in the padded source list (multiple of B)
-    int32_t L;      // hops (length + records)
     SliceWin w;
+    int cls;        // window size class
+};
+
+struct CaptureGuard {  // ends a stream capture left open by an exception
+    cudaStream_t s;
+    bool open = false;
+    ~CaptureGuard() {
+        if (open) {
+            cudaGraph_t gr = nullptr;
+            cudaStreamEndCapture(s, &gr);
+            if (gr) cudaGraphDestroy(gr);
+        }
+    }
 };
 
 static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vector<int32_t> &len,
@@ -689,8 +702,10 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     cudaStream_t s = R.s;
     const int B = R.B;
     const size_t elem = elem_size(R.prec);
-    if (sources.empty()) return;
     if (R.plus) SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ has no windowed form");
+    sources.erase(std::remove_if(sources.begin(), sources.end(), [&](int32_t v) { return len[v] + R.extra <= 0; }),
+                  sources.end());
+    if (sources.empty()) return;
     std::sort(sources.begin(), sources.end(), [&](int32_t a, int32_t b) {
         return len[a] != len[b] ? len[a] > len[b] : a < b;
     });
@@ -698,8 +713,8 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
         return static_cast<int32_t>(std::upper_bound(seg_start.begin(), seg_start.end(), v) - seg_start.begin()) - 1;
     };
     // blocks: up to B sources of one segment and one length
-    std::vector<int32_t> h_src;
     std::vector<WinBlock> blocks;
+    std::vector<std::vector<int32_t>> block_src;
     for (size_t i = 0; i < sources.size();) {
         const int32_t v0 = sources[i], sg = seg_of(v0), l0 = len[v0];
         size_t j = i;
@@ -710,52 +725,71 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             ++j;
         }
         WinBlock b{};
-        b.first = static_cast<int64_t>(h_src.size());
-        b.L = l0 + R.extra;
-        for (size_t q = i; q < j; ++q) h_src.push_back(sources[q]);
-        h_src.resize(h_src.size() + (B - (j - i)), -1);
         SliceWin &w = b.w;
+        w.L = l0 + R.extra;
         w.seg_lo = seg_start[sg];
         w.seg_hi = seg_start[sg + 1];
         w.src_lo = lo;
         w.src_hi = hi + 1;
         // storage: every row hop L + 1 may read (the neighbours of hop L's window)
         int32_t a, e;
-        window_rows(w, beta, b.L + 1, &a, &e);
+        window_rows(w, beta, w.L + 1, &a, &e);
         w.base = a;
         w.rows = e - a;
         const auto &H = g->h_heavy_ids;
         w.heavy_begin = static_cast<int32_t>(std::lower_bound(H.begin(), H.end(), w.seg_lo) - H.begin());
         w.heavy_cnt = static_cast<int32_t>(std::lower_bound(H.begin(), H.end(), w.seg_hi) - H.begin()) - w.heavy_begin;
+        b.cls = 0;
+        while ((1 << b.cls) < w.rows && b.cls < 31) ++b.cls;
         blocks.push_back(b);
+        block_src.emplace_back(sources.begin() + i, sources.begin() + j);
         i = j;
     }
-    // super-blocks: consecutive blocks of one length whose two ping-pong
-    // windows fit ~60% of L2 (at least one block)
-    const double budget = 0.6 * static_cast<double>(g->l2_bytes ? g->l2_bytes : (64u << 20));
+    std::vector<size_t> order(blocks.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return blocks[a].cls != blocks[b].cls ? blocks[a].cls < blocks[b].cls : blocks[a].w.L > blocks[b].w.L;
+    });
+    {
+        std::vector<WinBlock> sorted;
+        std::vector<int32_t> h;
+        for (size_t q : order) {
+            WinBlock b = blocks[q];
+            b.first = static_cast<int64_t>(sorted.size()) * B;
+            sorted.push_back(b);
+        }
+        blocks.swap(sorted);
+    }
+    std::vector<int32_t> h_src(blocks.size() * B, -1);
+    for (size_t q = 0; q < order.size(); ++q)
+        std::copy(block_src[order[q]].begin(), block_src[order[q]].end(), h_src.begin() + static_cast<int64_t>(q) * B);
+    // super-blocks: consecutive blocks of one class within a memory budget per
+    // ping-pong buffer (the windows of one launch need not share L2: a
+    // launch's CTAs run slice after slice)
+    size_t free_b = 0, total_b = 0;
+    SC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = std::max(static_cast<double>(R.slice_bytes),
+                                   std::min(4.0 * (1ull << 30), 0.125 * static_cast<double>(free_b)));
     const int max_sl = R.o->max_slices > 0 ? std::min(R.o->max_slices, 65535) : 65535;
     std::vector<size_t> sb_begin;
     size_t need = 0;
-    {
-        size_t i = 0;
-        while (i < blocks.size()) {
-            sb_begin.push_back(i);
-            double bytes = 0.0;
-            int64_t off = 0;
-            size_t j = i;
-            while (j < blocks.size() && static_cast<int>(j - i) < max_sl && blocks[j].L == blocks[i].L) {
-                const double add = 2.0 * static_cast<double>(blocks[j].w.rows) * B * elem;
-                if (j > i && bytes + add > budget) break;
-                bytes += add;
-                blocks[j].w.xoff = off;
-                off += static_cast<int64_t>(blocks[j].w.rows) * B;
-                ++j;
-            }
-            need = std::max(need, static_cast<size_t>(off) * elem);
-            i = j;
+    for (size_t i = 0; i < blocks.size();) {
+        sb_begin.push_back(i);
+        double bytes = 0.0;
+        int64_t off = 0;
+        size_t j = i;
+        while (j < blocks.size() && static_cast<int>(j - i) < max_sl && blocks[j].cls == blocks[i].cls) {
+            const double add = static_cast<double>(blocks[j].w.rows) * B * elem;
+            if (j > i && bytes + add > budget) break;
+            bytes += add;
+            blocks[j].w.xoff = off;
+            off += static_cast<int64_t>(blocks[j].w.rows) * B;
+            ++j;
         }
-        sb_begin.push_back(blocks.size());
+        need = std::max(need, static_cast<size_t>(off) * elem);
+        i = j;
     }
+    sb_begin.push_back(blocks.size());
     std::vector<SliceWin> h_win(blocks.size());
     for (size_t i = 0; i < blocks.size(); ++i) h_win[i] = blocks[i].w;
     g->src_list.reserve(h_src.size());
@@ -765,9 +799,10 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemcpyAsync(g->win_list.get(), h_win.data(), h_win.size() * sizeof(SliceWin), cudaMemcpyHostToDevice, s));
     const SliceWin *d_win = reinterpret_cast<const SliceWin *>(g->win_list.get());
-    if (R.time_kernels) {
+    const bool timed = R.time_kernels && !R.capture;
+    if (timed) {
         int64_t total_hops = 0;
-        for (size_t q = 0; q + 1 < sb_begin.size(); ++q) total_hops += std::max(blocks[sb_begin[q]].L - 1, 0);
+        for (size_t q = 0; q + 1 < sb_begin.size(); ++q) total_hops += blocks[sb_begin[q]].w.L;
         while (static_cast<int64_t>(g->hop_events.size()) < 2 * (R.hop_launches + total_hops)) {
             cudaEvent_t e;
             SC_CUDA(cudaEventCreate(&e));
@@ -776,11 +811,28 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     }
     const int rpc = light_rows_per_cta(R.prec, B, R.vpl);
     const auto &hrp = g->h_row_ptr;
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is replayed on the caller's
+    struct StreamGuard {
+        cudaStream_t c = nullptr;
+        ~StreamGuard() {
+            if (c) cudaStreamDestroy(c);
+        }
+    } cs;
+    cudaStream_t is = s;
+    if (R.capture) {
+        SC_CUDA(cudaStreamSynchronize(s));
+        SC_CUDA(cudaStreamCreateWithFlags(&cs.c, cudaStreamNonBlocking));
+        is = cs.c;
+    }
+    CaptureGuard cap{is};
+    if (R.capture) {
+        SC_CUDA(cudaStreamBeginCapture(is, cudaStreamCaptureModeThreadLocal));
+        cap.open = true;
+    }
     for (size_t q = 0; q + 1 < sb_begin.size(); ++q) {
         const size_t b0 = sb_begin[q], b1 = sb_begin[q + 1];
-        const int used = static_cast<int>(b1 - b0);
-        const int32_t L = blocks[b0].L;
-        const int nsrc = used * B;
+        const int32_t Lmax = blocks[b0].w.L;
         const int32_t *src = g->src_list.get() + blocks[b0].first;
         const SliceWin *win = d_win + b0;
         size_t bytes = 0;
@@ -788,44 +840,64 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             bytes += static_cast<size_t>(blocks[b].w.rows) * B * elem;
             int32_t cnt = 0;
             for (int64_t t = blocks[b].first; t < blocks[b].first + B; ++t) cnt += h_src[t] >= 0;
-            R.ell_min_src = std::min(R.ell_min_src, L);
-            R.ell_max_src = std::max(R.ell_max_src, L);
-            R.source_hops += static_cast<int64_t>(L) * cnt;
+            R.ell_min_src = std::min(R.ell_min_src, blocks[b].w.L);
+            R.ell_max_src = std::max(R.ell_max_src, blocks[b].w.L);
+            R.source_hops += static_cast<int64_t>(blocks[b].w.L) * cnt;
+            R.hops += blocks[b].w.L;
         }
-        if (L == 0) continue;
         void *xa = g->xa.get(), *xb = g->xb.get();
-        SC_CUDA(cudaMemsetAsync(xa, 0, bytes, s));
-        SC_CUDA(cudaMemsetAsync(xb, 0, bytes, s));
-        launch_first_or_gather(g, R.prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, R.rec, s, win);
+        SC_CUDA(cudaMemsetAsync(xa, 0, bytes, is));
+        SC_CUDA(cudaMemsetAsync(xb, 0, bytes, is));
+        launch_first_or_gather(g, R.prec, B, true, xa, src, static_cast<int>(b1 - b0) * B, nullptr, 1, nullptr,
+                               nullptr, nullptr, R.rec, is, win);
         R.launches += 1;
-        for (int32_t ell = 2; ell <= L; ++ell) {
+        size_t active = b1 - b0;
+        for (int32_t ell = 2; ell <= Lmax; ++ell) {
+            while (active > 0 && blocks[b0 + active - 1].w.L < ell - 1) --active;
             int ctas = 0;
             double hop_bytes = 0.0;
-            for (size_t b = b0; b < b1; ++b) {
+            for (size_t b = b0; b < b0 + active; ++b) {
+                if (blocks[b].w.L < ell) continue;
                 int32_t lo, hi;
                 window_rows(blocks[b].w, beta, ell, &lo, &hi);
                 ctas = std::max(ctas, blocks[b].w.heavy_cnt + ceil_div(hi - lo, rpc));
                 hop_bytes += 4.0 * (hrp[hi] - hrp[lo]) + 4.0 * (hi - lo + 1) +
                              (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * (hi - lo) + 2.0 * (hi - lo) * B * elem;
             }
-            HopLaunch h{xa, xb, used, src, nsrc, g->tau_entry.get(), ell - 1,
+            const int used = static_cast<int>(active);
+            HopLaunch h{xa, xb, used, src, used * B, g->tau_entry.get(), ell - 1,
                         g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
             h.win = win;
             h.ell = ell;
             h.beta = beta;
             h.win_ctas = ctas;
-            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
-            launch_hop(g, R.prec, B, R.vpl, h, s);
-            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], s));
+            if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], is));
+            launch_hop(g, R.prec, B, R.vpl, h, is);
+            if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], is));
             ++R.hop_launches;
             std::swap(xa, xb);
             R.launches += 1;
             R.alg_bytes += hop_bytes;
         }
-        launch_first_or_gather(g, R.prec, B, false, xa, src, nsrc, g->tau_entry.get(), L, g->acc_g.get(),
-                               g->acc_t1.get(), g->acc_t2.get(), R.rec, s, win);
+        // final gather of the blocks that run all Lmax hops (a leading run)
+        size_t last = 0;
+        while (b0 + last < b1 && blocks[b0 + last].w.L == Lmax) ++last;
+        launch_first_or_gather(g, R.prec, B, false, xa, src, static_cast<int>(last) * B, g->tau_entry.get(), Lmax,
+                               g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, is, win);
         R.launches += 1;
-        R.hops += L;
+    }
+    if (R.capture) {
+        cudaGraph_t gr = nullptr;
+        cap.open = false;
+        SC_CUDA(cudaStreamEndCapture(is, &gr));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) SC_FAIL(SC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphLaunch(ex, s);
+        cudaGraphExecDestroy(ex);  // freed once the launch completes
+        if (e2 != cudaSuccess) SC_FAIL(SC_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e2));
+        R.graph_launches += 1;
     }
 }
 
@@ -1107,6 +1179,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->walks = R.walks;
         rep->edges_extended = static_cast<int32_t>(extended);
         rep->extension_rounds = rounds;
+        rep->windowed = use_win ? 1 : 0;
         rep->tt_min = plus ? (R.tt_min == INT32_MAX ? 0 : R.tt_min) : 0;
         rep->tt_max = plus ? R.tt_max : 0;
         rep->switch_tests = R.switch_tests;
@@ -1181,9 +1254,258 @@ void certified_lengths_impl(sc_graph *g, double eps, int precision, int32_t *per
     *cap_out = cap;
 }
 
+// ---------------------------------------------------------------------------
+// batched traversal over many independent graphs: their disjoint union is
+// propagated in windowed blocks (one graph per block, window = that graph's
+// rows), recorded into one CUDA graph
+// ---------------------------------------------------------------------------
+__global__ void k_offset_copy(int32_t *__restrict__ dst, const int32_t *__restrict__ src, int64_t count, int32_t add) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < count) dst[i] = src[i] + add;
+}
+
+// per-segment sums of x over [off[i], off[i + 1]) in a fixed order (one CTA each)
+__global__ void k_segment_sum(const double *__restrict__ x, const int64_t *__restrict__ off, double *__restrict__ out) {
+    __shared__ double sh[256];
+    const int64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    double acc = 0.0;
+    for (int64_t k = a + threadIdx.x; k < b; k += 256) acc += x[k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options *o_in, const int32_t *ell_per_graph,
+                       double *const *s_hat, sc_report *reports) {
+    if (!graphs || count < 1 || !s_hat) SC_FAIL(SC_ERR_INVALID_ARG, "need count >= 1 graphs and outputs");
+    sc_options o;
+    if (o_in) o = *o_in;
+    else sc_options_default(&o);
+    if (!(o.eps > 0.0 && o.eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1), got %g", o.eps);
+    if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
+    if (o.mode != SC_MODE_TGT) SC_FAIL(SC_ERR_UNSUPPORTED, "batches run TGT (Algorithm 2) only");
+    if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_FIXED)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "batches take the Eq. 6 or a fixed length");
+    if (o.ell_policy == SC_ELL_FIXED && o.ell_fixed < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_fixed < 0");
+    if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
+    if (o.rows_split == -1) SC_FAIL(SC_ERR_UNSUPPORTED, "the TMA-gather hop has no windowed form");
+    if (o.rows_split < -1 || o.rows_split == 3 || o.rows_split > 4) SC_FAIL(SC_ERR_INVALID_ARG, "lane split %d", o.rows_split);
+    if (o.block_width != 0 && o.block_width != 32 && o.block_width != 64 && o.block_width != 128)
+        SC_FAIL(SC_ERR_INVALID_ARG, "block width %d not in {32, 64, 128}", o.block_width);
+    const bool out_dev = (o.flags & SC_OUT_DEVICE) != 0;
+    const bool record_after = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
+    const int extra = record_after ? 2 : 0;
+    int dev = -1;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!graphs[i] || !s_hat[i]) SC_FAIL(SC_ERR_INVALID_ARG, "graph or output %d is NULL", i);
+        if (dev >= 0 && graphs[i]->device != dev) SC_FAIL(SC_ERR_INVALID_ARG, "graphs on different devices");
+        dev = graphs[i]->device;
+        if (ell_per_graph && ell_per_graph[i] < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_per_graph[%d] < 0", i);
+    }
+    cudaStream_t s = graphs[0]->stream;
+    cudaEvent_t ev0, ev1, ev2;
+    SC_CUDA(cudaEventCreate(&ev0));
+    SC_CUDA(cudaEventCreate(&ev1));
+    SC_CUDA(cudaEventCreate(&ev2));
+    struct EvGuard {
+        cudaEvent_t a, b, c;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaEventDestroy(c);
+        }
+    } evg{ev0, ev1, ev2};
+    SC_CUDA(cudaEventRecord(ev0, s));
+
+    // ---- per-graph lengths: an override, the fixed length, or Eq. 6 with the graph's own lambda*
+    std::vector<int32_t> ell(count);
+    std::vector<double> lam(count, 0.0);
+    std::vector<int64_t> n_off(count + 1, 0), k_off(count + 1, 0);
+    int32_t big = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        sc_graph *g = graphs[i];
+        SC_CUDA(cudaStreamSynchronize(g->stream));
+        const int32_t over = ell_per_graph ? ell_per_graph[i] : 0;
+        if (over > 0) {
+            ell[i] = over;
+        } else if (o.ell_policy == SC_ELL_FIXED) {
+            ell[i] = o.ell_fixed;
+        } else {
+            if (!g->has_lambda) {
+                sc_lambda l;
+                sc_status st = estimate_lambda_impl(g, nullptr, &l);
+                if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
+            }
+            if (g->bipartite || g->lam.lambda_star >= 1.0)
+                SC_FAIL(SC_ERR_UNSUPPORTED, "graph %d: lambda_star >= 1 (bipartite): give it a length in ell_per_graph", i);
+            lam[i] = g->lam.lambda_star;
+            g->tau_entry.reserve(g->nnz);
+            DevBuf<int32_t> ts;
+            ts.reserve(g->n);
+            tau_entries_device(g, o.eps, lam[i], g->tau_entry.get(), ts.get(), &ell[i]);
+        }
+        n_off[i + 1] = n_off[i] + g->n;
+        k_off[i + 1] = k_off[i] + g->nnz;
+        if (g->nnz > graphs[big]->nnz) big = i;
+    }
+    if (n_off[count] >= (int64_t(1) << 31) || k_off[count] >= (int64_t(1) << 31))
+        SC_FAIL(SC_ERR_INVALID_ARG, "the batch holds 2^31 nodes or entries or more");
+    const int32_t N = static_cast<int32_t>(n_off[count]);
+    const int64_t NNZ = k_off[count];
+
+    // ---- the disjoint union
+    std::unique_ptr<sc_graph> U(new sc_graph());
+    U->device = dev;
+    U->stream = s;
+    U->n = N;
+    U->nnz = NNZ;
+    U->num_sms = graphs[0]->num_sms;
+    U->l2_bytes = graphs[0]->l2_bytes;
+    U->row_ptr.reserve(N + 1);
+    U->col_idx.reserve(NNZ);
+    U->rev.reserve(NNZ);
+    U->inv_deg_f.reserve(N);
+    U->inv_deg_d.reserve(N);
+    U->h_row_ptr.resize(N + 1);
+    U->min_degree = INT32_MAX;
+    for (int32_t i = 0; i < count; ++i) {
+        const sc_graph *g = graphs[i];
+        const int32_t a = static_cast<int32_t>(n_off[i]), ka = static_cast<int32_t>(k_off[i]);
+        k_offset_copy<<<ceil_div(g->n, 256), 256, 0, s>>>(U->row_ptr.get() + a, g->row_ptr.get(), g->n, ka);
+        k_offset_copy<<<ceil_div(g->nnz, 256), 256, 0, s>>>(U->col_idx.get() + ka, g->col_idx.get(), g->nnz, a);
+        k_offset_copy<<<ceil_div(g->nnz, 256), 256, 0, s>>>(U->rev.get() + ka, g->rev.get(), g->nnz, ka);
+        SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(U->inv_deg_f.get() + a, g->inv_deg_f.get(), g->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        SC_CUDA(cudaMemcpyAsync(U->inv_deg_d.get() + a, g->inv_deg_d.get(), g->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int32_t r = 0; r < g->n; ++r) U->h_row_ptr[a + r] = g->h_row_ptr[r] + ka;
+        U->min_degree = std::min(U->min_degree, g->min_degree);
+        U->max_degree = std::max(U->max_degree, g->max_degree);
+    }
+    U->h_row_ptr[N] = static_cast<int32_t>(NNZ);
+    SC_CUDA(cudaMemcpyAsync(U->row_ptr.get() + N, &U->h_row_ptr[N], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    U->tau_entry.reserve(NNZ);
+    for (int32_t i = 0; i < count; ++i) fill_i32(U->tau_entry.get() + k_off[i], graphs[i]->nnz, ell[i], s);
+    const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 256;
+    ensure_row_order(U.get(), heavy_t);
+    int32_t beta = 0;
+    for (int32_t i = 0; i < count; ++i) beta = std::max(beta, ensure_bandwidth(graphs[i]));
+
+    // ---- block width and lane split, tuned on the largest graph of the batch
+    sc_graph *gb = graphs[big];
+    gb->tau_entry.reserve(gb->nnz);
+    fill_i32(gb->tau_entry.get(), gb->nnz, ell[big], gb->stream);
+    gb->acc_g.reserve(gb->nnz);
+    gb->acc_t1.reserve(gb->nnz);
+    gb->acc_t2.reserve(gb->nnz);
+    gb->status.reserve(4);
+    SC_CUDA(cudaMemsetAsync(gb->status.get(), 0, 4 * sizeof(int32_t), gb->stream));
+    ensure_row_order(gb, heavy_t);
+    const int fixV = o.rows_split == 0 ? -1 : o.rows_split;
+    const TuneResult tr = autotune(gb, o.precision, o.block_width, fixV, o.max_slices, ell[big] + extra,
+                                   GatherRec{0, nullptr, 0}, false, gb->stream);
+    SC_CUDA(cudaStreamSynchronize(gb->stream));
+
+    Run R;
+    R.g = U.get();
+    R.o = &o;
+    R.s = s;
+    R.prec = o.precision;
+    R.B = tr.B;
+    R.vpl = tr.vpl;
+    int32_t nmax = 0;
+    for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, graphs[i]->n);
+    R.slice_bytes = static_cast<size_t>(nmax) * R.B * elem_size(R.prec);
+    R.slices = 0;
+    R.plus = false;
+    R.time_kernels = false;
+    R.extra = extra;
+    R.rec = GatherRec{0, nullptr, 0};
+    R.ms_per_source_hop = tr.ms_per_source_hop;
+    R.capture = true;
+    U->acc_g.reserve(NNZ);
+    U->acc_t1.reserve(NNZ);
+    U->acc_t2.reserve(NNZ);
+    U->status.reserve(4);
+    SC_CUDA(cudaMemsetAsync(U->status.get(), 0, 4 * sizeof(int32_t), s));
+    k_reset_rows<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), nullptr, N, U->tau_entry.get(), 0, U->acc_g.get(),
+                                                U->acc_t1.get(), U->acc_t2.get(), nullptr, 0);
+    SC_LAUNCH_CHECK();
+    std::vector<int32_t> len(N), all(N);
+    std::iota(all.begin(), all.end(), 0);
+    std::vector<int32_t> seg_start(count + 1);
+    for (int32_t i = 0; i < count; ++i) {
+        std::fill(len.begin() + n_off[i], len.begin() + n_off[i + 1], ell[i]);
+        seg_start[i] = static_cast<int32_t>(n_off[i]);
+    }
+    seg_start[count] = N;
+    SC_CUDA(cudaEventRecord(ev1, s));
+    run_blocks_win(R, all, len, seg_start, beta);
+
+    // ---- combine, per-graph Foster sums, outputs
+    DevBuf<double> d_s, seg_sum;
+    DevBuf<int64_t> d_off;
+    d_s.reserve(NNZ);
+    seg_sum.reserve(count);
+    d_off.reserve(count + 1);
+    k_combine<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), U->col_idx.get(), U->rev.get(), U->inv_deg_d.get(),
+                                             U->acc_g.get(), U->acc_t1.get(), U->acc_t2.get(), N,
+                                             o.estimator == SC_EST_END_CORRECTED, record_after ? 1 : 0, 0.0, d_s.get(),
+                                             nullptr);
+    SC_CUDA(cudaMemcpyAsync(d_off.get(), k_off.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_segment_sum<<<count, 256, 0, s>>>(d_s.get(), d_off.get(), seg_sum.get());
+    SC_LAUNCH_CHECK();
+    SC_CUDA(cudaEventRecord(ev2, s));
+    std::vector<double> foster(count);
+    SC_CUDA(cudaMemcpyAsync(foster.data(), seg_sum.get(), count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    for (int32_t i = 0; i < count; ++i)
+        SC_CUDA(cudaMemcpyAsync(s_hat[i], d_s.get() + k_off[i], graphs[i]->nnz * sizeof(double),
+                                out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    int32_t h_status = 0;
+    SC_CUDA(cudaMemcpy(&h_status, U->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (h_status & 1) SC_FAIL(SC_ERR_TIMEOUT, "a bounded wait expired");
+    float prop_ms = 0.f, total_ms = 0.f;
+    SC_CUDA(cudaEventElapsedTime(&prop_ms, ev1, ev2));
+    SC_CUDA(cudaEventElapsedTime(&total_ms, ev0, ev2));
+    if (reports) {
+        for (int32_t i = 0; i < count; ++i) {
+            sc_report *rep = reports + i;
+            std::memset(rep, 0, sizeof(*rep));
+            rep->ell_global = ell[i];
+            rep->ell_min_source = ell[i] + extra;
+            rep->ell_max_source = ell[i] + extra;
+            rep->block_width = R.B;
+            rep->rows_split = R.vpl;
+            rep->slices = 0;
+            rep->blocks = (graphs[i]->n + R.B - 1) / R.B;
+            rep->source_hops = static_cast<int64_t>(graphs[i]->n) * (ell[i] + extra);
+            rep->foster_sum = 0.5 * foster[i];
+            rep->lambda_star = lam[i];
+            rep->windowed = 1;
+            // batch totals
+            rep->launches = R.launches + 4 + 3 * count;
+            rep->hops = R.hops;
+            rep->hop_launches = R.hop_launches;
+            rep->algorithmic_bytes = R.alg_bytes;
+            rep->hop_bytes = R.alg_bytes;
+            rep->propagate_ms = prop_ms;
+            rep->total_ms = total_ms;
+        }
+    }
+}
+
 }  // namespace sc
 
 extern "C" sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                                   sc_report *report) {
     return sc::guarded([&] { sc::all_edges_impl(g, opts, s_hat, tail_bound, report); });
+}
+
+extern "C" sc_status sc_batch_all_edges(sc_graph *const *graphs, int32_t count, const sc_options *opts,
+                                        const int32_t *ell_per_graph, double *const *s_hat, sc_report *reports) {
+    return sc::guarded([&] { sc::batch_impl(graphs, count, opts, ell_per_graph, s_hat, reports); });
 }

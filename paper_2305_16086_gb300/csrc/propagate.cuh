@@ -97,6 +97,7 @@ struct SliceWin {
     int32_t seg_lo, seg_hi;
     int32_t src_lo, src_hi;
     int32_t heavy_begin, heavy_cnt;  // the segment's heavy rows in the id-sorted heavy list
+    int32_t L;                       // hops of the slice's block: no rows are computed past it
 };
 
 __host__ __device__ __forceinline__ void window_rows(const SliceWin &w, int32_t beta, int32_t ell, int32_t *lo,
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         base = w.base;
         window_rows(w, a.beta, a.ell, &lo, &hi);
         n_heavy = w.heavy_cnt;
+        if (a.ell > w.L) lo = hi = 0, n_heavy = 0;  // the block is done: only its gather remains
     }
     // rows are addressed as (row - base) within the slice
     const uint4 *xp = reinterpret_cast<const uint4 *>(a.x_prev + slice_off) - static_cast<int64_t>(base) * L::V;

@@ -1,0 +1,74 @@
+"""The N > 1 path of bench.py (independent replicas, no data-path exchange):
+its max-over-ranks timing and whole-job value, run as two gloo ranks on the
+CPU; and the reference arm leaves ranks other than 0 without work."""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, _ = bench.dist_setup()
+        ms = 100.0 + 50.0 * rank  # the second replica is slower
+        slowest = bench.max_over_ranks(dist, ms, "cpu")
+        q.put((r, w, slowest, bench.replica_value(w, 1000, slowest)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_take_the_slowest_rank():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for r, (rank, w, slowest, value) in enumerate(got):
+        assert rank == r and w == world
+        assert slowest == 150.0
+        assert value == pytest.approx(2 * 1000 / 0.150)
+
+
+def test_single_process_needs_no_group():
+    import bench
+
+    assert bench.max_over_ranks(None, 12.5, "cpu") == 12.5
+    assert bench.replica_value(1, 2_000, 1000.0) == pytest.approx(2_000.0)
+
+
+def test_reference_arm_other_ranks_do_nothing():
+    import bench
+
+    class Args:
+        workload = "ba_200k"
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(Args(), 2, 1) is None
+    assert buf.getvalue() == ""

@@ -1,0 +1,94 @@
+"""The R-MAT workload (skewed degrees, ~18% degree-one nodes, lambda* ~ 0.71)
+at scale 15 (n ~ 24k, m ~ 442k): TGT+ with the Philox walk tail, the learned
+length and BF16 storage, each against the oracle.
+
+  * TGT+ (FP32 blocks, eps = 1e-3): sampled edges within eps of the exact
+    values (CG); bit-identical across runs for one seed;
+  * learned length (FP32): sampled edges within eps of the exact values, and
+    each value the truncated series (Eq. 2) at an odd length;
+  * BF16 storage: against the FP64 series oracle at the same length within
+    the BF16 tolerance 3e-2 (a measured variant, not an eps claim).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+from oracle import exact, learned, series
+
+pytestmark = pytest.mark.gpu
+
+TOL32, TOLBF16 = 2e-6, 3e-2
+
+
+@pytest.fixture(scope="module")
+def rmat15():
+    return gg.rmat(15, 16, seed=5)
+
+
+def _sample(g, count, seed):
+    rng = np.random.default_rng(seed)
+    k = rng.choice(g.nnz, count, replace=False)
+    rows = np.searchsorted(g.row_ptr, k, side="right") - 1
+    return k, rows, g.col_idx[k]
+
+
+def _graph(g):
+    from paper_2305_16086_gb300 import Graph
+
+    return Graph(g.row_ptr, g.col_idx)
+
+
+def test_rmat_tgt_plus_within_eps_and_deterministic(cuda_lib, rmat15):
+    g = rmat15
+    eps = 1e-3
+    k, i, j = _sample(g, 300, 1)
+    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, np.stack([i, j], axis=1))
+    with _graph(g) as G:
+        G.estimate_lambda()
+        s1, _, rep = G.all_edges(eps=eps, mode="tgt_plus", precision="fp32", seed=11)
+        s2, _, _ = G.all_edges(eps=eps, mode="tgt_plus", precision="fp32", seed=11)
+    assert np.array_equal(s1, s2)
+    assert np.max(np.abs(s1[k] - r)) <= eps
+    assert rep["tt_max"] <= rep["ell_global"]
+
+
+def test_rmat_learned_within_eps(cuda_lib, rmat15):
+    from paper_2305_16086_gb300 import binding
+
+    g = rmat15
+    eps = 1e-3
+    train = gg.rmat(13, 16, seed=6)
+    init = np.random.default_rng(4).normal(0, 0.2, learned.NPARAM).astype(np.float32)
+    with _graph(train) as Gt:
+        Gt.estimate_lambda()
+        model, curve = binding.mlp_train([Gt], init, epochs=300, lr=1e-2, eps=eps, precision="fp32")
+    assert curve[-1] < curve[0]
+    k, i, j = _sample(g, 200, 2)
+    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, np.stack([i, j], axis=1))
+    with _graph(g) as G:
+        G.estimate_lambda()
+        binding.mlp_load(G, model)
+        s, _, rep = G.all_edges(eps=eps, policy="learned", precision="fp32")
+        _, _, rep_g = G.all_edges(eps=eps, policy="global", precision="fp32")
+    assert np.max(np.abs(s[k] - r)) <= eps
+    cap = rep_g["ell_global"]
+    src = np.unique(np.concatenate([i, j]))
+    matched = np.zeros(k.size, dtype=bool)
+    for t in range(1, cap + 1, 2):
+        st, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, t, sources=src)
+        matched |= np.abs(s[k] - st[k]) <= TOL32
+    assert matched.all()
+    assert rep["source_hops"] <= rep_g["source_hops"]
+
+
+def test_rmat_bf16_storage_against_series(cuda_lib, rmat15):
+    g = rmat15
+    k, i, j = _sample(g, 200, 3)
+    src = np.unique(np.concatenate([i, j]))
+    with _graph(g) as G:
+        G.estimate_lambda()
+        sb, _, rep = G.all_edges(eps=1e-3, precision="bf16")
+        sf, _, _ = G.all_edges(eps=1e-3, precision="fp32")
+    ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, rep["ell_global"], sources=src)
+    assert np.max(np.abs(sf[k] - ref[k])) <= TOL32
+    assert np.max(np.abs(sb[k] - ref[k])) <= TOLBF16
