@@ -199,22 +199,28 @@ __device__ __forceinline__ const T *slice_column(const T *x, int32_t n, const Sl
 // heavy rows from the id-sorted list and its light rows in natural order over
 // the window, skipping the heavy ones; rows are stored from the slice's base.
 // ---------------------------------------------------------------------------
-template <typename T, int B, int VPL>
+template <typename T, int B, int VPL, bool WIN>
 __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a) {
     using L = Layout<T, B, VPL>;
     using Acc = typename L::Acc;
     const int32_t n = a.n;
     int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
     int32_t base = 0, lo = 0, hi = n, n_heavy = a.n_heavy;
-    if (a.win) {
+    if constexpr (WIN) {
         const SliceWin w = a.win[blockIdx.y];
         slice_off = w.xoff;
         base = w.base;
-        window_rows(w, a.beta, a.ell, &lo, &hi);
+        int64_t wa = w.seg_lo, wb = w.seg_hi;
+        if (a.beta > 0) {
+            wa = max(wa, static_cast<int64_t>(w.src_lo) - static_cast<int64_t>(a.ell) * a.beta);
+            wb = min(wb, static_cast<int64_t>(w.src_hi) + static_cast<int64_t>(a.ell) * a.beta);
+        }
+        lo = static_cast<int32_t>(wa);
+        hi = static_cast<int32_t>(wb);
         n_heavy = w.heavy_cnt;
         if (a.ell > w.L) lo = hi = 0, n_heavy = 0;  // the block is done: only its gather remains
     }
-    // rows are addressed as (row - base) within the slice
+    // rows are addressed as (row - base) within the slice (base = 0 unwindowed)
     const uint4 *xp = reinterpret_cast<const uint4 *>(a.x_prev + slice_off) - static_cast<int64_t>(base) * L::V;
     uint4 *xn = reinterpret_cast<uint4 *>(a.x_next + slice_off) - static_cast<int64_t>(base) * L::V;
     const int32_t *__restrict__ row_ptr = a.row_ptr;
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
             const int32_t s = a.src[q];
             if (s >= 0) {
                 int32_t sb;
-                const T *xs = slice_column<T, B>(a.x_prev, n, a.win, q, &sb);
+                const T *xs = slice_column<T, B>(a.x_prev, n, WIN ? a.win : nullptr, q, &sb);
                 gather_source<T, B>(row_ptr, col, xs, sb, s, a.tau, a.gather_ell, a.g, a.t1, a.t2, threadIdx.x,
                                     kSpmmWarps * 32, a.rec);
             }
@@ -241,8 +247,13 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         // ---------------- heavy row: chunks spread over the CTA ----------------
         constexpr int NGRP = kSpmmWarps * L::G;  // chunk slots per round
         __shared__ Acc part[NGRP][B];
-        const int32_t row = a.win ? a.heavy_ids[a.win[blockIdx.y].heavy_begin + cta] : a.row_order[cta];
-        if (row < lo || row >= hi) return;  // outside the window: X_l is zero there
+        int32_t row;
+        if constexpr (WIN) {
+            row = a.heavy_ids[a.win[blockIdx.y].heavy_begin + cta];
+            if (row < lo || row >= hi) return;  // outside the window: X_l is zero there
+        } else {
+            row = a.row_order[cta];
+        }
         const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
         const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
         Acc total = Acc(0);  // thread t < B owns column t
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
     // ---------------- light rows: one row per group of LG lanes ----------------
     const int64_t idx = (static_cast<int64_t>(cta - n_heavy) * kSpmmWarps + warp) * L::G + grp;
     int32_t row;
-    if (a.win) {
+    if constexpr (WIN) {
         if (idx >= hi - lo) return;
         row = lo + static_cast<int32_t>(idx);
     } else {
@@ -306,7 +317,9 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         row = a.row_order ? a.row_order[a.n_heavy + idx] : static_cast<int32_t>(idx);
     }
     const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
-    if (a.win && re - rb > a.heavy_t) return;  // a heavy row: its own CTA computes it
+    if constexpr (WIN) {
+        if (re - rb > a.heavy_t) return;  // a heavy row: its own CTA computes it
+    }
     Acc acc[L::NACC], chunk[L::NACC];
 #pragma unroll
     for (int q = 0; q < L::NACC; ++q) {
@@ -400,7 +413,8 @@ inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s, int win_ct
     a.light_ctas = ceil_div(a.n - a.n_heavy, kSpmmWarps * L::G);
     a.gather_ctas = a.gather_ell > 0 ? B : 0;
     dim3 grid(a.gather_ctas + (a.win ? win_ctas : a.n_heavy + a.light_ctas), slices);
-    k_spmm_hop<T, B, VPL><<<grid, kSpmmWarps * 32, 0, s>>>(a);
+    if (a.win) k_spmm_hop<T, B, VPL, true><<<grid, kSpmmWarps * 32, 0, s>>>(a);
+    else k_spmm_hop<T, B, VPL, false><<<grid, kSpmmWarps * 32, 0, s>>>(a);
 }
 
 }  // namespace sc
