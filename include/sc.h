@@ -243,6 +243,8 @@ typedef struct sc_report {
     int64_t source_hops;       /* sum over sources of hops traversed (the traversal's work) */
     int32_t extension_rounds;  /* learned policy: rerun rounds for edges that failed their bound */
     int32_t windowed;          /* 1 if the blocks ran windowed (SC_OPT_WINDOWS_*) */
+    int64_t walk_steps;        /* TGT+: walk steps taken (both walks of every pair) */
+    double walk_device_ms;     /* TGT+: device time of the walk launches (events) */
 } sc_report;
 
 /*

@@ -82,7 +82,8 @@ class Report(ctypes.Structure):
                 ("walks", ctypes.c_int64), ("edges_extended", ctypes.c_int32),
                 ("tt_min", ctypes.c_int32), ("tt_max", ctypes.c_int32),
                 ("switch_tests", ctypes.c_int32), ("switch_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
-                ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32)]
+                ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32),
+                ("walk_steps", ctypes.c_int64), ("walk_device_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

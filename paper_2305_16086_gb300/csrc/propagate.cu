@@ -26,6 +26,11 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
                         int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s);
 long long tgtplus_last_steps(sc_graph *g);
 constexpr int kCostRuleHops = 4;  // the cost rule tests the last hops only
+// TGT+ cost rule rates measured on GB300: a hop costs about this much per
+// source and CSR entry (BA-200k, FP32 blocks: 1.1 us per source over 4.0M
+// entries), a walk step (three dependent random reads) about kWalkStepNs
+constexpr double kHopNsPerSourceEntry = 2.75e-4;
+constexpr double kWalkStepNs = 0.5;
 void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_entry, int32_t *tau_src,
                         int32_t *ell_global_host);
 
@@ -533,7 +538,8 @@ struct Run {
     double ms_per_source_hop;
     bool capture = false;  // windowed loop: record into one CUDA graph
     // statistics
-    int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0, graph_launches = 0;
+    int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0, graph_launches = 0, walk_steps = 0;
+    double walk_device_ms = 0.0;
     double alg_bytes = 0.0, switch_ms = 0.0, walk_ms = 0.0;
     int32_t ell_min_src = INT32_MAX, ell_max_src = 0, tt_min = INT32_MAX, tt_max = 0, switch_tests = 0;
 };
@@ -610,10 +616,12 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
                 R.launches += 3;
-                const double hop_ms = R.ms_per_source_hop * used_slices * B;
+                // cost rule with fixed GB300 rates, so that the decision (and the
+                // result) depends on the graph and the seed only
+                const double hop_ns = kHopNsPerSourceEntry * static_cast<double>(nnz) * used_slices * B;
                 const bool go = paper_rule ? (lhs > rhs)
-                                           : (static_cast<double>(steps) * g->walk_step_ns * 1e-6 <
-                                              static_cast<double>(L - (ell - 1)) * hop_ms);
+                                           : (static_cast<double>(steps) * kWalkStepNs <
+                                              static_cast<double>(L - (ell - 1)) * hop_ns);
                 if (go) {
                     tt = ell - 1;
                     break;
@@ -651,8 +659,8 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 R.walks += pairs;
                 float wms = 0.f;
                 SC_CUDA(cudaEventElapsedTime(&wms, ev_w0, ev_w1));
-                const long long st = tgtplus_last_steps(g);
-                if (st > 1000) g->walk_step_ns = 0.5 * g->walk_step_ns + 0.5 * (1e6 * wms / static_cast<double>(st));
+                R.walk_steps += tgtplus_last_steps(g);
+                R.walk_device_ms += wms;
             }
         }
     }
@@ -1185,6 +1193,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->switch_tests = R.switch_tests;
         rep->switch_ms = R.switch_ms;
         rep->walk_ms = R.walk_ms;
+        rep->walk_steps = R.walk_steps;
+        rep->walk_device_ms = R.walk_device_ms;
     }
 }
 

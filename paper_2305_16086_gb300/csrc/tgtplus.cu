@@ -176,12 +176,6 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
     return pairs;
 }
 
-}  // namespace sc
-
-namespace sc {
-
-}  // namespace sc
-
-namespace sc {
 long long tgtplus_last_steps(sc_graph *g) { return g->last_walk_steps; }
+
 }  // namespace sc
