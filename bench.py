@@ -73,9 +73,9 @@ def recorded_traffic(config_key: str):
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("kernel_source_sha") != kernel_source_sha() or d.get("config_key") != config_key:
+    if d.get("kernel_source_sha") != kernel_source_sha():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("configs", {}).get(config_key)
 
 
 class ClockSampler:
