@@ -42,6 +42,9 @@ WORKLOADS = {
                     make=lambda gg: gg.barabasi_albert(200_000, 10, 1)),
     "tree_gnp_2k": dict(desc="uniform random tree + G(n,p), n=2000, avg degree 10, seed 0",
                         make=lambda gg: gg.tree_plus_gnp(2000, 10.0, 0)),
+    "lattice_1000": dict(desc="1000x1000 lattice, 5% of edges deleted outside a random spanning tree, seed 2 "
+                              "(bipartite, bandwidth 1000)",
+                         make=lambda gg: gg.perturbed_grid(1000, 1000, 0.05, 2)),
 }
 KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spmm_hop_ba200k_traffic.json")
@@ -223,16 +226,73 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args, world, rank):
+    """The many-graph workload through sc_batch_all_edges: 512 graphs, n
+    log-uniform in [1e3, 5e4] (G(n, 8/(n-1)) LCC, Barabasi-Albert m = 5 and
+    perturbed lattices in turn), FP32 blocks. Non-bipartite graphs take their
+    own Eq. 6 length; the lattices (no Eq. 6 length) take --grid-ell."""
+    import torch
+
+    import graphgen as gg
+    from paper_2305_16086_gb300 import Graph, binding
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    gs = gg.batch_graphs(512, 1000, 50000, base_seed=4)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    Gs = [Graph(g.row_ptr, g.col_idx, stream=stream) for g in gs]
+    ells = [args.grid_ell if g.meta.get("bipartite") else 0 for g in gs]
+    for G, e in zip(Gs, ells):
+        if e == 0:
+            G.estimate_lambda(allow_unconverged=True)
+    kw = dict(eps=args.eps, precision=args.precision, estimator="end_corrected")
+    for _ in range(args.warmup):
+        binding.batch_all_edges(Gs, ells, **kw)
+    torch.cuda.synchronize()
+    times, reps = [], None
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            _, reps = binding.batch_all_edges(Gs, ells, **kw)
+            times.append((time.perf_counter() - t) * 1e3)
+    m = sum(g.m for g in gs)
+    ms = statistics.mean(times)
+    lens = [r["ell_global"] for r in reps]
+    line = {"metric": "AESC edges/sec over a batch of 512 graphs (batched FP32, one CUDA-graph launch)",
+            "value": m / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "512 graphs, n log-uniform in [1000, 50000]: G(n, 8/(n-1)) LCC, "
+                                   "Barabasi-Albert m=5, perturbed lattices, seeds 4..515",
+                       "graphs": len(gs), "n_total": sum(g.n for g in gs), "m_total": m, "eps": args.eps,
+                       "lattice_length": args.grid_ell, "estimator": "end_corrected",
+                       "lengths_min_max": [min(lens), max(lens)], "block_width": reps[0]["block_width"],
+                       "hop_launches": reps[0]["hop_launches"], "generation_s": gen_s},
+            "roofline": {"bound": "hbm", "achieved": reps[0]["hop_bytes"] / (reps[0]["propagate_ms"] / 1e3) / 1e9,
+                         "peak": measured_peaks()[0], "unit": "GB/s", "note": "algorithmic bytes over the "
+                         "propagation time (whole CUDA graph, not one kernel)"},
+            "clocks": clk.summary(), "gpu_launches": int(reps[0]["launches"])}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    for G in Gs:
+        G.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ba_200k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ba_200k", choices=sorted(WORKLOADS) + ["batch_512"])
+    ap.add_argument("--grid-ell", type=int, default=1001, help="length of the lattices in batch_512")
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--policy", default="learned", choices=["learned", "global", "per_edge"])
+    ap.add_argument("--policy", default="learned", choices=["learned", "global", "per_edge", "fixed"])
+    ap.add_argument("--ell", type=int, default=0, help="length for --policy fixed")
+    ap.add_argument("--estimator", default="plain", choices=["plain", "end_corrected"])
     ap.add_argument("--no-arms", action="store_true")
     ap.add_argument("--block-width", type=int, default=0)
     ap.add_argument("--rows-split", type=int, default=0)
@@ -247,6 +307,9 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batch_512":
+        run_batch(args, world, rank)
         return
 
     import torch
@@ -264,7 +327,8 @@ def main():
     g = WORKLOADS[args.workload]["make"](gg)
     stream = torch.cuda.current_stream()
     run_kw = dict(eps=args.eps, precision=args.precision, policy=args.policy, block_width=args.block_width,
-                  rows_split=args.rows_split, heavy_threshold=args.heavy_threshold)
+                  rows_split=args.rows_split, heavy_threshold=args.heavy_threshold, ell_fixed=args.ell,
+                  estimator=args.estimator)
 
     G = Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), stream=stream)
     lam = G.estimate_lambda(allow_unconverged=True)
@@ -345,8 +409,9 @@ def main():
     # comparison arms: the plain global length in FP32 and FP64 (one warm-up, one timed step each)
     arms = {}
     if not args.no_arms:
-        for name, prec in (("global_fp32", "fp32"), ("global_fp64", "fp64")):
-            kw = dict(run_kw, policy="global", precision=prec)
+        arm_policy = "global" if args.policy == "learned" else args.policy
+        for name, prec in ((f"{arm_policy}_fp32", "fp32"), (f"{arm_policy}_fp64", "fp64")):
+            kw = dict(run_kw, policy=arm_policy, precision=prec)
             G.all_edges(out=out, **kw)
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -372,7 +437,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "m": g.m, "eps": args.eps,
-                   "policy": args.policy, "precision": f"{args.precision} blocks, fp64 accumulation",
+                   "policy": args.policy, "estimator": args.estimator, "windowed": bool(rep0["windowed"]),
+                   "precision": f"{args.precision} blocks, fp64 accumulation",
                    "batching": f"{rep0['slices']} block(s) of {rep0['block_width']} sources per launch, "
                                f"{rep0['blocks']} blocks",
                    "ell_global": rep0["ell_global"], "lambda_star": lam["lambda_star"],

@@ -169,17 +169,21 @@ void ensure_row_order(sc_graph *g, int32_t heavy_threshold) {
     g->heavy_threshold_cached = heavy_threshold;
 }
 
-// largest |i - j| over the rows' entries: one warp per row, maximum by atomics
+// largest |i - j| over the rows' entries: threads stride over the entries of
+// their rows (grid-stride), one atomic per CTA
 __global__ void k_bandwidth(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
                             int32_t *out) {
-    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= n) return;
+    __shared__ int32_t cta_m;
+    if (threadIdx.x == 0) cta_m = 0;
+    __syncthreads();
     int32_t m = 0;
-    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) m = max(m, abs(col[k] - r));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0 && m > 0) atomicMax(out, m);
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int32_t a = row_ptr[r], b = row_ptr[r + 1];
+        if (b > a) m = max(m, max(abs(col[a] - r), abs(col[b - 1] - r)));  // rows are sorted
+    }
+    atomicMax(&cta_m, m);
+    __syncthreads();
+    if (threadIdx.x == 0 && cta_m > 0) atomicMax(out, cta_m);
 }
 
 int32_t ensure_bandwidth(sc_graph *g) {
@@ -187,7 +191,8 @@ int32_t ensure_bandwidth(sc_graph *g) {
     DevBuf<int32_t> d;
     d.reserve(1);
     SC_CUDA(cudaMemsetAsync(d.get(), 0, sizeof(int32_t), g->stream));
-    k_bandwidth<<<ceil_div(g->n, 8), 256, 0, g->stream>>>(g->row_ptr.get(), g->col_idx.get(), g->n, d.get());
+    const int grid = std::max(1, std::min(ceil_div(g->n, 256), (g->num_sms > 0 ? g->num_sms : 148) * 4));
+    k_bandwidth<<<grid, 256, 0, g->stream>>>(g->row_ptr.get(), g->col_idx.get(), g->n, d.get());
     SC_LAUNCH_CHECK();
     int32_t h = 0;
     SC_CUDA(cudaMemcpyAsync(&h, d.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));

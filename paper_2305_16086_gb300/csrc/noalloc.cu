@@ -187,6 +187,9 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
     k_na_init<<<ceil_div(nnz, tb), tb, 0, s>>>(acc, tau, nnz, ell);
     k_na_sources<<<ceil_div(nsrc, tb), tb, 0, s>>>(src, nsrc, n);
     SC_LAUNCH_CHECK();
+    int dev = 0, num_sms = 0;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     for (int64_t first = 0; first < n && ell > 0; first += B) {
         const int nb = static_cast<int>(std::min<int64_t>(B, n - first));
         const int32_t *bsrc = src + first;
@@ -214,7 +217,7 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
             ha.t1 = nullptr;
             ha.t2 = nullptr;
             ha.rec = GatherRec{0, nullptr, 0};
-            launch_spmm_hop<double, B, 1>(ha, 1, s);
+            launch_spmm_hop<double, B, 1>(ha, 1, s, num_sms);
             std::swap(a, b);
         }
         k_gather<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,

@@ -135,11 +135,12 @@ struct HopLaunch {
     double *g, *t1, *t2;
     int32_t *status;  // TMA kernel: bounded-wait expiry flag
     GatherRec rec;
-    // windowed launch: per slice windows, the hop computed, the bandwidth and
-    // the largest heavy + light CTA count over the slices
+    // windowed launch: per slice windows, the hop computed, the bandwidth, and
+    // the largest heavy-row count and window (rows) over the slices
     const SliceWin *win = nullptr;
     int32_t ell = 0, beta = 0;
-    int win_ctas = 0;
+    int win_heavy = 0;
+    int64_t win_rows = 0;
 };
 
 // ---- TMA-gather variant (lane split value 0) --------------------------------
@@ -236,7 +237,7 @@ static void hop_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.beta = h.beta;
     a.heavy_ids = g->heavy_ids.get();
     a.heavy_t = g->heavy_threshold_cached;
-    launch_spmm_hop<T, B, VPL>(a, h.slices, s, h.win_ctas);
+    launch_spmm_hop<T, B, VPL>(a, h.slices, s, g->num_sms, h.win_heavy, h.win_rows);
 }
 
 // lane split 0 = the TMA-gather kernel; 1, 2, 4 = 16-byte vectors per lane of the SIMT kernel
@@ -329,11 +330,6 @@ void launch_first_or_gather(const sc_graph *g, int prec, int B, bool first, cons
     SC_LAUNCH_CHECK();
 }
 
-// rows one CTA of the SIMT hop kernel takes on the light path
-static int light_rows_per_cta(int prec, int B, int vpl) {
-    const int V = B * static_cast<int>(elem_size(prec)) / 16;  // 16-byte vectors per row
-    return kSpmmWarps * (32 / (V / vpl));
-}
 
 // blocks propagated per launch: both ping-pong blocks within ~60% of L2
 static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
@@ -817,7 +813,6 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             g->hop_events.push_back(e);
         }
     }
-    const int rpc = light_rows_per_cta(R.prec, B, R.vpl);
     const auto &hrp = g->h_row_ptr;
     // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is replayed on the caller's
@@ -862,13 +857,15 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
         size_t active = b1 - b0;
         for (int32_t ell = 2; ell <= Lmax; ++ell) {
             while (active > 0 && blocks[b0 + active - 1].w.L < ell - 1) --active;
-            int ctas = 0;
+            int heavy_max = 0;
+            int64_t rows_max = 0;
             double hop_bytes = 0.0;
             for (size_t b = b0; b < b0 + active; ++b) {
                 if (blocks[b].w.L < ell) continue;
                 int32_t lo, hi;
                 window_rows(blocks[b].w, beta, ell, &lo, &hi);
-                ctas = std::max(ctas, blocks[b].w.heavy_cnt + ceil_div(hi - lo, rpc));
+                heavy_max = std::max(heavy_max, blocks[b].w.heavy_cnt);
+                rows_max = std::max<int64_t>(rows_max, hi - lo);
                 hop_bytes += 4.0 * (hrp[hi] - hrp[lo]) + 4.0 * (hi - lo + 1) +
                              (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * (hi - lo) + 2.0 * (hi - lo) * B * elem;
             }
@@ -878,7 +875,8 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             h.win = win;
             h.ell = ell;
             h.beta = beta;
-            h.win_ctas = ctas;
+            h.win_heavy = heavy_max;
+            h.win_rows = rows_max;
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], is));
             launch_hop(g, R.prec, B, R.vpl, h, is);
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], is));

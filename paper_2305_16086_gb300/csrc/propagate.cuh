@@ -16,6 +16,8 @@
 // result is then scaled once by 1/d_x.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sc {
@@ -121,9 +123,9 @@ struct HopArgs {
     T *x_next;         // X_l
     int32_t n;
     // row schedule: row_order[0 .. n_heavy) are the rows of degree above the
-    // heavy threshold (one CTA each, longest first), the rest are the light
-    // rows in natural order for the row groups; row_order == nullptr means
-    // natural order with no heavy rows
+    // heavy threshold heavy_t (one CTA each, longest first); the row groups
+    // take every row in natural order and skip those (n_heavy = 0: no heavy
+    // rows, row_order unused)
     const int32_t *row_order;
     int32_t n_heavy;
     int32_t light_ctas;
@@ -306,61 +308,77 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         return;
     }
 
-    // ---------------- light rows: one row per group of LG lanes ----------------
-    const int64_t idx = (static_cast<int64_t>(cta - n_heavy) * kSpmmWarps + warp) * L::G + grp;
-    int32_t row;
-    if constexpr (WIN) {
-        if (idx >= hi - lo) return;
-        row = lo + static_cast<int32_t>(idx);
-    } else {
-        if (idx >= n - a.n_heavy) return;
-        row = a.row_order ? a.row_order[a.n_heavy + idx] : static_cast<int32_t>(idx);
+    // ---------------- light rows: one row per group of LG lanes at a time ----------------
+    // The light CTAs stride over the rows (a few rows per group, about 32 CTAs
+    // per SM in the grid) and load the next row's bounds while the current
+    // row's gathers are in flight.
+    // Rows are taken in natural order; the heavy ones (their own CTAs above)
+    // are skipped.
+    if (cta - n_heavy >= a.light_ctas) return;
+    const int64_t nlight = WIN ? static_cast<int64_t>(hi - lo) : static_cast<int64_t>(n);
+    const int64_t stride = static_cast<int64_t>(a.light_ctas) * kSpmmWarps * L::G;
+    const int32_t row0 = WIN ? lo : 0;
+    const int32_t heavy_t = n_heavy > 0 || WIN ? a.heavy_t : 0x7fffffff;
+    int64_t idx = (static_cast<int64_t>(cta - n_heavy) * kSpmmWarps + warp) * L::G + grp;
+    auto row_at = [&](int64_t i) -> int32_t { return row0 + static_cast<int32_t>(i); };
+    int32_t row = 0, rb = 0, re = 0;
+    if (idx < nlight) {
+        row = row_at(idx);
+        rb = row_ptr[row];
+        re = row_ptr[row + 1];
     }
-    const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
-    if constexpr (WIN) {
-        if (re - rb > a.heavy_t) return;  // a heavy row: its own CTA computes it
-    }
-    Acc acc[L::NACC], chunk[L::NACC];
+    for (; idx < nlight; idx += stride) {
+        const int32_t cur = row, cb = rb, ce = re;
+        if (idx + stride < nlight) {
+            row = row_at(idx + stride);
+            rb = row_ptr[row];
+            re = row_ptr[row + 1];
+        }
+        if (ce - cb > heavy_t) continue;  // a heavy row: its own CTA computes it
+        Acc acc[L::NACC], chunk[L::NACC];
 #pragma unroll
-    for (int q = 0; q < L::NACC; ++q) {
-        acc[q] = Acc(0);
-        chunk[q] = Acc(0);
-    }
-    int32_t k = rb;
-    for (; k + L::U <= re; k += L::U) {
-        int32_t j[L::U];
+        for (int q = 0; q < L::NACC; ++q) {
+            acc[q] = Acc(0);
+            chunk[q] = Acc(0);
+        }
+        int32_t k = cb;
+        for (; k + L::U <= ce; k += L::U) {
+            int32_t j[L::U];
 #pragma unroll
-        for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
-        uint4 v[L::U][VPL];
+            for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
+            uint4 v[L::U][VPL];
 #pragma unroll
-        for (int u = 0; u < L::U; ++u)
+            for (int u = 0; u < L::U; ++u)
 #pragma unroll
-            for (int p = 0; p < VPL; ++p) v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
+                for (int p = 0; p < VPL; ++p)
+                    v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
 #pragma unroll
-        for (int u = 0; u < L::U; ++u)
+            for (int u = 0; u < L::U; ++u)
 #pragma unroll
-            for (int p = 0; p < VPL; ++p) vadd(chunk + p * L::E, v[u][p], T());
-        if (((k + L::U - rb) % kChunk) == 0) {  // a chunk of 32 positions is complete
+                for (int p = 0; p < VPL; ++p) vadd(chunk + p * L::E, v[u][p], T());
+            if (((k + L::U - cb) % kChunk) == 0) {  // a chunk of 32 positions is complete
 #pragma unroll
-            for (int q = 0; q < L::NACC; ++q) {
-                acc[q] += chunk[q];
-                chunk[q] = Acc(0);
+                for (int q = 0; q < L::NACC; ++q) {
+                    acc[q] += chunk[q];
+                    chunk[q] = Acc(0);
+                }
             }
         }
-    }
-    for (; k < re; ++k) {
-        const int32_t j = col[k];
+        for (; k < ce; ++k) {
+            const int32_t j = col[k];
+#pragma unroll
+            for (int p = 0; p < VPL; ++p)
+                vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
+        }
+#pragma unroll
+        for (int q = 0; q < L::NACC; ++q) acc[q] += chunk[q];
+        const Acc sc = a.inv_deg[cur];
+#pragma unroll
+        for (int q = 0; q < L::NACC; ++q) acc[q] *= sc;
 #pragma unroll
         for (int p = 0; p < VPL; ++p)
-            vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
+            xn[static_cast<int64_t>(cur) * L::V + gl + p * L::LG] = vpack(acc + p * L::E, T());
     }
-#pragma unroll
-    for (int q = 0; q < L::NACC; ++q) acc[q] += chunk[q];
-    const Acc sc = a.inv_deg[row];
-#pragma unroll
-    for (int q = 0; q < L::NACC; ++q) acc[q] *= sc;
-#pragma unroll
-    for (int p = 0; p < VPL; ++p) xn[static_cast<int64_t>(row) * L::V + gl + p * L::LG] = vpack(acc + p * L::E, T());
 }
 
 // X_1 = P e_s for each source s of the launch (Alg. 2 line 2 followed by the
@@ -405,14 +423,27 @@ constexpr int light_rows_per_cta() {
     return kSpmmWarps * Layout<T, B, VPL>::G;
 }
 
-// launch helper: one hop over `slices` slices, optionally gathering X_{l-1};
-// a windowed launch passes the largest heavy + light CTA count of its slices
+// light CTAs of a launch: enough for one row per group, at most kLightCtasPerSm
+// per SM (each group then takes a few rows in turn)
+constexpr int kLightCtasPerSm = 32;
+
+inline int light_ctas_for(int64_t rows, int rows_per_cta, int num_sms) {
+    const int64_t need = (rows + rows_per_cta - 1) / rows_per_cta;
+    const int64_t cap = static_cast<int64_t>(num_sms > 0 ? num_sms : 148) * kLightCtasPerSm;
+    return static_cast<int>(std::max<int64_t>(std::min(need, cap), 1));
+}
+
+// launch helper: one hop over `slices` slices, optionally gathering X_{l-1}.
+// Unwindowed: the light rows are n - n_heavy. Windowed: win_heavy is the
+// largest heavy-row count and win_rows the largest window of the slices.
 template <typename T, int B, int VPL>
-inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s, int win_ctas = 0) {
+inline void launch_spmm_hop(HopArgs<T> a, int slices, cudaStream_t s, int num_sms, int win_heavy = 0,
+                            int64_t win_rows = 0) {
     using L = Layout<T, B, VPL>;
-    a.light_ctas = ceil_div(a.n - a.n_heavy, kSpmmWarps * L::G);
+    constexpr int rpc = kSpmmWarps * L::G;
+    a.light_ctas = light_ctas_for(a.win ? win_rows : a.n, rpc, num_sms);
     a.gather_ctas = a.gather_ell > 0 ? B : 0;
-    dim3 grid(a.gather_ctas + (a.win ? win_ctas : a.n_heavy + a.light_ctas), slices);
+    dim3 grid(a.gather_ctas + (a.win ? win_heavy : a.n_heavy) + a.light_ctas, slices);
     if (a.win) k_spmm_hop<T, B, VPL, true><<<grid, kSpmmWarps * 32, 0, s>>>(a);
     else k_spmm_hop<T, B, VPL, false><<<grid, kSpmmWarps * 32, 0, s>>>(a);
 }

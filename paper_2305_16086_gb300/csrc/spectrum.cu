@@ -22,38 +22,45 @@ namespace sc {
 // ---------------------------------------------------------------------------
 // A3: truncation length per CSR entry
 // ---------------------------------------------------------------------------
-// one warp per row: the lanes take the row's entries (hub rows are long)
+// one warp per row (grid-stride over rows): the lanes take the row's entries
+// (hub rows are long); the longest length goes through one atomic per CTA
 __global__ void k_tau_entries(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
                               double eps, double lam, int32_t *__restrict__ tau, int32_t *__restrict__ tau_src,
                               int32_t *ell_global) {
-    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ int32_t cta_best;
+    if (threadIdx.x == 0) cta_best = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    if (r >= n) return;
-    const double di = static_cast<double>(row_ptr[r + 1] - row_ptr[r]);
     const double denom = __dmul_rn(eps, __dsub_rn(1.0, __dmul_rn(lam, lam)));
     const double log_inv_lam = log(__ddiv_rn(1.0, lam));
-    int32_t best = 0;
-    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
-        const int32_t j = col[k];
-        const double dj = static_cast<double>(row_ptr[j + 1] - row_ptr[j]);
-        // X_e = 1/d_i + 1/d_j - 2/(d_i d_j), evaluated left to right without contraction
-        const double xe = __dsub_rn(__dadd_rn(__ddiv_rn(1.0, di), __ddiv_rn(1.0, dj)), __ddiv_rn(2.0, __dmul_rn(di, dj)));
-        int32_t t = 1;
-        if (xe > 0.0 && lam > 0.0) {
-            const double val = __dsub_rn(__ddiv_rn(log(__ddiv_rn(xe, denom)), log_inv_lam), 1.0);
-            const double f = ceil(val);
-            if (f > 1.0) t = f > 2.0e9 ? 2000000001 : static_cast<int32_t>(f);
+    int32_t warp_best = 0;
+    for (int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += gridDim.x * (blockDim.x >> 5)) {
+        const double di = static_cast<double>(row_ptr[r + 1] - row_ptr[r]);
+        int32_t best = 0;
+        for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+            const int32_t j = col[k];
+            const double dj = static_cast<double>(row_ptr[j + 1] - row_ptr[j]);
+            // X_e = 1/d_i + 1/d_j - 2/(d_i d_j), evaluated left to right without contraction
+            const double xe =
+                __dsub_rn(__dadd_rn(__ddiv_rn(1.0, di), __ddiv_rn(1.0, dj)), __ddiv_rn(2.0, __dmul_rn(di, dj)));
+            int32_t t = 1;
+            if (xe > 0.0 && lam > 0.0) {
+                const double val = __dsub_rn(__ddiv_rn(log(__ddiv_rn(xe, denom)), log_inv_lam), 1.0);
+                const double f = ceil(val);
+                if (f > 1.0) t = f > 2.0e9 ? 2000000001 : static_cast<int32_t>(f);
+            }
+            if ((t & 1) == 0) t += 1;
+            tau[k] = t;
+            best = max(best, t);
         }
-        if ((t & 1) == 0) t += 1;
-        tau[k] = t;
-        best = max(best, t);
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) {
-        tau_src[r] = best;
-        atomicMax(ell_global, best);
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) tau_src[r] = best;
+        warp_best = max(warp_best, best);
     }
+    if (lane == 0) atomicMax(&cta_best, warp_best);
+    __syncthreads();
+    if (threadIdx.x == 0 && cta_best > 0) atomicMax(ell_global, cta_best);
 }
 
 void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_entry, int32_t *tau_src,
@@ -62,7 +69,8 @@ void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_e
     g->status.reserve(4);
     cudaStream_t s = g->stream;
     SC_CUDA(cudaMemsetAsync(g->status.get(), 0, sizeof(int32_t), s));
-    k_tau_entries<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->n, eps,
+    const int grid = std::max(1, std::min(ceil_div(g->n, 8), (g->num_sms > 0 ? g->num_sms : 148) * 8));
+    k_tau_entries<<<grid, 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->n, eps,
                                                        std::max(lam_star, 0.0), tau_entry, tau_src, g->status.get());
     SC_LAUNCH_CHECK();
     SC_CUDA(cudaMemcpyAsync(ell_global_host, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
