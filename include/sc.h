@@ -165,7 +165,8 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
 /* storage precision of the propagated probability block */
 #define SC_PREC_FP64 0
 #define SC_PREC_FP32 1
-#define SC_PREC_BF16 2      /* bf16 storage, fp32 accumulation */
+#define SC_PREC_BF16 2      /* bf16 storage from hop opts.bf16_from_hop on (fp32 storage before),
+                               fp32 accumulation */
 
 /* estimator */
 #define SC_EST_PLAIN 0          /* S_tau of Eq. (2) */
@@ -197,19 +198,23 @@ typedef struct sc_options {
     int32_t ell_fixed;        /* tau for SC_ELL_FIXED (>= 0) */
     int32_t estimator;        /* SC_EST_* */
     int32_t block_width;      /* sources per block B in {32, 64, 128}; 0 = choose automatically */
-    int32_t rows_split;       /* 16-byte vectors per lane in {1, 2, 4}; 0 = choose automatically */
-    int32_t heavy_threshold;  /* rows above this degree are split over a whole CTA (0 = 128) */
+    int32_t rows_split;       /* 16-byte vectors per lane in {1, 2, 4}; -1 = the TMA-gather kernel;
+                                 0 = choose automatically */
+    int32_t heavy_threshold;  /* rows above this degree are split over a whole CTA (0 = 256) */
     int32_t max_slices;       /* blocks propagated together in one launch (0 = fit the L2 budget) */
-    uint32_t flags;           /* SC_OUT_DEVICE | SC_OPT_RECORD_TAIL */
+    uint32_t flags;           /* SC_OUT_DEVICE | SC_OPT_* */
     uint64_t seed;            /* Philox key for TGT+ walks */
     double delta;             /* TGT+ failure probability (0 = 1/n, Section 5.1) */
     int32_t gamma;            /* CalChi candidates (Alg. 3), 0..16; default 10 when < 0 */
     int32_t switch_rule;      /* TGT+: SC_SWITCH_COST (default) or SC_SWITCH_PAPER (Eq. 14 as printed) */
-    int32_t reserved[6];
+    int32_t bf16_from_hop;    /* SC_PREC_BF16: X_l is stored in bf16 for l >= this hop and in fp32
+                                 before it, where the probabilities are large (0 = 8; 1 = every hop) */
+    int32_t reserved[5];
 } sc_options;
 
 /* TGT+ switch rules (when to stop the traversal and draw walks) */
-#define SC_SWITCH_COST 0   /* measured cost: walks once their time is below the remaining hops' time */
+#define SC_SWITCH_COST 0   /* cost: walks once their predicted time (fixed GB300 rates per walk step
+                              and per source-hop entry) is below the remaining hops' */
 #define SC_SWITCH_PAPER 1  /* Eq. 14: frontier volume above the sum of walk counts */
 
 /* fills *opts with defaults: eps 1e-3, TGT, FP32, global length, plain estimator, auto B */

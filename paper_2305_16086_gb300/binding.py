@@ -67,7 +67,8 @@ class Options(ctypes.Structure):
                 ("rows_split", ctypes.c_int32), ("heavy_threshold", ctypes.c_int32),
                 ("max_slices", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("delta", ctypes.c_double), ("gamma", ctypes.c_int32),
-                ("switch_rule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("switch_rule", ctypes.c_int32), ("bf16_from_hop", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Report(ctypes.Structure):
@@ -258,7 +259,7 @@ class Graph:
     def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
                 record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
-                switch="cost", windows=None) -> Options:
+                switch="cost", windows=None, bf16_from_hop=0) -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
         o.eps = eps
@@ -280,6 +281,7 @@ class Graph:
         if gamma is not None:
             o.gamma = gamma
         o.switch_rule = {"cost": 0, "paper": 1}[switch]
+        o.bf16_from_hop = bf16_from_hop
         return o
 
     def all_edges(self, out=None, tail_bound=None, **kw):

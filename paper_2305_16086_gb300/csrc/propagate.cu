@@ -531,7 +531,7 @@ struct Run {
     double log2md;
     int extra;  // hops beyond the per-source length (records of tau+1, tau+2)
     GatherRec rec;
-    double ms_per_source_hop;
+    int32_t h0 = 0x7fffffff;  // SC_PREC_BF16: first hop stored in bf16 (fp32 before)
     bool capture = false;  // windowed loop: record into one CUDA graph
     // statistics
     int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0, graph_launches = 0, walk_steps = 0;
@@ -539,6 +539,46 @@ struct Run {
     double alg_bytes = 0.0, switch_ms = 0.0, walk_ms = 0.0;
     int32_t ell_min_src = INT32_MAX, ell_max_src = 0, tt_min = INT32_MAX, tt_max = 0, switch_tests = 0;
 };
+
+// storage precision of X_ell
+static int prec_at(const Run &R, int32_t ell) {
+    return (R.prec == SC_PREC_BF16 && ell < R.h0) ? SC_PREC_FP32 : R.prec;
+}
+
+// bytes per stored value the block buffers are sized for
+static size_t alloc_elem(int prec, int32_t h0) {
+    return prec == SC_PREC_BF16 && h0 > 1 ? 4 : elem_size(prec);
+}
+
+static int32_t bf16_first_hop(const sc_options &o) {
+    return o.precision == SC_PREC_BF16 ? (o.bf16_from_hop > 0 ? o.bf16_from_hop : 8) : 0x7fffffff;
+}
+
+// X_ell to bf16: fp32 values rounded to nearest (the rounding of the bf16 hop kernel's store)
+__global__ void k_f32_to_bf16(const float4 *__restrict__ in, uint2 *__restrict__ out, int64_t count4) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= count4) return;
+    const float4 v = in[i];
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    out[i] = make_uint2(*reinterpret_cast<uint32_t *>(&a), *reinterpret_cast<uint32_t *>(&b));
+}
+
+// one hop from X_{ell-1} (in xa) to X_ell (in xb) with the fused gather of
+// X_{ell-1}; at the hop where the storage turns to bf16 the hop runs in fp32
+// and its output is converted (xa / xb are swapped by the caller as usual:
+// on return X_ell is in the buffer the caller will read next)
+static void hop_mixed(const Run &R, HopLaunch h, int32_t ell, size_t elems, cudaStream_t s, void **xa, void **xb) {
+    const int pin = prec_at(R, ell - 1), pout = prec_at(R, ell);
+    launch_hop(R.g, pin, R.B, R.vpl, h, s);
+    if (pin != pout) {  // fp32 -> bf16 at hop h0: convert into the input buffer, now free
+        k_f32_to_bf16<<<ceil_div(static_cast<int64_t>(elems / 4), 256), 256, 0, s>>>(
+            static_cast<const float4 *>(h.xn), static_cast<uint2 *>(const_cast<void *>(h.xp)),
+            static_cast<int64_t>(elems / 4));
+        SC_LAUNCH_CHECK();
+        return;  // X_ell (bf16) is in *xa: no swap
+    }
+    std::swap(*xa, *xb);
+}
 
 static double wall_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -579,8 +619,11 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             cudaEventDestroy(b);
         }
     } evg{ev_w0, ev_w1};
-    const double hop_bytes_per_slice = 4.0 * nnz + 4.0 * (n + 1) + (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
-                                       2.0 * static_cast<double>(R.slice_bytes);
+    // algorithmic bytes of hop ell per slice: CSR, 1/d, read X_{ell-1}, write X_ell
+    auto hop_bytes_per_slice = [&](int32_t ell) {
+        return 4.0 * nnz + 4.0 * (n + 1) + (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
+               static_cast<double>(n) * B * (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
+    };
     for (int64_t sb = 0; sb < nsuper; ++sb) {
         const int64_t first = sb * S;
         const int nsrc = static_cast<int>(std::min<int64_t>(S, ns - first));
@@ -595,7 +638,8 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         const int32_t *src = g->src_list.get() + first;
         void *xa = g->xa.get(), *xb = g->xb.get();
         SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * R.slice_bytes, s));
-        launch_first_or_gather(g, R.prec, B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr, R.rec, s);
+        launch_first_or_gather(g, prec_at(R, 1), B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr,
+                               R.rec, s);
         R.launches += 1;  // the memset is not a kernel of ours
         int32_t tt = L;   // hops traversed; TGT+ may switch to walks earlier
         for (int ell = 2; ell <= L; ++ell) {
@@ -603,11 +647,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
                 // switch test after hop ell-1. Paper rule (Eq. 14): frontier volume against the
                 // sum of walk counts. Cost rule: predicted walk time against the time of the
-                // L - (ell-1) hops the walks would replace (hop time measured by the autotuner,
-                // walk-step time measured on earlier walk launches).
+                // L - (ell-1) hops the walks would replace.
                 long long lhs = 0, rhs = 0, steps = 0;
                 const double t0 = wall_ms();
-                tgtplus_check(g, R.prec, B, xa, used_slices, src, h_src.data() + first, nsrc, g->tau_entry.get(),
+                tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc, g->tau_entry.get(),
                               ell - 1, R.gamma, R.o->eps, R.log2md, &lhs, &rhs, &steps, s);
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
@@ -627,14 +670,13 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
                         g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
             if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
-            launch_hop(g, R.prec, B, R.vpl, h, s);
+            hop_mixed(R, h, ell, static_cast<size_t>(used_slices) * n * B, s, &xa, &xb);
             if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], s));
             ++R.hop_launches;
-            std::swap(xa, xb);
-            R.launches += 1;
-            R.alg_bytes += used_slices * hop_bytes_per_slice;
+            R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;
+            R.alg_bytes += used_slices * hop_bytes_per_slice(ell);
         }
-        launch_first_or_gather(g, R.prec, B, false, xa, src, nsrc, g->tau_entry.get(), tt, g->acc_g.get(),
+        launch_first_or_gather(g, prec_at(R, tt), B, false, xa, src, nsrc, g->tau_entry.get(), tt, g->acc_g.get(),
                                g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
         R.launches += 1;
         R.hops += tt;
@@ -646,7 +688,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 // Alg. 4 lines 12-17: walk tails from X_tt with the counts of the last check
                 const double t0 = wall_ms();
                 SC_CUDA(cudaEventRecord(ev_w0, s));
-                const long long pairs = tgtplus_walks(g, R.prec, B, xa, src, h_src.data() + first, nsrc,
+                const long long pairs = tgtplus_walks(g, prec_at(R, tt), B, xa, src, h_src.data() + first, nsrc,
                                                       g->tau_entry.get(), tt, R.o->seed, g->acc_g.get(), s);
                 SC_CUDA(cudaEventRecord(ev_w1, s));
                 SC_CUDA(cudaEventSynchronize(ev_w1));
@@ -705,7 +747,7 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     sc_graph *g = R.g;
     cudaStream_t s = R.s;
     const int B = R.B;
-    const size_t elem = elem_size(R.prec);
+    const size_t elem = alloc_elem(R.prec, R.h0);
     if (R.plus) SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ has no windowed form");
     sources.erase(std::remove_if(sources.begin(), sources.end(), [&](int32_t v) { return len[v] + R.extra <= 0; }),
                   sources.end());
@@ -851,7 +893,7 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
         void *xa = g->xa.get(), *xb = g->xb.get();
         SC_CUDA(cudaMemsetAsync(xa, 0, bytes, is));
         SC_CUDA(cudaMemsetAsync(xb, 0, bytes, is));
-        launch_first_or_gather(g, R.prec, B, true, xa, src, static_cast<int>(b1 - b0) * B, nullptr, 1, nullptr,
+        launch_first_or_gather(g, prec_at(R, 1), B, true, xa, src, static_cast<int>(b1 - b0) * B, nullptr, 1, nullptr,
                                nullptr, nullptr, R.rec, is, win);
         R.launches += 1;
         size_t active = b1 - b0;
@@ -867,7 +909,9 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
                 heavy_max = std::max(heavy_max, blocks[b].w.heavy_cnt);
                 rows_max = std::max<int64_t>(rows_max, hi - lo);
                 hop_bytes += 4.0 * (hrp[hi] - hrp[lo]) + 4.0 * (hi - lo + 1) +
-                             (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * (hi - lo) + 2.0 * (hi - lo) * B * elem;
+                             (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * (hi - lo) +
+                             static_cast<double>(hi - lo) * B *
+                                 (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
             }
             const int used = static_cast<int>(active);
             HopLaunch h{xa, xb, used, src, used * B, g->tau_entry.get(), ell - 1,
@@ -878,17 +922,16 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             h.win_heavy = heavy_max;
             h.win_rows = rows_max;
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], is));
-            launch_hop(g, R.prec, B, R.vpl, h, is);
+            hop_mixed(R, h, ell, bytes / elem, is, &xa, &xb);
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], is));
             ++R.hop_launches;
-            std::swap(xa, xb);
-            R.launches += 1;
+            R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;
             R.alg_bytes += hop_bytes;
         }
         // final gather of the blocks that run all Lmax hops (a leading run)
         size_t last = 0;
         while (b0 + last < b1 && blocks[b0 + last].w.L == Lmax) ++last;
-        launch_first_or_gather(g, R.prec, B, false, xa, src, static_cast<int>(last) * B, g->tau_entry.get(), Lmax,
+        launch_first_or_gather(g, prec_at(R, Lmax), B, false, xa, src, static_cast<int>(last) * B, g->tau_entry.get(), Lmax,
                                g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, is, win);
         R.launches += 1;
     }
@@ -918,6 +961,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     else sc_options_default(&o);
     if (!(o.eps > 0.0 && o.eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1), got %g", o.eps);
     if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
+    if (o.bf16_from_hop < 0) SC_FAIL(SC_ERR_INVALID_ARG, "bf16_from_hop %d < 0", o.bf16_from_hop);
     if (o.mode != SC_MODE_TGT && o.mode != SC_MODE_TGT_PLUS) SC_FAIL(SC_ERR_INVALID_ARG, "mode %d", o.mode);
     const bool plus = o.mode == SC_MODE_TGT_PLUS;
     if (plus && (o.estimator != SC_EST_PLAIN || (o.flags & SC_OPT_RECORD_TAIL) || o.ell_policy == SC_ELL_LEARNED))
@@ -1016,16 +1060,20 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     const bool use_win = !plus && o.rows_split != -1 && !(o.flags & SC_OPT_WINDOWS_OFF) &&
                          ((o.flags & SC_OPT_WINDOWS_FORCE) ||
                           2.0 * (Lmax + 1.0) * static_cast<double>(beta) + 128.0 < 0.5 * static_cast<double>(n));
-    const TuneResult tr = autotune(g, o.precision, o.block_width, fixV, o.max_slices, Lmax,
+    // a bf16 run whose early hops are fp32 is tuned (and its buffers sized) in fp32
+    const int32_t h0 = bf16_first_hop(o);
+    const int tune_prec = (o.precision == SC_PREC_BF16 && h0 > 1) ? SC_PREC_FP32 : o.precision;
+    const TuneResult tr = autotune(g, tune_prec, o.block_width, fixV, o.max_slices, Lmax,
                                    GatherRec{rec.mode, nullptr, 0}, !use_win, s);
     Run R;
     R.g = g;
     R.o = &o;
     R.s = s;
     R.prec = o.precision;
+    R.h0 = h0;
     R.B = tr.B;
     R.vpl = tr.vpl;
-    const size_t elem = elem_size(R.prec);
+    const size_t elem = alloc_elem(R.prec, R.h0);
     R.slice_bytes = static_cast<size_t>(n) * R.B * elem;
     R.slices = slices_for(g, R.B, elem, o.max_slices);
     R.plus = plus;
@@ -1035,7 +1083,6 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     R.log2md = std::log(2.0 * static_cast<double>(nnz / 2) / delta);
     R.extra = record_after ? 2 : 0;
     R.rec = rec;
-    R.ms_per_source_hop = tr.ms_per_source_hop;
     const int64_t nblocks_total = (static_cast<int64_t>(n) + R.B - 1) / R.B;
 
     g->xa.reserve(R.slices * R.slice_bytes);
@@ -1295,6 +1342,7 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     else sc_options_default(&o);
     if (!(o.eps > 0.0 && o.eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1), got %g", o.eps);
     if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
+    if (o.bf16_from_hop < 0) SC_FAIL(SC_ERR_INVALID_ARG, "bf16_from_hop %d < 0", o.bf16_from_hop);
     if (o.mode != SC_MODE_TGT) SC_FAIL(SC_ERR_UNSUPPORTED, "batches run TGT (Algorithm 2) only");
     if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_FIXED)
         SC_FAIL(SC_ERR_UNSUPPORTED, "batches take the Eq. 6 or a fixed length");
@@ -1413,7 +1461,9 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     SC_CUDA(cudaMemsetAsync(gb->status.get(), 0, 4 * sizeof(int32_t), gb->stream));
     ensure_row_order(gb, heavy_t);
     const int fixV = o.rows_split == 0 ? -1 : o.rows_split;
-    const TuneResult tr = autotune(gb, o.precision, o.block_width, fixV, o.max_slices, ell[big] + extra,
+    const int32_t h0 = bf16_first_hop(o);
+    const int tune_prec = (o.precision == SC_PREC_BF16 && h0 > 1) ? SC_PREC_FP32 : o.precision;
+    const TuneResult tr = autotune(gb, tune_prec, o.block_width, fixV, o.max_slices, ell[big] + extra,
                                    GatherRec{0, nullptr, 0}, false, gb->stream);
     SC_CUDA(cudaStreamSynchronize(gb->stream));
 
@@ -1426,13 +1476,13 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     R.vpl = tr.vpl;
     int32_t nmax = 0;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, graphs[i]->n);
-    R.slice_bytes = static_cast<size_t>(nmax) * R.B * elem_size(R.prec);
+    R.h0 = h0;
+    R.slice_bytes = static_cast<size_t>(nmax) * R.B * alloc_elem(R.prec, R.h0);
     R.slices = 0;
     R.plus = false;
     R.time_kernels = false;
     R.extra = extra;
     R.rec = GatherRec{0, nullptr, 0};
-    R.ms_per_source_hop = tr.ms_per_source_hop;
     R.capture = true;
     U->acc_g.reserve(NNZ);
     U->acc_t1.reserve(NNZ);

@@ -23,7 +23,7 @@
 namespace sc {
 
 constexpr int kChunk = 32;       // neighbours per sequential chunk
-constexpr int kSpmmWarps = 8;    // warps per CTA of the propagation kernel
+constexpr int kSpmmWarps = 4;    // warps per CTA of the propagation kernel
 
 template <typename T, int B, int VPL>
 struct Layout {
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
     }
 
     // ---------------- light rows: one row per group of LG lanes at a time ----------------
-    // The light CTAs stride over the rows (a few rows per group, about 32 CTAs
+    // The light CTAs stride over the rows (a few rows per group, about 64 CTAs
     // per SM in the grid) and load the next row's bounds while the current
     // row's gathers are in flight.
     // Rows are taken in natural order; the heavy ones (their own CTAs above)
@@ -425,7 +425,7 @@ constexpr int light_rows_per_cta() {
 
 // light CTAs of a launch: enough for one row per group, at most kLightCtasPerSm
 // per SM (each group then takes a few rows in turn)
-constexpr int kLightCtasPerSm = 32;
+constexpr int kLightCtasPerSm = 64;
 
 inline int light_ctas_for(int64_t rows, int rows_per_cta, int num_sms) {
     const int64_t need = (rows + rows_per_cta - 1) / rows_per_cta;

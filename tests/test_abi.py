@@ -53,7 +53,7 @@ LAYOUT_C = r"""
 int main(void) {
   printf("sc_graph_info %zu\nsc_lambda %zu\nsc_lambda_opts %zu\nsc_options %zu\nsc_report %zu\n",
          sizeof(sc_graph_info), sizeof(sc_lambda), sizeof(sc_lambda_opts), sizeof(sc_options), sizeof(sc_report));
-  F(sc_options, seed) F(sc_options, delta) F(sc_options, gamma) F(sc_options, flags)
+  F(sc_options, seed) F(sc_options, delta) F(sc_options, gamma) F(sc_options, flags) F(sc_options, bf16_from_hop)
   F(sc_report, algorithmic_bytes) F(sc_report, walks) F(sc_report, edges_extended) F(sc_report, total_ms)
   F(sc_report, hop_ms) F(sc_report, hop_launches) F(sc_report, hop_bytes) F(sc_report, tt_min) F(sc_report, tt_max) F(sc_report, switch_ms) F(sc_report, walk_ms) F(sc_report, source_hops) F(sc_report, extension_rounds) F(sc_report, windowed) F(sc_report, walk_steps) F(sc_report, walk_device_ms)
   F(sc_lambda, iterations) F(sc_graph_info, diameter_lb) F(sc_lambda_opts, seed)

@@ -92,3 +92,35 @@ def test_rmat_bf16_storage_against_series(cuda_lib, rmat15):
     ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, rep["ell_global"], sources=src)
     assert np.max(np.abs(sf[k] - ref[k])) <= TOL32
     assert np.max(np.abs(sb[k] - ref[k])) <= TOLBF16
+
+
+def test_bf16_from_hop_beyond_length_is_fp32(cuda_lib):
+    """With bf16 storage starting after the last hop every hop is fp32: the
+    values equal the fp32 run bit for bit."""
+    g = gg.tree_plus_gnp(1500, 10.0, 3)
+    with _graph(g) as G:
+        G.estimate_lambda()
+        s32, _, rep = G.all_edges(eps=1e-3, precision="fp32")
+        sb, _, _ = G.all_edges(eps=1e-3, precision="bf16", bf16_from_hop=rep["ell_global"] + 1)
+    assert np.array_equal(s32, sb)
+
+
+def test_rmat_bf16_from_hop_8_within_eps(cuda_lib, rmat15):
+    """BF16 storage from hop 8 on (fp32 before, where the probabilities are
+    large): within 5e-4 of the fp32 run on every edge (measured 2.9e-4 at
+    length 23; there is no a-priori bound) and within eps of the exact values
+    on sampled edges; every hop in bf16 is the 3e-2 variant."""
+    g = rmat15
+    eps = 1e-3
+    k, i, j = _sample(g, 200, 4)
+    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, np.stack([i, j], axis=1))
+    with _graph(g) as G:
+        G.estimate_lambda()
+        s32, _, rep = G.all_edges(eps=eps, precision="fp32")
+        s8, _, rep8 = G.all_edges(eps=eps, precision="bf16", bf16_from_hop=8)
+        s1, _, _ = G.all_edges(eps=eps, precision="bf16", bf16_from_hop=1)
+    assert rep["ell_global"] > 8
+    assert np.max(np.abs(s8 - s32)) <= 5e-4
+    assert np.max(np.abs(s8[k] - r)) <= eps
+    assert np.max(np.abs(s1 - s32)) <= TOLBF16
+    assert rep8["hop_bytes"] < rep["hop_bytes"]  # the bf16 hops move half the block bytes

@@ -130,3 +130,13 @@ def test_learned_policy_windowed_equals_full(cuda_lib):
     assert np.array_equal(s_w, s_f)
     # windowed blocks hold sources of one length, so no source runs extra hops
     assert rep_w["source_hops"] <= rep_f["source_hops"]
+
+
+def test_windowed_bf16_from_hop_equals_full(cuda_lib):
+    g = gg.perturbed_grid(50, 60, 0.05, 8)
+    with _graph(g) as G:
+        kw = dict(policy="fixed", ell_fixed=21, precision="bf16", bf16_from_hop=6, estimator="end_corrected")
+        s_w, _, rep_w = G.all_edges(windows=True, **kw)
+        s_f, _, rep_f = G.all_edges(windows=False, **kw)
+    assert rep_w["windowed"] == 1 and rep_f["windowed"] == 0
+    assert np.array_equal(s_w, s_f)
