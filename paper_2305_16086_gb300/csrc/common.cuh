@@ -150,6 +150,10 @@ struct sc_graph {
     int32_t bandwidth = -1;
     // per-slice windows of windowed launches
     sc::DevBuf<unsigned char> win_list;
+    // bit mask of the block's first-hop rows (hop 2 from the sources alone)
+    sc::DevBuf<uint32_t> mask;
+    // X_L at the sources (the last hop, computed where the gather reads it)
+    sc::DevBuf<double> last_diag;
     // row runs of about equal CSR entries, one per warp, for the TMA kernel
     sc::DevBuf<int32_t> part;
     int32_t nparts = 0;

@@ -196,9 +196,9 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
         double *a = xa, *b = xb;
         SC_CUDA(cudaMemsetAsync(a, 0, 8 * static_cast<size_t>(B) * n, s));
         k_first_hop<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, inv_deg, bsrc, nb, a, n, nullptr);
-        for (int hop = 2; hop <= ell; ++hop) {
+        for (int hop = 2; hop < ell; ++hop) {
             // natural row order, every row on the light path (no schedule array
-            // without allocation); the tail CTAs gather X_{hop-1}. hop - 1 <= ell
+            // without allocation); the first CTAs gather X_{hop-1}. hop - 1 <= ell
             // = tau[k] always, so the hop tau+1 / tau+2 records are never written.
             HopArgs<double> ha{};
             ha.row_ptr = row_ptr;
@@ -220,8 +220,12 @@ static void noalloc_impl(int32_t n, int64_t nnz, const int32_t *row_ptr, const i
             launch_spmm_hop<double, B, 1>(ha, 1, s, num_sms);
             std::swap(a, b);
         }
-        k_gather<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr,
-                                                            nullptr, GatherRec{0, nullptr, 0}, nullptr);
+        if (ell >= 2)  // the last hop only where the gather reads it, with the gathers of hops ell-1, ell
+            k_last_hop<double, B><<<nb, kSpmmWarps * 32, 0, s>>>(row_ptr, col_idx, inv_deg, a, n, bsrc, nb, tau,
+                                                                  ell, acc, nullptr, nullptr, GatherRec{0, nullptr, 0});
+        else
+            k_gather<double, B><<<nb, 128, 0, s>>>(row_ptr, col_idx, a, n, bsrc, nb, tau, ell, acc, nullptr, nullptr,
+                                                   GatherRec{0, nullptr, 0}, nullptr);
         SC_LAUNCH_CHECK();
     }
     k_na_combine<<<ceil_div(n, 8), 256, 0, s>>>(row_ptr, col_idx, rev, inv_deg, acc, n, s_hat);

@@ -11,6 +11,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "hop2_mask.cuh"
 #include "hop_tma.cuh"
 #include "tgtplus.cuh"
 #include "propagate.cuh"
@@ -319,6 +320,102 @@ static void first_gather_p(const sc_graph *g, int B, bool first, const void *x, 
     }
 }
 
+template <typename T, int B>
+static void last_hop_t(sc_graph *g, const void *x, const int32_t *src, int nsrc, int max_deg, const int32_t *tau,
+                       int ell, double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+    g->last_diag.reserve(nsrc);
+    k_last_diag<T, B><<<nsrc, kSpmmWarps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g),
+                                                      static_cast<const T *>(x), g->n, src, nsrc, tau, ell, a, b, c,
+                                                      rec, g->last_diag.get());
+    dim3 grid(nsrc, std::min(ceil_div(std::max(max_deg, 1), kSpmmWarps), 65535));
+    k_last_rows<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), inv_deg_of<T>(g),
+                                                      static_cast<const T *>(x), g->n, src, nsrc, tau, ell, a, b, c,
+                                                      rec, g->last_diag.get());
+}
+
+template <typename T>
+static void last_hop_p(sc_graph *g, int B, const void *x, const int32_t *src, int nsrc, int max_deg,
+                       const int32_t *tau, int ell, double *a, double *b, double *c, const GatherRec &rec,
+                       cudaStream_t s) {
+    switch (B) {
+    case 32: last_hop_t<T, 32>(g, x, src, nsrc, max_deg, tau, ell, a, b, c, rec, s); break;
+    case 64: last_hop_t<T, 64>(g, x, src, nsrc, max_deg, tau, ell, a, b, c, rec, s); break;
+    case 128: last_hop_t<T, 128>(g, x, src, nsrc, max_deg, tau, ell, a, b, c, rec, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
+    }
+}
+
+template <typename T, int B>
+static void hop2_mask_t(const sc_graph *g, uint32_t *mask, void *x2, int slices, const int32_t *src, int nsrc,
+                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+    k_mask_scatter<B><<<nsrc, 128, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), src, nsrc, mask, g->n);
+    MaskHopArgs<T> m{};
+    m.row_ptr = g->row_ptr.get();
+    m.col = g->col_idx.get();
+    m.inv_deg = inv_deg_of<T>(g);
+    m.mask = mask;
+    m.x_next = static_cast<T *>(x2);
+    m.n = g->n;
+    m.row_order = g->row_order.get();
+    m.n_heavy = g->n_heavy;
+    m.heavy_t = g->heavy_threshold_cached;
+    constexpr int rpc = kSpmmWarps * (32 / (B / 4));
+    m.light_ctas = light_ctas_for(g->n, rpc, g->num_sms);
+    m.gather_ctas = B;
+    m.src = src;
+    m.nsrc = nsrc;
+    m.tau = tau;
+    m.g = a;
+    m.t1 = b;
+    m.t2 = c;
+    m.rec = rec;
+    dim3 grid(m.gather_ctas + m.n_heavy + m.light_ctas, slices);
+    k_hop2_mask<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(m);
+}
+
+template <typename T>
+static void hop2_mask_p(const sc_graph *g, int B, uint32_t *mask, void *x2, int slices, const int32_t *src, int nsrc,
+                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+    switch (B) {
+    case 32: hop2_mask_t<T, 32>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
+    case 64: hop2_mask_t<T, 64>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
+    case 128: hop2_mask_t<T, 128>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
+    }
+}
+
+// hops 1 and 2 of a block from its sources alone (X_1 is never stored): marks
+// N(s_b) in a bit mask (zeroed here), computes X_2 into x2 and gathers hop 1
+void launch_hop2_mask(sc_graph *g, int prec, int B, void *x2, int slices, const int32_t *src, int nsrc,
+                      const int32_t *tau, double *a, double *b, double *cc, const GatherRec &rec, cudaStream_t s) {
+    const size_t words = static_cast<size_t>(slices) * g->n * (B / 32);
+    g->mask.reserve(words);
+    SC_CUDA(cudaMemsetAsync(g->mask.get(), 0, words * sizeof(uint32_t), s));
+    switch (prec) {
+    case SC_PREC_FP64: hop2_mask_p<double>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s); break;
+    case SC_PREC_FP32: hop2_mask_p<float>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s); break;
+    case SC_PREC_BF16:
+        hop2_mask_p<__nv_bfloat16>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s);
+        break;
+    }
+    SC_LAUNCH_CHECK();
+}
+
+// hop `ell` (the block's last) computed only where its gather reads it, with
+// the gathers of X_{ell-1} and X_ell; x = X_{ell-1}; max_deg = the largest
+// degree of the sources
+void launch_last_hop(sc_graph *g, int prec, int B, const void *x, const int32_t *src, int nsrc, int max_deg,
+                     const int32_t *tau, int ell, double *a, double *b, double *cc, const GatherRec &rec,
+                     cudaStream_t s) {
+    if (nsrc <= 0) return;
+    switch (prec) {
+    case SC_PREC_FP64: last_hop_p<double>(g, B, x, src, nsrc, max_deg, tau, ell, a, b, cc, rec, s); break;
+    case SC_PREC_FP32: last_hop_p<float>(g, B, x, src, nsrc, max_deg, tau, ell, a, b, cc, rec, s); break;
+    case SC_PREC_BF16: last_hop_p<__nv_bfloat16>(g, B, x, src, nsrc, max_deg, tau, ell, a, b, cc, rec, s); break;
+    }
+    SC_LAUNCH_CHECK();
+}
+
 void launch_first_or_gather(const sc_graph *g, int prec, int B, bool first, const void *x, const int32_t *src,
                             int nsrc, const int32_t *tau, int ell, double *a, double *b, double *cc,
                             const GatherRec &rec, cudaStream_t s, const SliceWin *win = nullptr) {
@@ -345,7 +442,8 @@ static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
 
 // Autotuner: for every admissible (B, lane split) time what one block of
 // sources costs on this graph: the zeroing of X_1, the first hop, a hop with
-// the fused gather (taken L - 1 times) and the final gather, over a strided
+// the fused gather (taken L - 2 times) and a gather (standing for the last
+// hop, which only computes what its gather reads), over a strided
 // sample of sources (values do not change the cost). Keeps the least time per
 // source; cached per graph, precision, request and length. The gathers write
 // the accumulators, which the caller resets afterwards.
@@ -423,7 +521,7 @@ static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_sl
             SC_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
             SC_CUDA(cudaEventElapsedTime(&c2, ev[2], ev[3]));
             const double hop = b / reps;
-            const double block = a + c2 + (L - 1) * hop;
+            const double block = a + c2 + std::max(L - 2, 0) * hop;  // the last hop runs gather-sized
             best_block[ci] = std::min(best_block[ci], block / nsrc);
             best_hop[ci] = std::min(best_hop[ci], hop / nsrc);
         }
@@ -567,7 +665,10 @@ __global__ void k_f32_to_bf16(const float4 *__restrict__ in, uint2 *__restrict__
 // X_{ell-1}; at the hop where the storage turns to bf16 the hop runs in fp32
 // and its output is converted (xa / xb are swapped by the caller as usual:
 // on return X_ell is in the buffer the caller will read next)
-static void hop_mixed(const Run &R, HopLaunch h, int32_t ell, size_t elems, cudaStream_t s, void **xa, void **xb) {
+// A windowed loop also zeroes the fp32 copy after the conversion: its later
+// hops write only their windows and read zeros outside them.
+static void hop_mixed(const Run &R, HopLaunch h, int32_t ell, size_t elems, cudaStream_t s, void **xa, void **xb,
+                      bool windowed = false) {
     const int pin = prec_at(R, ell - 1), pout = prec_at(R, ell);
     launch_hop(R.g, pin, R.B, R.vpl, h, s);
     if (pin != pout) {  // fp32 -> bf16 at hop h0: convert into the input buffer, now free
@@ -575,6 +676,7 @@ static void hop_mixed(const Run &R, HopLaunch h, int32_t ell, size_t elems, cuda
             static_cast<const float4 *>(h.xn), static_cast<uint2 *>(const_cast<void *>(h.xp)),
             static_cast<int64_t>(elems / 4));
         SC_LAUNCH_CHECK();
+        if (windowed) SC_CUDA(cudaMemsetAsync(h.xn, 0, elems * sizeof(float), s));
         return;  // X_ell (bf16) is in *xa: no swap
     }
     std::swap(*xa, *xb);
@@ -637,12 +739,25 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         if (L == 0) continue;
         const int32_t *src = g->src_list.get() + first;
         void *xa = g->xa.get(), *xb = g->xb.get();
-        SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * R.slice_bytes, s));
-        launch_first_or_gather(g, prec_at(R, 1), B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr,
-                               R.rec, s);
-        R.launches += 1;  // the memset is not a kernel of ours
-        int32_t tt = L;   // hops traversed; TGT+ may switch to walks earlier
-        for (int ell = 2; ell <= L; ++ell) {
+        // hops 1-2 from the sources alone when X_1 is read by nothing else (no TGT+
+        // test or walk from X_1, no sparse last hop at 2, one storage type)
+        const bool from_mask = !R.plus && L >= 3 && prec_at(R, 1) == prec_at(R, 2);
+        int ell0 = 2;
+        if (from_mask) {
+            launch_hop2_mask(g, prec_at(R, 2), B, xb, used_slices, src, nsrc, g->tau_entry.get(), g->acc_g.get(),
+                             g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+            std::swap(xa, xb);
+            R.launches += 2;
+            ell0 = 3;
+        } else {
+            SC_CUDA(cudaMemsetAsync(xa, 0, used_slices * R.slice_bytes, s));
+            launch_first_or_gather(g, prec_at(R, 1), B, true, xa, src, nsrc, nullptr, 1, nullptr, nullptr, nullptr,
+                                   R.rec, s);
+            R.launches += 1;  // the memset is not a kernel of ours
+        }
+        int32_t tt = L;  // hops traversed; TGT+ may switch to walks earlier
+        bool last_done = false;
+        for (int ell = ell0; ell <= L; ++ell) {
             const bool paper_rule = R.o->switch_rule == SC_SWITCH_PAPER;
             if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
                 // switch test after hop ell-1. Paper rule (Eq. 14): frontier volume against the
@@ -666,7 +781,21 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                     break;
                 }
             }
-            // hop ell computes X_ell and, in its tail CTAs, gathers X_{ell-1}
+            if (ell == L && prec_at(R, ell - 1) == prec_at(R, ell)) {
+                // the block's last hop: X_L only where the gather reads it, fused with
+                // the gathers of X_{L-1} and X_L
+                int max_deg = 0;
+                for (int q = 0; q < nsrc; ++q) {
+                    const int32_t v = h_src[first + q];
+                    if (v >= 0) max_deg = std::max(max_deg, g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
+                }
+                launch_last_hop(g, prec_at(R, ell), B, xa, src, nsrc, max_deg, g->tau_entry.get(), ell,
+                                g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+                R.launches += 2;
+                last_done = true;
+                break;
+            }
+            // hop ell computes X_ell and, in its first CTAs, gathers X_{ell-1}
             HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
                         g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
             if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
@@ -676,9 +805,11 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;
             R.alg_bytes += used_slices * hop_bytes_per_slice(ell);
         }
-        launch_first_or_gather(g, prec_at(R, tt), B, false, xa, src, nsrc, g->tau_entry.get(), tt, g->acc_g.get(),
-                               g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
-        R.launches += 1;
+        if (!last_done) {
+            launch_first_or_gather(g, prec_at(R, tt), B, false, xa, src, nsrc, g->tau_entry.get(), tt,
+                                   g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+            R.launches += 1;
+        }
         R.hops += tt;
         R.source_hops += static_cast<int64_t>(tt) * nsrc;
         if (R.plus) {
@@ -922,7 +1053,7 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             h.win_heavy = heavy_max;
             h.win_rows = rows_max;
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], is));
-            hop_mixed(R, h, ell, bytes / elem, is, &xa, &xb);
+            hop_mixed(R, h, ell, bytes / elem, is, &xa, &xb, true);
             if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], is));
             ++R.hop_launches;
             R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;

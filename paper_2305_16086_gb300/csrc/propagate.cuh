@@ -155,6 +155,24 @@ struct HopArgs {
 // hub's row does not serialise on one warp).
 // xs points at the source's column of its slice, whose first stored row is
 // `base`.
+// the update of entry k by its hop-ell term
+__device__ __forceinline__ void gather_term(int32_t k, double term, const int32_t *__restrict__ tau, int32_t ell,
+                                            double *__restrict__ g, double *__restrict__ t1, double *__restrict__ t2,
+                                            const GatherRec &rec) {
+    const int32_t tk = tau[k];
+    if (ell <= tk) {
+        g[k] += term;
+        if (rec.mode == 1) {
+            if (ell == tk - 1) t1[k] = term;
+            else if (ell == tk) t2[k] = term;
+        }
+    } else if (rec.mode == 0) {
+        if (ell == tk + 1) t1[k] = term;
+        else if (ell == tk + 2) t2[k] = term;
+    }
+    if (rec.all) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
+}
+
 template <typename T, int B>
 __device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                               const T *__restrict__ xs, int32_t base, int32_t s,
@@ -164,19 +182,8 @@ __device__ __forceinline__ void gather_source(const int32_t *__restrict__ row_pt
     const double diag = static_cast<double>(to_acc(xs[static_cast<int64_t>(s - base) * B]));
     for (int32_t k = row_ptr[s] + tid; k < row_ptr[s + 1]; k += nthr) {
         const int32_t j = col[k];
-        const double term = diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j - base) * B]));
-        const int32_t tk = tau[k];
-        if (ell <= tk) {
-            g[k] += term;
-            if (rec.mode == 1) {
-                if (ell == tk - 1) t1[k] = term;
-                else if (ell == tk) t2[k] = term;
-            }
-        } else if (rec.mode == 0) {
-            if (ell == tk + 1) t1[k] = term;
-            else if (ell == tk + 2) t2[k] = term;
-        }
-        if (rec.all) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
+        gather_term(k, diag - static_cast<double>(to_acc(xs[static_cast<int64_t>(j - base) * B])), tau, ell, g, t1,
+                    t2, rec);
     }
 }
 
@@ -415,6 +422,120 @@ __global__ void k_gather(const int32_t *__restrict__ row_ptr, const int32_t *__r
     int32_t base;
     const T *xs = slice_column<T, B>(x, n, win, q, &base);
     gather_source<T, B>(row_ptr, col, xs, base, s, tau, ell, g, t1, t2, threadIdx.x, blockDim.x, rec);
+}
+
+// X_ell[r, b] from X_{ell-1} for one row r and one column b, by one warp,
+// in the summation order of k_spmm_hop (chunks of 32 consecutive entries
+// summed in order, chunk sums added in chunk order, one scale by 1/d), then
+// rounded to the storage type: the value a full hop would have stored.
+// xs: column b of X_{ell-1}, rows addressed from `base`.
+template <typename T, int B>
+__device__ __forceinline__ double hop_value(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                            const typename AccOf<T>::type *__restrict__ inv_deg,
+                                            const T *__restrict__ xs, int32_t base, int32_t r, int lane) {
+    using Acc = typename AccOf<T>::type;
+    const int32_t rb = row_ptr[r], re = row_ptr[r + 1];
+    Acc acc = Acc(0);
+    for (int32_t c0 = rb; c0 < re; c0 += 32 * kChunk) {  // 32 chunks per round, lane l sums chunk l
+        const int32_t kb = c0 + lane * kChunk, ke = min(kb + kChunk, re);
+        Acc chunk = Acc(0);
+#pragma unroll 8
+        for (int32_t k = kb; k < ke; ++k) chunk += to_acc(xs[static_cast<int64_t>(col[k] - base) * B]);
+        const int nch = min(32, (re - c0 + kChunk - 1) / kChunk);  // chunks in this round (warp-uniform)
+        for (int l = 0; l < nch; ++l) acc += __shfl_sync(0xffffffffu, chunk, l);
+    }
+    acc *= inv_deg[r];
+    return static_cast<double>(to_acc(from_acc<T>(acc)));
+}
+
+// The last hop of a block, fused with the gathers of X_{ell-1} and X_ell
+// (ell = the block's last hop, Alg. 2 lines 6-11): X_ell is only read at each
+// source and its neighbours, so only those values are computed, one warp per
+// value, instead of the whole n x B block. One CTA per source; the values are
+// those of a full hop (hop_value), so the result is bit for bit the one of
+// k_spmm_hop followed by k_gather.
+template <typename T, int B>
+__global__ void __launch_bounds__(kSpmmWarps * 32) k_last_hop(const int32_t *__restrict__ row_ptr,
+                                                              const int32_t *__restrict__ col,
+                                                              const typename AccOf<T>::type *__restrict__ inv_deg,
+                                                              const T *__restrict__ x_prev, int32_t n,
+                                                              const int32_t *__restrict__ src, int32_t nsrc,
+                                                              const int32_t *__restrict__ tau, int32_t ell,
+                                                              double *__restrict__ g, double *__restrict__ t1,
+                                                              double *__restrict__ t2, const GatherRec rec) {
+    __shared__ double diag;
+    const int32_t q = blockIdx.x;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    if (s < 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t base;
+    const T *xs = slice_column<T, B>(x_prev, n, nullptr, q, &base);
+    // hop ell - 1 (as the fused gather of a full hop-ell launch would)
+    gather_source<T, B>(row_ptr, col, xs, base, s, tau, ell - 1, g, t1, t2, threadIdx.x, blockDim.x, rec);
+    if (warp == 0) {
+        const double v = hop_value<T, B>(row_ptr, col, inv_deg, xs, base, s, lane);
+        if (lane == 0) diag = v;
+    }
+    __syncthreads();  // also orders the hop ell - 1 updates before the hop ell ones
+    const int32_t kb = row_ptr[s], ke = row_ptr[s + 1];
+    for (int32_t k = kb + warp; k < ke; k += kSpmmWarps) {
+        const double xj = hop_value<T, B>(row_ptr, col, inv_deg, xs, base, col[k], lane);
+        if (lane == 0) gather_term(k, diag - xj, tau, ell, g, t1, t2, rec);
+    }
+}
+
+// The same last hop in two launches, so that a source with many (or heavy)
+// neighbours spreads over many CTAs: k_last_diag gathers X_{ell-1} and
+// computes X_ell[s, b] (one CTA per source); k_last_rows computes X_ell at
+// the neighbours, one warp per neighbour, over a (source, neighbour range)
+// grid, and gathers hop ell.
+template <typename T, int B>
+__global__ void __launch_bounds__(kSpmmWarps * 32) k_last_diag(const int32_t *__restrict__ row_ptr,
+                                                               const int32_t *__restrict__ col,
+                                                               const typename AccOf<T>::type *__restrict__ inv_deg,
+                                                               const T *__restrict__ x_prev, int32_t n,
+                                                               const int32_t *__restrict__ src, int32_t nsrc,
+                                                               const int32_t *__restrict__ tau, int32_t ell,
+                                                               double *__restrict__ g, double *__restrict__ t1,
+                                                               double *__restrict__ t2, const GatherRec rec,
+                                                               double *__restrict__ diag) {
+    const int32_t q = blockIdx.x;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    if (s < 0) return;
+    int32_t base;
+    const T *xs = slice_column<T, B>(x_prev, n, nullptr, q, &base);
+    gather_source<T, B>(row_ptr, col, xs, base, s, tau, ell - 1, g, t1, t2, threadIdx.x, blockDim.x, rec);
+    if (threadIdx.x < 32) {
+        const double v = hop_value<T, B>(row_ptr, col, inv_deg, xs, base, s, threadIdx.x);
+        if (threadIdx.x == 0) diag[q] = v;
+    }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kSpmmWarps * 32) k_last_rows(const int32_t *__restrict__ row_ptr,
+                                                               const int32_t *__restrict__ col,
+                                                               const typename AccOf<T>::type *__restrict__ inv_deg,
+                                                               const T *__restrict__ x_prev, int32_t n,
+                                                               const int32_t *__restrict__ src, int32_t nsrc,
+                                                               const int32_t *__restrict__ tau, int32_t ell,
+                                                               double *__restrict__ g, double *__restrict__ t1,
+                                                               double *__restrict__ t2, const GatherRec rec,
+                                                               const double *__restrict__ diag) {
+    const int32_t q = blockIdx.x;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    if (s < 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t base;
+    const T *xs = slice_column<T, B>(x_prev, n, nullptr, q, &base);
+    const int32_t ke = row_ptr[s + 1];
+    for (int32_t k = row_ptr[s] + static_cast<int32_t>(blockIdx.y) * kSpmmWarps + warp; k < ke;
+         k += static_cast<int32_t>(gridDim.y) * kSpmmWarps) {
+        const double xj = hop_value<T, B>(row_ptr, col, inv_deg, xs, base, col[k], lane);
+        if (lane == 0) gather_term(k, diag[q] - xj, tau, ell, g, t1, t2, rec);
+    }
 }
 
 // rows one CTA of the SIMT hop kernel computes on the light path
