@@ -44,35 +44,18 @@ struct MaskHopArgs {
     GatherRec rec;
 };
 
-// four columns c0..c0+3 of X_1 at row j: the stored 1/d_j where marked
-template <typename T>
-__device__ __forceinline__ void mask_add(typename AccOf<T>::type *acc, uint32_t bits,
-                                         typename AccOf<T>::type x) {
-    using Acc = typename AccOf<T>::type;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += ((bits >> c) & 1u) ? x : Acc(0);
-}
 
-template <typename T>
-__device__ __forceinline__ void store4(T *out, const typename AccOf<T>::type *v) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) out[c] = from_acc<T>(v[c]);
-}
 
 // CTAs [0, gather_ctas): the gather of hop 1 for the slice's sources (term
 // X_1[s,b] - X_1[j,b] = 0 - stored 1/d_j); the next n_heavy CTAs: one heavy
-// row each; the rest: light rows, LG = B/4 lanes (four columns each) per
-// row, striding over the rows in natural order and skipping heavy ones.
+// row each (a warp per chunk); the rest: light rows, one warp per row,
+// striding over the rows in natural order and skipping heavy ones.
 template <typename T, int B>
 __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs<T> a) {
     using Acc = typename AccOf<T>::type;
-    constexpr int LG = B / 4, G = 32 / LG, W = B / 32, U = 8;
+    constexpr int W = B / 32;  // mask words per node
     const int32_t n = a.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / LG, gl = lane % LG;
-    const int c0 = gl * 4;
-    const int shift = c0 % 32;
-    const uint32_t *mask = a.mask + static_cast<int64_t>(blockIdx.y) * n * W + c0 / 32;
     T *xn = a.x_next + static_cast<int64_t>(blockIdx.y) * n * B;
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
@@ -88,29 +71,65 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
         return;
     }
     const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;
+    // one chunk of 32 entries (CSR positions k0 .. k0 + cnt) by one warp. Lane
+    // l owns the CPL = W = B/32 columns l*W .., i.e. bits of mask word
+    // l / GW (GW = 32 / W lanes per word). The lanes load the words in a
+    // transposed order (lane l: word l / GW of neighbours r*GW + l % GW, r < W)
+    // so that one shuffle per neighbour hands every lane its own word; one
+    // more hands round the stored 1/d. Neighbours are taken in CSR order.
+    constexpr int CPL = B / 32, GW = 32 / W;
+    const int lc0 = lane * CPL, lw = lane / GW, lshift = lc0 % 32;
+    const uint32_t *mrow = a.mask + static_cast<int64_t>(blockIdx.y) * n * W;
+    auto chunk_sum = [&](int32_t k0, int cnt, Acc *chunk) {
+        uint32_t vr[W];
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+            const int nb = r * GW + lane % GW;
+            vr[r] = nb < cnt ? mrow[static_cast<int64_t>(col[k0 + nb]) * W + lw] : 0u;
+        }
+        const Acc xj = lane < cnt ? x1(col[k0 + lane]) : Acc(0);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) chunk[c] = Acc(0);
+        // X_1 is sparse: most neighbours have an all-zero mask and add only
+        // zeros, so only the marked ones are handed round (still in CSR order)
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+            const uint32_t b = __ballot_sync(0xffffffffu, vr[r] != 0u);
+            uint32_t nz = 0u;  // bit uu: neighbour r * GW + uu has a marked column
+#pragma unroll
+            for (int w = 0; w < W; ++w) nz |= (b >> (w * GW)) & (GW == 32 ? 0xffffffffu : ((1u << GW) - 1u));
+            while (nz) {
+                const int uu = __ffs(nz) - 1;
+                nz &= nz - 1u;
+                const uint32_t m = __shfl_sync(0xffffffffu, vr[r], lw * GW + uu);
+                const Acc xv = __shfl_sync(0xffffffffu, xj, r * GW + uu);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) chunk[c] += ((m >> (lshift + c)) & 1u) ? xv : Acc(0);
+            }
+        }
+    };
     if (cta < a.n_heavy) {
-        constexpr int NGRP = kSpmmWarps * G;
-        __shared__ Acc part[NGRP][B];
+        // heavy row: warp w sums chunks w, w + kSpmmWarps, ...; the chunk sums
+        // are added in chunk order through shared memory
+        __shared__ Acc part[kSpmmWarps][B];
         const int32_t row = a.row_order[cta];
         const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
         const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
         Acc total = Acc(0);  // thread t < B owns column t
-        for (int32_t base = 0; base < nchunks; base += NGRP) {
-            const int slot = warp * G + grp;
-            const int32_t c = base + slot;
-            Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+        for (int32_t base = 0; base < nchunks; base += kSpmmWarps) {
+            const int32_t c = base + warp;
+            Acc chunk[CPL];
             if (c < nchunks) {
-                const int32_t kb = rb + c * kChunk, ke = min(kb + kChunk, re);
-                for (int32_t k = kb; k < ke; ++k) {
-                    const int32_t j = col[k];
-                    mask_add<T>(acc, (mask[static_cast<int64_t>(j) * W] >> shift) & 0xFu, x1(j));
-                }
+                chunk_sum(rb + c * kChunk, min(kChunk, re - (rb + c * kChunk)), chunk);
+            } else {
+#pragma unroll
+                for (int e = 0; e < CPL; ++e) chunk[e] = Acc(0);
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) part[slot][c0 + e] = acc[e];
+            for (int e = 0; e < CPL; ++e) part[warp][lc0 + e] = chunk[e];
             __syncthreads();
             if (threadIdx.x < B) {
-                const int cnt = min(NGRP, nchunks - base);
+                const int cnt = min(kSpmmWarps, nchunks - base);
                 for (int q = 0; q < cnt; ++q) total += part[q][threadIdx.x];
             }
             __syncthreads();
@@ -118,45 +137,30 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
         if (threadIdx.x < B) xn[static_cast<int64_t>(row) * B + threadIdx.x] = from_acc<T>(total * a.inv_deg[row]);
         return;
     }
+    // light rows: one warp per row, chunk by chunk
     if (cta - a.n_heavy >= a.light_ctas) return;
-    const int64_t stride = static_cast<int64_t>(a.light_ctas) * kSpmmWarps * G;
+    const int64_t stride = static_cast<int64_t>(a.light_ctas) * kSpmmWarps;
     const int32_t heavy_t = a.n_heavy > 0 ? a.heavy_t : 0x7fffffff;
-    for (int64_t idx = (static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp) * G + grp; idx < n;
-         idx += stride) {
+    for (int64_t idx = static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp; idx < n; idx += stride) {
         const int32_t row = static_cast<int32_t>(idx);
         const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
         if (re - rb > heavy_t) continue;  // a heavy row: its own CTA computes it
-        Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, chunk[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-        int32_t k = rb;
-        for (; k + U <= re; k += U) {
-            int32_t j[U];
-            uint32_t m[U];
-            Acc x[U];
+        Acc acc[CPL], chunk[CPL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) j[u] = col[k + u];
+        for (int c = 0; c < CPL; ++c) acc[c] = Acc(0);
+        for (int32_t k0 = rb; k0 < re; k0 += kChunk) {
+            chunk_sum(k0, min(kChunk, re - k0), chunk);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                m[u] = mask[static_cast<int64_t>(j[u]) * W];
-                x[u] = x1(j[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) mask_add<T>(chunk, (m[u] >> shift) & 0xFu, x[u]);
-            if (((k + U - rb) % kChunk) == 0) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    acc[c] += chunk[c];
-                    chunk[c] = Acc(0);
-                }
-            }
-        }
-        for (; k < re; ++k) {
-            const int32_t j = col[k];
-            mask_add<T>(chunk, (mask[static_cast<int64_t>(j) * W] >> shift) & 0xFu, x1(j));
+            for (int c = 0; c < CPL; ++c) acc[c] += chunk[c];
         }
         const Acc sc = a.inv_deg[row];
+        // the lane's CPL values are contiguous: one vector store
+        struct alignas(CPL * sizeof(T)) Vec {
+            T v[CPL];
+        } out;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = (acc[c] + chunk[c]) * sc;
-        store4<T>(xn + static_cast<int64_t>(row) * B + c0, acc);
+        for (int c = 0; c < CPL; ++c) out.v[c] = from_acc<T>(acc[c] * sc);
+        *reinterpret_cast<Vec *>(xn + static_cast<int64_t>(row) * B + lc0) = out;
     }
 }
 

@@ -359,8 +359,7 @@ static void hop2_mask_t(const sc_graph *g, uint32_t *mask, void *x2, int slices,
     m.row_order = g->row_order.get();
     m.n_heavy = g->n_heavy;
     m.heavy_t = g->heavy_threshold_cached;
-    constexpr int rpc = kSpmmWarps * (32 / (B / 4));
-    m.light_ctas = light_ctas_for(g->n, rpc, g->num_sms);
+    m.light_ctas = light_ctas_for(g->n, kSpmmWarps, g->num_sms);  // one light row per warp
     m.gather_ctas = B;
     m.src = src;
     m.nsrc = nsrc;
