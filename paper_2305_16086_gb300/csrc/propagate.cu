@@ -739,8 +739,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         const int32_t *src = g->src_list.get() + first;
         void *xa = g->xa.get(), *xb = g->xb.get();
         // hops 1-2 from the sources alone when X_1 is read by nothing else (no TGT+
-        // test or walk from X_1, no sparse last hop at 2, one storage type)
-        const bool from_mask = !R.plus && L >= 3 && prec_at(R, 1) == prec_at(R, 2);
+        // switch test or walk from X_1, no sparse last hop at 2, one storage type)
+        const bool test_at_1 =
+            R.plus && (R.o->switch_rule == SC_SWITCH_PAPER || 1 >= std::max(1, L - kCostRuleHops));
+        const bool from_mask = !test_at_1 && L >= 3 && prec_at(R, 1) == prec_at(R, 2);
         int ell0 = 2;
         if (from_mask) {
             launch_hop2_mask(g, prec_at(R, 2), B, xb, used_slices, src, nsrc, g->tau_entry.get(), g->acc_g.get(),
