@@ -182,6 +182,7 @@ struct sc_graph {
     sc::DevBuf<long long> tp_pvol, tp_cvol, tp_walks, tp_counters, tp_packed, tp_chunk_w0;
     sc::DevBuf<int32_t> tp_eq, tp_ek, tp_chunk_entry, tp_entry_chunk0;
     sc::DevBuf<double> tp_chunk_sum;
+    sc::DevBuf<double> tp_srcstat;  // per column: rho_hat, min and max of p over N(s)
     std::vector<cudaEvent_t> hop_events;  // pairs bracketing timed propagation launches
     ~sc_graph() {
         for (cudaEvent_t e : hop_events) cudaEventDestroy(e);

@@ -1,5 +1,6 @@
 // Host side of TGT+ (Algorithm 4): the switch test of Eq. 14 after a hop and
 // the random-walk tail, dispatched over (precision, B).
+#include <algorithm>
 #include <cmath>
 
 #include "tgtplus.cuh"
@@ -7,8 +8,8 @@
 namespace sc {
 
 template <typename T, int B>
-static void chi_check_t(sc_graph *g, const void *x, int slices, const int32_t *src, int nsrc, const int32_t *tau,
-                        int ell, int gamma, double eps, double log2md, cudaStream_t s) {
+static void chi_check_t(sc_graph *g, const void *x, int slices, const int32_t *src, int nsrc, int max_deg,
+                        const int32_t *tau, int ell, int gamma, double eps, double log2md, cudaStream_t s) {
     const int nct = ceil_div(g->n, kChiRowsPerCta);
     const int ncols = slices * B;
     double *pval = g->tp_pval.get();
@@ -37,7 +38,10 @@ static void chi_check_t(sc_graph *g, const void *x, int slices, const int32_t *s
     a.log_2m_delta = log2md;
     a.walk_count = g->tp_walks.get();
     a.rhs = g->tp_counters.get();
-    k_chi_entries<T, B><<<nsrc, 256, 0, s>>>(static_cast<const T *>(x), a);
+    k_chi_source<T, B><<<nsrc, 32, 0, s>>>(static_cast<const T *>(x), a, g->tp_srcstat.get());
+    const int nw = 256 / 32;
+    dim3 grid(nsrc, std::min(ceil_div(std::max(max_deg, 1), nw), 65535));
+    k_chi_entries<T, B><<<grid, 256, 0, s>>>(static_cast<const T *>(x), a, g->tp_srcstat.get());
 }
 
 template <typename T, int B>
@@ -88,6 +92,7 @@ void tgtplus_reserve(sc_graph *g, int slices, int B) {
     g->tp_cmin.reserve(cols);
     g->tp_cmax.reserve(cols);
     g->tp_cvol.reserve(cols);
+    g->tp_srcstat.reserve(3 * cols);
     g->tp_walks.reserve(g->nnz);
     g->tp_counters.reserve(4);
 }
@@ -99,7 +104,10 @@ void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, cons
                    int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
                    long long *rhs, long long *steps, cudaStream_t s) {
     SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, 4 * sizeof(long long), s));
-    SC_DISPATCH_TB(prec, B, chi_check_t, g, x, slices, src, nsrc, tau, ell, gamma, eps, log2md, s);
+    int max_deg = 0;
+    for (int q = 0; q < nsrc; ++q)
+        if (h_src[q] >= 0) max_deg = std::max(max_deg, g->h_row_ptr[h_src[q] + 1] - g->h_row_ptr[h_src[q]]);
+    SC_DISPATCH_TB(prec, B, chi_check_t, g, x, slices, src, nsrc, max_deg, tau, ell, gamma, eps, log2md, s);
     SC_LAUNCH_CHECK();
     std::vector<long long> vol(static_cast<size_t>(slices) * B);
     long long h_cnt[3] = {0, 0, 0};

@@ -237,15 +237,12 @@ struct ChiArgs {
     long long *rhs;          // [0] sum of the launch's walk counts (Eq. 14 right side), [2] walk steps
 };
 
-// One CTA per source: warp 0 finds rho_hat (Alg. 3) and min / max of p over
-// N(i); then one warp per entry k = (i -> j), its lanes striding over N(j),
-// gives chi (Eq. 17, or Eq. 15 for gamma = 0) and R (Eq. 13) for the walk
-// length L = tau_k - ell. The floating-point expressions follow the oracle's
-// evaluation order (no FMA contraction).
+// Per source (one warp): rho_hat (Alg. 3) and min / max of p over N(i),
+// into stat[3 q .. 3 q + 2].
 template <typename T, int B>
-__global__ void k_chi_entries(const T *__restrict__ x, const ChiArgs a) {
+__global__ void k_chi_source(const T *__restrict__ x, const ChiArgs a, double *__restrict__ stat) {
     const int32_t q = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     if (q >= a.nsrc) return;
     const int32_t s = a.src[q];
     if (s < 0) return;
@@ -253,46 +250,63 @@ __global__ void k_chi_entries(const T *__restrict__ x, const ChiArgs a) {
     auto px = [&](int32_t v) { return static_cast<double>(to_acc(xs[static_cast<int64_t>(v) * B])); };
     const double *cv = a.cval + static_cast<int64_t>(q) * kGammaMax;
     const int32_t *ci = a.cid + static_cast<int64_t>(q) * kGammaMax;
+    const int g = a.gamma;
+    // rho_hat = max(max over edges inside C of p(c_a) + p(c_b), p(c_1) + p(c_gamma))
+    double best = -INFINITY;
+    if (g > 0) {
+        for (int t = lane; t < g * g; t += 32) {
+            const int u = t / g, v = t % g;
+            if (u < v && has_edge(a.row_ptr, a.col, ci[u], ci[v])) best = fmax(best, __dadd_rn(cv[u], cv[v]));
+        }
+    }
+    double nmin = INFINITY, nmax = -INFINITY;
+    for (int32_t k = a.row_ptr[s] + lane; k < a.row_ptr[s + 1]; k += 32) {
+        const double v = px(a.col[k]);
+        nmin = fmin(nmin, v);
+        nmax = fmax(nmax, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        nmin = fmin(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
+        nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    }
+    if (lane == 0) {
+        stat[3 * q] = g > 0 ? fmax(best, __dadd_rn(cv[0], cv[g - 1])) : 0.0;
+        stat[3 * q + 1] = nmin;
+        stat[3 * q + 2] = nmax;
+    }
+}
+
+// Per entry k = (i -> j) of source q = blockIdx.x, one warp each over a
+// (source, entry range) grid so that a hub source spreads over many CTAs:
+// the lanes stride over N(j) for chi (Eq. 17, or Eq. 15 for gamma = 0), then
+// R (Eq. 13) for the walk length L = tau_k - ell. The floating-point
+// expressions follow the oracle's evaluation order (no FMA contraction).
+template <typename T, int B>
+__global__ void k_chi_entries(const T *__restrict__ x, const ChiArgs a, const double *__restrict__ stat) {
+    const int32_t q = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (q >= a.nsrc) return;
+    const int32_t s = a.src[q];
+    if (s < 0) return;
+    const T *xs = x + static_cast<int64_t>(q / B) * a.n * B + (q % B);
+    auto px = [&](int32_t v) { return static_cast<double>(to_acc(xs[static_cast<int64_t>(v) * B])); };
     const double vmin = a.cmin[q], vmax = a.cmax[q];
     const int g = a.gamma;
     const int32_t rb = a.row_ptr[s], re = a.row_ptr[s + 1];
-    __shared__ double sh_rho, sh_nmin, sh_nmax;
     __shared__ unsigned long long sh_cnt[2];
-    if (warp == 0) {
-        // rho_hat = max(max over edges inside C of p(c_a) + p(c_b), p(c_1) + p(c_gamma))
-        double best = -INFINITY;
-        if (g > 0) {
-            for (int t = lane; t < g * g; t += 32) {
-                const int u = t / g, v = t % g;
-                if (u < v && has_edge(a.row_ptr, a.col, ci[u], ci[v])) best = fmax(best, __dadd_rn(cv[u], cv[v]));
-            }
-        }
-        double nmin = INFINITY, nmax = -INFINITY;
-        for (int32_t k = rb + lane; k < re; k += 32) {
-            const double v = px(a.col[k]);
-            nmin = fmin(nmin, v);
-            nmax = fmax(nmax, v);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-            nmin = fmin(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
-            nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-        }
-        if (lane == 0) {
-            sh_rho = g > 0 ? fmax(best, __dadd_rn(cv[0], cv[g - 1])) : 0.0;
-            sh_nmin = nmin;
-            sh_nmax = nmax;
-            sh_cnt[0] = 0;
-            sh_cnt[1] = 0;
-        }
+    if (threadIdx.x == 0) {
+        sh_cnt[0] = 0;
+        sh_cnt[1] = 0;
     }
     __syncthreads();
-    const double rho = sh_rho, nmin_i = sh_nmin, nmax_i = sh_nmax;
+    const double rho = stat[3 * q], nmin_i = stat[3 * q + 1], nmax_i = stat[3 * q + 2];
     const double d_i = static_cast<double>(re - rb);
     const double denom = __dmul_rn(__dmul_rn(__dmul_rn(d_i, d_i), a.eps), a.eps);
     unsigned long long local = 0, steps = 0;
-    for (int32_t k = rb + warp; k < re; k += nw) {
+    for (int32_t k = rb + static_cast<int32_t>(blockIdx.y) * nw + warp; k < re;
+         k += static_cast<int32_t>(gridDim.y) * nw) {
         const int32_t L = a.tau[k] - a.ell;
         if (L <= 0) {
             if (lane == 0) a.walk_count[k] = 0;
