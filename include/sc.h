@@ -259,17 +259,24 @@ typedef struct sc_report {
  * neighbour j the half sum g(v_i, v_j) of Eq. (9) is accumulated (Alg. 2
  * line 11) for the hops l <= tau_ij; the output is
  * s_hat(e_ij) = g(v_i, v_j) + g(v_j, v_i) (Alg. 2 line 12), one length per
- * edge for both halves.
+ * edge for both halves. TGT+ (SC_MODE_TGT_PLUS, Algorithm 4): the traversal
+ * of a block stops at the switch hop and the rest of each half sum is the
+ * mean of Philox-driven walk pairs (Eq. 11, counts from Eq. 13 with chi from
+ * Alg. 3); results are bit-identical for a given seed.
  *
  *   opts       : NULL = defaults (sc_options_default)
  *   s_hat      : double[nnz], host or device per SC_OUT_DEVICE
  *   tail_bound : nullable double[nnz]; with SC_OPT_RECORD_TAIL the
  *                a-posteriori bound on the remaining tail of each edge
  *   report     : nullable
- * The global and per-edge policies need lambda: sc_estimate_lambda is run
- * first if the graph has no cached value. A bipartite graph under these
- * policies fails with SC_ERR_UNSUPPORTED (lambda_star = 1: no finite length);
- * use SC_ELL_FIXED or SC_ELL_LEARNED with the end-corrected estimator.
+ * The global, per-edge and learned policies need lambda: sc_estimate_lambda
+ * is run first if the graph has no cached value. A bipartite graph under
+ * these policies fails with SC_ERR_UNSUPPORTED (lambda_star = 1: no finite
+ * length); use SC_ELL_FIXED with the end-corrected estimator. Errors:
+ * SC_ERR_INVALID_ARG (NULL graph or output, bad option values),
+ * SC_ERR_UNSUPPORTED (TGT+ with the learned policy, the end-corrected
+ * estimator or tail records), SC_ERR_TIMEOUT (a bounded wait of the TMA hop
+ * expired), SC_ERR_OOM, SC_ERR_CUDA. Outputs are unspecified on error.
  */
 sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                        sc_report *report);

@@ -13,7 +13,7 @@ namespace sc {
 
 constexpr int kGammaMax = 16;        // largest supported candidate count (Alg. 3)
 constexpr int kChiScanThreads = 128;
-constexpr int kChiRowsPerCta = 256;
+constexpr int kChiRowsPerCta = 64;
 constexpr uint32_t kWalkTag = 0x57414C4Bu;
 constexpr long long kWalkCountCap = 1ll << 40;
 
