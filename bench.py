@@ -51,10 +51,17 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spmm_hop_ba200k_traffic.json")
 
 
 def kernel_source_sha() -> str:
+    """Hash of the hop kernel's code with comments and blank space removed
+    (a comment edit does not make recorded counters stale)."""
+    import re
+
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(l.strip() for l in text.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -125,8 +125,8 @@ typedef struct sc_lambda_opts {
 
 /*
  * sc_estimate_lambda -- spectrum extremes of N = D^{1/2} P D^{-1/2}
- * (Lemma 3.1), the lambda that sets the truncation length (Eq. 6, Alg. 1
- * line 1). FP64 Lanczos with full reorthogonalisation on the device, after
+ * (Lemma 3.1), the lambda that sets the truncation length (Eq. 6, Algorithm 1's
+ * initial length). FP64 Lanczos with full reorthogonalisation on the device, after
  * deflating the top eigenvector sqrt(d)/sqrt(2m) (and, for a bipartite graph,
  * the bottom one). opts may be NULL for defaults. The result is also cached
  * in the graph for sc_all_edges. SC_ERR_LAMBDA_NOT_CONVERGED is returned
@@ -136,12 +136,12 @@ sc_status sc_estimate_lambda(sc_graph *g, const sc_lambda_opts *opts, sc_lambda 
 
 /*
  * sc_truncation_length -- tau per edge and per source from Eq. (5)-(6)
- * with omega = 2 (Alg. 1 line 1), Upsilon = Delta_t = 0:
+ * with omega = 2 (Algorithm 1's initial length), Upsilon = Delta_t = 0:
  *   f(e_ij, eps) = ceil( log(X_e / (eps (1 - lambda^2))) / log(1/lambda) - 1 ),
  *   X_e = 1/d_i + 1/d_j - 2/(d_i d_j), tau_ij = smallest odd integer >= max(f, 1),
- * tau_p(i) = max_j tau_ij (Alg. 2 line 4), ell_global = max_i tau_p(i).
+ * tau_p(i) = max_j tau_ij (Algorithm 2's per-source length), ell_global = max_i tau_p(i).
  *
- *   eps            : > 0 (TGT uses eps, TGT+ passes eps/2, Alg. 4 line 2)
+ *   eps            : > 0 (TGT uses eps; TGT+, Algorithm 4, passes eps/2)
  *   lam            : from sc_estimate_lambda; NULL = the graph's cached value
  *                    (SC_ERR_INVALID_ARG if none); lambda_star must be < 1
  *   ell_global_out : host int32 (may be NULL)
@@ -156,7 +156,7 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
 
 /* truncation policy */
 #define SC_ELL_GLOBAL 0     /* one length for every edge: max of Eq. (6) over all edges */
-#define SC_ELL_PER_EDGE 1   /* tau_ij of Eq. (6) per edge; sources run tau_p (Alg. 2 line 4) */
+#define SC_ELL_PER_EDGE 1   /* tau_ij of Eq. (6) per edge; sources run tau_p (Algorithm 2's per-source length) */
 #define SC_ELL_FIXED 2      /* opts.ell_fixed for every edge (no eigenvalue needed) */
 #define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP (sc_mlp_load); every edge
                                is then certified by the bound of sc_certified_lengths and, if it
@@ -255,11 +255,10 @@ typedef struct sc_report {
 /*
  * sc_all_edges -- estimate s(e) for every edge (Definition 2.2).
  * TGT (Algorithm 2): blocks of B sources are propagated together, X_l =
- * D^-1 A X_{l-1} (Alg. 2 lines 6-9 in pull form), and for each source i and
- * neighbour j the half sum g(v_i, v_j) of Eq. (9) is accumulated (Alg. 2
- * line 11) for the hops l <= tau_ij; the output is
- * s_hat(e_ij) = g(v_i, v_j) + g(v_j, v_i) (Alg. 2 line 12), one length per
- * edge for both halves. TGT+ (SC_MODE_TGT_PLUS, Algorithm 4): the traversal
+ * D^-1 A X_{l-1} (Algorithm 2's hop, in pull form), and for each source i and
+ * neighbour j the half sum g(v_i, v_j) of Eq. (9) is accumulated for the
+ * hops l <= tau_ij; the output is s_hat(e_ij) = g(v_i, v_j) + g(v_j, v_i)
+ * (Algorithm 2's final combine), one length per edge for both halves. TGT+ (SC_MODE_TGT_PLUS, Algorithm 4): the traversal
  * of a block stops at the switch hop and the rest of each half sum is the
  * mean of Philox-driven walk pairs (Eq. 11, counts from Eq. 13 with chi from
  * Alg. 3); results are bit-identical for a given seed.

@@ -10,8 +10,8 @@
  *  oracle_series  -- the truncated graph traversal of Algorithm 2 (TGT),
  *                    written plainly: for every requested source v_i a dense
  *                    FP64 vector p(., v_i) is pushed hop by hop over the
- *                    edges (Alg. 2 lines 6-9) and the per-edge half sums
- *                    g(v_i, v_j) of Eq. (9) are accumulated (Alg. 2 line 11).
+ *                    edges (Algorithm 2's hop) and the per-edge half sums
+ *                    g(v_i, v_j) of Eq. (9) are accumulated (Algorithm 2's accumulation).
  *                    Truncation is per CSR entry: entry k = (i -> j) keeps
  *                    the terms with hop l <= tau[k]. The terms at
  *                    hops tau[k]+1 and tau[k]+2 are also returned (they feed
@@ -75,22 +75,22 @@ int oracle_series(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                 const int32_t i = sources[si];
                 const int32_t k0 = row_ptr[i], k1 = row_ptr[i + 1];
                 const double d_i = (double)(k1 - k0);
-                /* line 2: p_0(., v_i) = e_i */
+                /* initialisation: p_0(., v_i) = e_i */
                 memset(p_prev, 0, sizeof(double) * (size_t)n);
                 p_prev[i] = 1.0;
-                /* line 3: g(v_i, v_j) = p_0(v_i,v_i)/d(v_i) - p_0(v_j,v_i)/d(v_i) = 1/d(v_i) */
+                /* hop 0 of Eq. (9): g(v_i, v_j) = p_0(v_i,v_i)/d(v_i) - p_0(v_j,v_i)/d(v_i) = 1/d(v_i) */
                 int32_t tau_p = 0;
                 for (int32_t k = k0; k < k1; ++k) {
                     g_out[k] = 1.0 / d_i;
                     if (t1_out) t1_out[k] = 0.0;
                     if (t2_out) t2_out[k] = 0.0;
-                    if (tau[k] > tau_p) tau_p = tau[k]; /* line 4 */
+                    if (tau[k] > tau_p) tau_p = tau[k]; /* the source's length: max over its edges */
                 }
                 const int32_t steps = tau_p + extra_steps;
                 for (int32_t l = 1; l <= steps; ++l) {
-                    /* line 6 */
+                    /* hop l: p_l(., v_i) from p_{l-1}(., v_i) */
                     memset(p_next, 0, sizeof(double) * (size_t)n);
-                    /* lines 7-9: push p_{l-1}(v_j, v_i) / d(v_x) to every neighbour v_x */
+                    /* push p_{l-1}(v_j, v_i) / d(v_x) to every neighbour v_x of each v_j reached */
                     for (int32_t j = 0; j < n; ++j) {
                         const double pj = p_prev[j];
                         if (pj > 0.0) {
@@ -101,7 +101,7 @@ int oracle_series(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                             }
                         }
                     }
-                    /* lines 10-11 */
+                    /* Eq. (9): add hop l's term to every edge of v_i with l <= tau_ij */
                     for (int32_t k = k0; k < k1; ++k) {
                         const int32_t j = col_idx[k];
                         const double term = p_next[i] / d_i - p_next[j] / d_i;

@@ -10,7 +10,7 @@ The series (Eq. 2) truncated at hop tau:
 split into the two half sums of Eq. (9),
 
     g_tau(v_i, v_j) = sum_{l=0}^{tau} (p_l(v_i,v_i) - p_l(v_j,v_i)) / d(v_i),
-    s_tau(e_ij)     = g_tau(v_i, v_j) + g_tau(v_j, v_i)     (Alg. 2 line 12).
+    s_tau(e_ij)     = g_tau(v_i, v_j) + g_tau(v_j, v_i)     (Algorithm 2's final combine).
 
 ``half_sums`` runs Algorithm 2 in C (oracle.c) for chosen sources and returns
 g, plus the hop tau+1 and tau+2 half terms. Both halves of an edge use the

@@ -17,8 +17,8 @@ walk length for the entry (i -> j).
   rho_hat from the edges inside C, else p(c_1) + p(c_gamma). Reading taken
   here: rho_hat = max(largest p(c_a) + p(c_b) over edges inside C,
   p(c_1) + p(c_gamma)). An edge with one end outside C sums to at most
-  p(c_1) + p(c_gamma), so this is always an upper bound of rho; the paper's
-  line 4 keeps only the first term when an edge exists inside C, which can be
+  p(c_1) + p(c_gamma), so this is always an upper bound of rho; Algorithm 3 as
+  printed keeps only the first term when an edge exists inside C, which can be
   below rho (``calchi(..., literal=True)`` computes that version).
 * Eq. 13: R = ceil(8 chi^2 log(2m/delta) / (d_i^2 eps^2)), at least 1.
 * Eq. 11: X = (sum_{t=1..L} p(W_i[t]) - sum_{t=1..L} p(W_j[t])) / d_i, walks
@@ -47,13 +47,13 @@ def _nbrs(row_ptr, col_idx, v):
 
 
 def top_candidates(p, gamma):
-    """Alg. 3 line 2: the gamma largest entries of p, ties by smaller node id."""
+    """Algorithm 3's candidate set: the gamma largest entries of p, ties by smaller node id."""
     order = np.lexsort((np.arange(p.size), -p))
     return order[:gamma]
 
 
 def rho_hat(row_ptr, col_idx, p, gamma, literal=False):
-    """Upper bound of rho (Eq. 16) from the candidate set C (Alg. 3 lines 2-5)."""
+    """Upper bound of rho (Eq. 16) from the candidate set C (Algorithm 3)."""
     C = top_candidates(p, gamma)
     best = -np.inf
     cset = set(C.tolist())
@@ -133,7 +133,7 @@ def frontier_volume(row_ptr, p):
 
 
 def source_column(n, row_ptr, col_idx, i, hops):
-    """p_hops(., v_i) = P^hops e_i by repeated push hops (Alg. 2 lines 6-9)."""
+    """p_hops(., v_i) = P^hops e_i by repeated push hops (Algorithm 2's hop)."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     deg = np.diff(row_ptr)
     p = np.zeros(n)

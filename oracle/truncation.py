@@ -1,4 +1,4 @@
-"""Eigenvalue bound and truncation lengths (oracle for Eq. 5-6, Alg. 1 line 1).
+"""Eigenvalue bound and truncation lengths (oracle for Eq. 5-6, Algorithm 1's initial length).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the timed
 CPU baseline; the CUDA path never imports it.
@@ -11,14 +11,14 @@ absolute value, the paper's lambda_2 is the second largest in absolute value,
 
 lambda_plus the largest eigenvalue below 1 and lambda_minus the smallest.
 
-Truncation length (Eq. 6 with omega = 2, Upsilon = Delta_t = 0, i.e. Alg. 1
-line 1):
+Truncation length (Eq. 6 with omega = 2, Upsilon = Delta_t = 0, i.e. the
+initial length of Algorithm 1):
 
     f(e_ij, eps) = ceil( log( X_e / (eps (1 - lambda_star^2)) ) / log(1/lambda_star) - 1 ),
     X_e = 1/d_i + 1/d_j - 2/(d_i d_j),
 
 and tau_ij is the smallest odd integer >= f (Eq. 5), at least 1. The per
-source length of Alg. 2 line 4 is tau_p(i) = max_j tau_ij; the global length
+source length of Algorithm 2's per-source length is tau_p(i) = max_j tau_ij; the global length
 is max over all edges.
 """
 from __future__ import annotations
@@ -107,7 +107,7 @@ def tau_entries(n, row_ptr, col_idx, eps: float, lam_star: float):
 
 
 def tau_per_source(n, row_ptr, tau_k):
-    """Alg. 2 line 4: tau_p(i) = max over the entries of row i."""
+    """Algorithm 2's per-source length: tau_p(i) = max over the entries of row i."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     out = np.zeros(n, dtype=np.int64)
     deg = np.diff(row_ptr)

@@ -8,7 +8,7 @@ namespace sc {
 
 // ---------------------------------------------------------------------------
 // Hop 2 from the sources alone. X_1[j, b] is the stored 1/d_j exactly when j
-// is a neighbour of s_b (Alg. 2 line 2 and the first hop) and 0 otherwise,
+// is a neighbour of s_b (Algorithm 2's initialisation and the first hop) and 0 otherwise,
 // so X_2 needs no X_1 block: bit b of mask[j] marks j in N(s_b), and row r of
 // X_2 sums the stored 1/d_j over its marked neighbours. Adding the zeros of
 // the unmarked columns changes no sum, so every value is bit for bit the one

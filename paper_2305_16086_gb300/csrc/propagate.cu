@@ -1,5 +1,5 @@
 // sc_all_edges: the truncated graph traversal of Algorithm 2 (TGT) over
-// blocks of sources, the per-edge combine of Alg. 2 line 12, the
+// blocks of sources, the per-edge combine of Algorithm 2's final combine, the
 // end-corrected estimator and the a-posteriori tail bound.
 #include <algorithm>
 #include <chrono>
@@ -38,7 +38,7 @@ void tau_entries_device(sc_graph *g, double eps, double lam_star, int32_t *tau_e
 // ---------------------------------------------------------------------------
 // accumulator initialisation and combine
 // ---------------------------------------------------------------------------
-// s_hat(e_ij) = g(v_i,v_j) + g(v_j,v_i) (Alg. 2 line 12) with g = unscaled / d,
+// s_hat(e_ij) = g(v_i,v_j) + g(v_j,v_i) (Algorithm 2's final combine) with g = unscaled / d,
 // optionally + t_{tau+1}/2; tail bound from q = t_{tau+1} + t_{tau+2}.
 __global__ void k_combine(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                           const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
@@ -817,7 +817,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             R.tt_min = std::min(R.tt_min, tt);
             R.tt_max = std::max(R.tt_max, tt);
             if (tt < L) {
-                // Alg. 4 lines 12-17: walk tails from X_tt with the counts of the last check
+                // Algorithm 4's walk phase: walk tails from X_tt with the counts of the last check
                 const double t0 = wall_ms();
                 SC_CUDA(cudaEventRecord(ev_w0, s));
                 const long long pairs = tgtplus_walks(g, prec_at(R, tt), B, xa, src, h_src.data() + first, nsrc,
@@ -852,7 +852,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
 // length, longest first; a launch (super-block) takes consecutive blocks of
 // one class up to a memory budget. Hop l of a super-block runs over its
 // leading blocks with L >= l - 1 (the others are done): blocks with L >= l
-// compute X_l, and all of them gather X_{l-1} (Alg. 2 lines 10-11), which
+// compute X_l, and all of them gather X_{l-1} (Algorithm 2's accumulation of Eq. 9), which
 // is the final gather of the blocks with L = l - 1. With R.capture the whole
 // loop is recorded into one CUDA graph and replayed as one launch.
 // ---------------------------------------------------------------------------
@@ -1150,7 +1150,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         std::fill(len.begin(), len.end(), o.ell_fixed);
         fill_i32(g->tau_entry.get(), nnz, o.ell_fixed, s);
     } else {
-        // TGT+ asks for a tail of at most eps/2 and leaves eps/2 to the walks (Alg. 4 line 2)
+        // TGT+ (Algorithm 4) asks for a tail of at most eps/2 and leaves eps/2 to the walks
         tau_entries_device(g, plus ? 0.5 * o.eps : o.eps, lam_star, g->tau_entry.get(), tau_src.get(), &ell_global);
         if (o.ell_policy == SC_ELL_GLOBAL) {
             std::fill(len.begin(), len.end(), ell_global);

@@ -6,7 +6,7 @@
 // probabilities p_l(x, s_b) contiguous, rows 16-byte aligned); S = slices x B
 // sources are propagated by one launch, slice q at X + q * n * B.
 //
-// Hop l: X_l[x, :] = (1/d_x) * sum_{j in N(x)} X_{l-1}[j, :]   (Alg. 2 lines 6-9,
+// Hop l: X_l[x, :] = (1/d_x) * sum_{j in N(x)} X_{l-1}[j, :]   (Algorithm 2's hop,
 // pull form of the scatter p_l(v_x, v_i) += p_{l-1}(v_j, v_i) / d(v_x)).
 //
 // Summation order (fixed, independent of B, of the lane split, of the row
@@ -146,7 +146,7 @@ struct HopArgs {
     int32_t heavy_t;
 };
 
-// Alg. 2 lines 10-11 for hop `ell` and launch source q (slice q / B, column
+// Algorithm 2's accumulation of Eq. 9 for hop `ell` and launch source q (slice q / B, column
 // q % B): for source i = s_b and each entry k = (i -> j) the unscaled half term
 // p_l(v_i,v_i) - p_l(v_j,v_i) is added to g[k] while ell <= tau[k]; t1, t2
 // keep the terms of hops tau+1, tau+2 (mode 0) or tau-1, tau (mode 1). (The
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
     }
 }
 
-// X_1 = P e_s for each source s of the launch (Alg. 2 line 2 followed by the
+// X_1 = P e_s for each source s of the launch (Algorithm 2's initialisation followed by the
 // first hop): X_1[j, b] = 1/d_j for j in N(s_b). X_1 must be zero on entry.
 // One CTA per source.
 template <typename T, int B>
@@ -449,7 +449,7 @@ __device__ __forceinline__ double hop_value(const int32_t *__restrict__ row_ptr,
 }
 
 // The last hop of a block, fused with the gathers of X_{ell-1} and X_ell
-// (ell = the block's last hop, Alg. 2 lines 6-11): X_ell is only read at each
+// (ell = the block's last hop, Algorithm 2's hop and accumulation): X_ell is only read at each
 // source and its neighbours, so only those values are computed, one warp per
 // value, instead of the whole n x B block. One CTA per source; the values are
 // those of a full hop (hop_value), so the result is bit for bit the one of

@@ -8,8 +8,8 @@
 //     Krylov space never contains them. The tridiagonal Ritz problem is
 //     solved on the host (Sturm bisection for the two extreme Ritz values,
 //     inverse iteration for the last component of their Ritz vectors).
-// A3: Eq. (6) with omega = 2, Upsilon = Delta_t = 0 (Alg. 1 line 1), rounded
-//     up to an odd integer (Eq. 5); per-source maximum (Alg. 2 line 4).
+// A3: Eq. (6) with omega = 2, Upsilon = Delta_t = 0 (Algorithm 1's initial length), rounded
+//     up to an odd integer (Eq. 5); per-source maximum (Algorithm 2's per-source length).
 #include <algorithm>
 #include <cmath>
 #include <vector>

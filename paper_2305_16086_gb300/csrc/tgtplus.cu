@@ -123,7 +123,7 @@ void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, cons
     g->last_walk_steps = h_cnt[2];
 }
 
-// Alg. 4 lines 12-17 for the launch's sources: the entries' walk pairs are cut
+// Algorithm 4's walk phase for the launch's sources: the entries' walk pairs are cut
 // into chunks of kWalkChunk (planned on the host from the packed counts), one
 // warp per chunk, and each entry adds its chunk sums in chunk order.
 // Returns the number of walk pairs drawn.

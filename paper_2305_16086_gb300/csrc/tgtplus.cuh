@@ -423,7 +423,7 @@ __global__ void k_walk_chunks(const T *__restrict__ x, const WalkArgs a, const W
     if (lane == 0) c.chunk_sum[ch] = acc;
 }
 
-// g[k] += (sum of the entry's chunk sums, in chunk order) / R_k  (Alg. 4 line 17)
+// g[k] += (sum of the entry's chunk sums, in chunk order) / R_k  (Algorithm 4's walk estimate)
 static __global__ void k_walk_finish(const int32_t *__restrict__ entry_k, const int32_t *__restrict__ entry_chunk0,
                               int32_t nentries, const double *__restrict__ chunk_sum,
                               const long long *__restrict__ walk_count, double *__restrict__ g) {

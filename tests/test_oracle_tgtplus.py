@@ -4,8 +4,8 @@
   * Lemma 4.1 (g_tau = g_tt + g_{tt->tau}) and the unbiasedness of X (Eq. 11)
     against exact matrix powers.
   * Lemma 4.3 / Eq. 17 against exhaustive enumeration of every walk.
-  * rho_hat >= rho (Eq. 16 by brute force), and a case where the literal
-    line 4 of Alg. 3 falls below rho.
+  * rho_hat >= rho (Eq. 16 by brute force), and a case where Algorithm 3's
+    rho_hat, taken literally, falls below rho.
   * Eq. 13's Hoeffding guarantee over many seeds.
 """
 import itertools
@@ -165,7 +165,7 @@ def test_full_tgt_plus_within_eps_on_small_graph():
 
     _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
     eps = 0.05
-    tau = truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam)  # Alg. 4 line 2
+    tau = truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam)  # Algorithm 4 sets the lengths for eps / 2
     ghat = np.zeros(g.nnz)
     for i in range(g.n):
         a, b = g.row_ptr[i], g.row_ptr[i + 1]
