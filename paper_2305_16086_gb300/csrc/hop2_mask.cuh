@@ -1,5 +1,5 @@
 // The second hop of a block computed from its sources alone (no stored X_1
-// block), for the single-graph driver.
+// block), for the single-graph block loop.
 #pragma once
 
 #include "propagate.cuh"

@@ -1083,7 +1083,7 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
 }
 
 // ---------------------------------------------------------------------------
-// the driver
+// sc_all_edges
 // ---------------------------------------------------------------------------
 static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep,
                            double *rec_all = nullptr, int rec_stride = 0) {

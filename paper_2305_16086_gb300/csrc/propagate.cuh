@@ -1,6 +1,6 @@
 // Kernels of the truncated graph traversal (Algorithm 2), shared by the
-// single-graph driver (propagate.cu), the allocation-free driver and the
-// batched driver.
+// single-graph entry point (propagate.cu), the allocation-free one and the
+// batched one.
 //
 // Layout: a block of B sources is an n x B row-major matrix X (node x's B
 // probabilities p_l(x, s_b) contiguous, rows 16-byte aligned); S = slices x B
