@@ -88,27 +88,31 @@ __global__ void __launch_bounds__(kChiScanThreads)
         val[s * NT] = -INFINITY;
         id[s * NT] = INT32_MAX;
     }
-    double vmin = INFINITY, vmax = -INFINITY;
+    // the scan compares in the block's arithmetic type V (widening to double is
+    // exact and order-preserving, so every decision is the one in double; this
+    // keeps the FP64 units, slow on this GPU, out of the per-element loop)
+    using V = typename AccOf<T>::type;
+    V vmin = V(INFINITY), vmax = V(-INFINITY), thr = V(-INFINITY);  // thr: the list's last value
     long long vol = 0;
     for (int32_t rb = r0 + sub; rb < r1; rb += TPC * BATCH) {
-        double v[BATCH];
+        V v[BATCH];
         int32_t d[BATCH];
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             const int32_t r = rb + u * TPC;
-            v[u] = r < r1 ? static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B + c])) : -INFINITY;
+            v[u] = r < r1 ? to_acc(xs[static_cast<int64_t>(r) * B + c]) : V(-INFINITY);
             d[u] = r < r1 ? row_ptr[r + 1] - row_ptr[r] : 0;
         }
-#pragma unroll 1
+#pragma unroll
         for (int u = 0; u < BATCH; ++u) {
             const int32_t r = rb + u * TPC;
             if (r < r1) {
-                vmin = fmin(vmin, v[u]);
-                vmax = fmax(vmax, v[u]);
-                if (v[u] != 0.0) vol += d[u];
+                vmin = min(vmin, v[u]);
+                vmax = max(vmax, v[u]);
+                if (v[u] != V(0)) vol += d[u];
                 // rows arrive in increasing order: a tie never beats the last slot
-                if (v[u] > val[(kGammaMax - 1) * NT]) {
-                    double cv = v[u];
+                if (v[u] > thr) {
+                    double cv = static_cast<double>(v[u]);
                     int32_t ci = r;
 #pragma unroll 1
                     for (int s = 0; s < kGammaMax; ++s) {
@@ -121,12 +125,13 @@ __global__ void __launch_bounds__(kChiScanThreads)
                             ci = ti;
                         }
                     }
+                    thr = static_cast<V>(val[(kGammaMax - 1) * NT]);  // exact: list values come from V
                 }
             }
         }
     }
-    smin[threadIdx.x] = vmin;
-    smax[threadIdx.x] = vmax;
+    smin[threadIdx.x] = static_cast<double>(vmin);
+    smax[threadIdx.x] = static_cast<double>(vmax);
     svol[threadIdx.x] = vol;
     __syncthreads();
     for (int half = TPC / 2; half > 0; half >>= 1) {  // tree of sorted merges over the column's threads
