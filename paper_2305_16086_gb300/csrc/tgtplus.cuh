@@ -22,22 +22,6 @@ __device__ __forceinline__ bool better(double v, int32_t x, double w, int32_t y)
     return v > w || (v == w && x < y);
 }
 
-// insert (v, x) into the descending list (val, id) of length kGammaMax
-__device__ __forceinline__ void top_insert(double *val, int32_t *id, double v, int32_t x) {
-    if (!better(v, x, val[kGammaMax - 1], id[kGammaMax - 1])) return;
-#pragma unroll
-    for (int s = 0; s < kGammaMax; ++s) {
-        if (better(v, x, val[s], id[s])) {
-            const double tv = val[s];
-            const int32_t ti = id[s];
-            val[s] = v;
-            id[s] = x;
-            v = tv;
-            x = ti;
-        }
-    }
-}
-
 // a := the kGammaMax best of the two sorted (descending) lists a and b; list
 // element s of a sits at av[s * as] (strided, so that the lists of the threads
 // of a warp interleave across shared-memory banks)
