@@ -22,10 +22,32 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_to(_SRC, tmp)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def compile_to(src: str, out: str) -> None:
+    """gcc -O2 with OpenMP into the shared library ``out``."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+
+
+def bind(path: str):
+    """Load a compiled oracle.c from ``path`` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    L.oracle_series.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32,
+                                ctypes.c_int32, i32p, f64p, f64p, f64p, ctypes.c_int32]
+    L.oracle_series.restype = ctypes.c_int
+    L.oracle_cg.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, i32p,
+                            ctypes.c_double, ctypes.c_int32, f64p, i32p, ctypes.c_int32]
+    L.oracle_cg.restype = ctypes.c_int
+    L.oracle_series_terms.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p,
+                                      ctypes.POINTER(ctypes.c_int64), f64p, ctypes.c_int32]
+    L.oracle_series_terms.restype = ctypes.c_int
+    return L
 
 
 def lib():
@@ -33,19 +55,7 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
-            i32p = ctypes.POINTER(ctypes.c_int32)
-            f64p = ctypes.POINTER(ctypes.c_double)
-            L.oracle_series.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32,
-                                        ctypes.c_int32, i32p, f64p, f64p, f64p, ctypes.c_int32]
-            L.oracle_series.restype = ctypes.c_int
-            L.oracle_cg.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, i32p,
-                                    ctypes.c_double, ctypes.c_int32, f64p, i32p, ctypes.c_int32]
-            L.oracle_cg.restype = ctypes.c_int
-            L.oracle_series_terms.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p,
-                                              ctypes.POINTER(ctypes.c_int64), f64p, ctypes.c_int32]
-            L.oracle_series_terms.restype = ctypes.c_int
-            _lib = L
+            _lib = bind(_LIB)
     return _lib
 
 

@@ -34,6 +34,16 @@ def test_features_on_named_graphs():
     assert np.allclose(F[:, 5], np.log(1 / (1 - 0.5)))
 
 
+def test_features_by_hand_on_lollipop():
+    # K4 on {0, 1, 2, 3} and the path 3 - 4 - 5: degrees 3, 3, 3, 4, 2, 1; 2m = 16
+    F = learned.features(*_csr(gg.lollipop(4, 2)), 0.4)
+    assert np.allclose(F[:, 0], np.log([3, 3, 3, 4, 2, 1]))
+    assert np.allclose(F[:, 1], np.log([3, 3, 3, 2, 1, 2]))  # smallest neighbour degree
+    assert np.allclose(F[:, 2], [1, 1, 1, 3 / 6, 0, 0])
+    assert np.allclose(F[:, 3], np.log(np.array([10, 10, 10, 11, 5, 2]) / 16))
+    assert np.allclose(F[:, 4], [(1 / 3 + 1 / 3 + 1 / 4) / 3] * 3 + [(3 / 3 + 1 / 2) / 4, (1 / 4 + 1) / 2, 1 / 2])
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_p2_feature_is_two_step_return_probability(seed):
     g = gg.tree_plus_gnp(50, 5.0, seed)

@@ -1,0 +1,301 @@
+"""Sensitivity of the oracle's pins: a plausible mistake planted anywhere in the
+oracle must make at least one pin fail.
+
+Each mutant is a copy of one oracle routine with one change a careful author
+could still make: a dropped term, a flipped sign, the wrong endpoint's degree,
+a transposed operand, an off-by-one length, a lost factor. The copy is built
+on the CPU (the C routines compiled into a scratch library, the Python modules
+executed from edited source) and swapped in for the duration of one test; the
+oracle on disk is never touched. The pins are the existing pin tests, called
+with fixed arguments. Only changes to what the paper or the mathematics fixes
+are planted: conventions of this implementation that the paper leaves open
+(which Philox counter feeds which walk) are pinned by the GPU tests' bit-exact
+comparison, not here. A control runs every battery on the unmodified oracle
+first, so that a battery cannot "kill" a mutant by being broken itself, and
+only the failures a wrong value causes count as kills (an assertion, or the
+oracle's own error for an impossible state), not a typo in the mutation.
+CPU only.
+"""
+from __future__ import annotations
+
+import inspect
+import os
+import sys
+import types
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle import _native, exact, learned, philox, series, tgtplus, truncation
+
+import test_oracle_exact as te
+import test_oracle_learned as tl
+import test_oracle_series as ts
+import test_oracle_tgtplus as tt
+
+KILLS = (AssertionError, RuntimeError, ValueError, FloatingPointError, np.linalg.LinAlgError,
+         ZeroDivisionError, OverflowError)
+
+# ---------------------------------------------------------------- batteries
+
+SERIES = [
+    ("K_n closed form", lambda: ts.test_complete_graph_closed_form(5, 3)),
+    ("C_n closed form", lambda: ts.test_cycle_closed_form(9, 5)),
+    ("exact rational series, lollipop", lambda: ts.test_matches_exact_rational_series(lambda: gg.lollipop(4, 2), 3)),
+    ("exact rational series, tree + G(n,p)",
+     lambda: ts.test_matches_exact_rational_series(lambda: gg.tree_plus_gnp(7, 3.0, 1), 6)),
+    ("odd-tau lower bound, monotone", lambda: ts.test_odd_tau_lower_bound_and_monotone(0)),
+    ("bipartite 1/m bias, end correction", lambda: ts.test_bipartite_bias_and_end_correction(8)),
+    ("end-corrected grid bounds", ts.test_end_corrected_grid_lower_bound_and_tail_bound),
+    ("plain tail bound", lambda: ts.test_plain_tail_bound(0)),
+    ("Theorem 3.2 guarantee", lambda: ts.test_theorem_3_2_eps_guarantee(1e-2, 0)),
+    ("per-entry lengths", ts.test_per_entry_lengths_match_global_runs),
+    ("tail bounds tight", ts.test_tail_bounds_are_tight_at_large_tau),
+]
+
+TRUNCATION = [
+    ("least odd length", ts.test_tau_is_smallest_odd_meeting_the_bound),
+    ("Theorem 3.2 guarantee", lambda: ts.test_theorem_3_2_eps_guarantee(1e-3, 1)),
+    ("C_n spectrum", lambda: ts.test_spectrum_cycle(8)),
+    ("named spectra", ts.test_spectrum_named),
+    ("ARPACK vs dense", ts.test_spectrum_sparse_path_matches_dense),
+]
+
+EXACT = [
+    ("enumeration = matrix tree = dense", lambda: te.test_kirchhoff_matches_matrix_tree_and_dense(te.SMALL[4])),
+    ("golden fractions", te.test_golden_fractions),
+    ("K_a,b closed form", lambda: te.test_complete_bipartite_closed_form(2, 3)),
+    ("bridges", te.test_bridges_are_one),
+    ("Foster", lambda: te.test_foster_random(0)),
+    ("CG and LU vs dense", lambda: te.test_cg_and_sparse_lu_match_dense(lambda: gg.tree_plus_gnp(300, 6.0, 5))),
+]
+
+TGTPLUS = [
+    ("Philox known answers", tt.test_philox_known_answers),
+    ("uniform index ends", tt.test_uniform_index_range_and_ends),
+    ("Lemma 4.1, unbiased walks", tt.test_lemma_4_1_and_unbiased_walk_estimator),
+    ("Lemma 4.3 by enumeration", lambda: tt.test_lemma_4_3_bounds_by_enumeration(0, 2)),
+    ("rho_hat bound", tt.test_rho_hat_upper_bound_and_literal_counterexample),
+    ("Eq. 15", tt.test_eq15_gamma_zero),
+    ("Eq. 13 Hoeffding", tt.test_walk_count_formula_and_hoeffding),
+    ("TGT+ within eps", tt.test_full_tgt_plus_within_eps_on_small_graph),
+]
+
+LEARNED = [
+    ("features on named graphs", tl.test_features_on_named_graphs),
+    ("features by hand", tl.test_features_by_hand_on_lollipop),
+    ("p2 feature = P^2", lambda: tl.test_p2_feature_is_two_step_return_probability(0)),
+    ("hop terms vs powers", tl.test_hop_terms_match_series_and_powers),
+    ("certified lengths", lambda: tl.test_certified_lengths(lambda: gg.tree_plus_gnp(500, 8.0, 2), 1e-2)),
+    ("gradient vs finite differences", tl.test_mlp_gradient_matches_finite_differences),
+    ("Adam first step", tl.test_adam_first_step_closed_form),
+]
+
+BATTERIES = {"series": SERIES, "truncation": TRUNCATION, "exact": EXACT, "tgtplus": TGTPLUS,
+             "learned": LEARNED}
+
+
+def _first_kill(battery):
+    """Name of the first pin that fails, else None."""
+    for name, fn in battery:
+        try:
+            fn()
+        except KILLS:
+            return name
+    return None
+
+
+# ---------------------------------------------------------------- mutants
+# (id, target, battery, old text, new text); target "c" edits oracle/csrc/oracle.c,
+# otherwise the named oracle module. The old text must occur exactly once.
+
+C_MUTANTS = [
+    ("hop term sign", "series",
+     "const double term = p_next[i] / d_i - p_next[j] / d_i;",
+     "const double term = p_next[j] / d_i - p_next[i] / d_i;"),
+    ("neighbour term over d_j", "series",
+     "const double term = p_next[i] / d_i - p_next[j] / d_i;",
+     "const double term = p_next[i] / d_i - p_next[j] / (double)(row_ptr[j + 1] - row_ptr[j]);"),
+    ("hop 0 dropped", "series",
+     "g_out[k] = 1.0 / d_i;",
+     "g_out[k] = 0.0;"),
+    ("one hop short", "series",
+     "if (l <= tau[k]) g_out[k] += term;",
+     "if (l < tau[k]) g_out[k] += term;"),
+    ("one hop long", "series",
+     "if (l <= tau[k]) g_out[k] += term;",
+     "if (l <= tau[k] + 1) g_out[k] += term;"),
+    ("push over the sender's degree (P transposed)", "series",
+     "p_next[x] += pj / d_x;",
+     "p_next[x] += pj / (double)(row_ptr[j + 1] - row_ptr[j]);"),
+    ("source length = min over its edges", "series",
+     "if (tau[k] > tau_p) tau_p = tau[k];",
+     "if (k == k0 || tau[k] < tau_p) tau_p = tau[k];"),
+    ("first omitted term taken one hop late", "series",
+     "else if (l == tau[k] + 1) { if (t1_out) t1_out[k] = term; }",
+     "else if (l == tau[k] + 2) { if (t1_out) t1_out[k] = term; }"),
+    ("resistance read as x_u + x_v", "exact",
+     "r_out[t] = x[a] - x[b];",
+     "r_out[t] = x[a] + x[b];"),
+    ("signless Laplacian", "exact",
+     "acc -= x[col_idx[e]];",
+     "acc += x[col_idx[e]];"),
+    ("per-hop term sign", "learned",
+     "= p_next[i] / d_i - p_next[col_idx[k]] / d_i;",
+     "= p_next[col_idx[k]] / d_i - p_next[i] / d_i;"),
+    ("per-hop terms from hop 1 on", "learned",
+     "o[(int64_t)(k - k0) * (L + 1)] = 1.0 / d_i;",
+     "o[(int64_t)(k - k0) * (L + 1)] = 0.0;"),
+]
+
+PY_MUTANTS = [
+    # series.py
+    ("series", "halves: g(i,j) twice", "series", "s = g + g[rev]", "s = g + g"),
+    ("series", "end correction: whole term", "series", "s = s + 0.5 * tf1", "s = s + tf1"),
+    ("series", "end-corrected bound without the 2", "series",
+     "return q / (2.0 * (1.0 - lam_plus))", "return q / (1.0 - lam_plus)"),
+    ("series", "plain bound over 1 - lambda", "series",
+     "return q / (1.0 - lam_star * lam_star)", "return q / (1.0 - lam_star)"),
+    # truncation.py
+    ("truncation", "Eq. 6 without the -1", "truncation",
+     "(1.0 - lam * lam))) / math.log(1.0 / lam) - 1.0", "(1.0 - lam * lam))) / math.log(1.0 / lam)"),
+    ("truncation", "Eq. 6 over 1 - lambda", "truncation",
+     "(eps * (1.0 - lam * lam))", "(eps * (1.0 - lam))"),
+    ("truncation", "X_e sign", "truncation",
+     "x_e = 1.0 / d_i + 1.0 / d_j - 2.0 / (d_i * d_j)", "x_e = 1.0 / d_i + 1.0 / d_j + 2.0 / (d_i * d_j)"),
+    ("truncation", "rounded to even", "truncation",
+     "np.where(t % 2 == 0, t + 1, t)", "np.where(t % 2 == 1, t + 1, t)"),
+    ("truncation", "lambda_plus = 1 (trivial mode kept)", "truncation",
+     "lam_plus = float(w[-2])", "lam_plus = float(w[-1])"),
+    ("truncation", "lambda_star without the modulus", "truncation",
+     "lam_star = max(abs(lam_plus), abs(lam_minus))", "lam_star = max(lam_plus, lam_minus)"),
+    ("truncation", "ARPACK: lambda_minus from the wrong end", "truncation",
+     'which="SA"', 'which="LA"'),
+    # exact.py
+    ("exact", "resistance without the cross factor 2", "exact",
+     "dg[rows] + dg[cols] - 2.0 * m[rows, cols]", "dg[rows] + dg[cols] - m[rows, cols]"),
+    ("exact", "grounding deletes the first row, the last column", "exact",
+     "return lap[:-1, :-1]", "return lap[1:, :-1]"),
+    ("exact", "enumeration counts cyclic subsets", "exact",
+     "continue  # n-1 acyclic edges on n nodes always span", "pass"),
+    ("exact", "matrix tree: T(G-e)/T(G) itself", "exact",
+     "out[e] = 1 - Fraction(_spanning_tree_count(n, rest), total)",
+     "out[e] = Fraction(_spanning_tree_count(n, rest), total)"),
+    ("exact", "sparse LU: x_u + x_v", "exact",
+     "x[pp[:, 0], np.arange(pp.shape[0])] - x[pp[:, 1], np.arange(pp.shape[0])]",
+     "x[pp[:, 0], np.arange(pp.shape[0])] + x[pp[:, 1], np.arange(pp.shape[0])]"),
+    # philox.py
+    ("philox", "Philox words swapped", "tgtplus",
+     "c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]", "c = [hi0 ^ c[1] ^ k0, lo0, hi1 ^ c[3] ^ k1, lo1]"),
+    ("philox", "Philox key not advanced", "tgtplus", "k1 = k1 + W1", "k1 = k1"),
+    ("philox", "neighbour index by modulo", "tgtplus",
+     "return ((np.asarray(u32, dtype=np.uint64) * np.asarray(d, dtype=np.uint64)) >> np.uint64(32)).astype(np.int64)",
+     "return (np.asarray(u32, dtype=np.uint64) % np.asarray(d, dtype=np.uint64)).astype(np.int64)"),
+    # tgtplus.py
+    ("tgtplus", "LB with L terms of min p", "tgtplus",
+     "lb = nb.min() + (L - 1) * p.min()", "lb = nb.min() + L * p.min()"),
+    ("tgtplus", "UB with L - 2 terms of rho", "tgtplus",
+     "(L - 1) * rho / 2.0", "(L - 2) * rho / 2.0"),
+    ("tgtplus", "UB without the halving", "tgtplus",
+     "ub = nb.max() / 2.0 + p.max() / 2.0", "ub = nb.max() / 2.0 + p.max() / 4.0"),
+    ("tgtplus", "rho_hat as printed (edges inside C only)", "tgtplus",
+     "    return max(best, two)", "    return best if best > -np.inf else two"),
+    ("tgtplus", "candidates = smallest entries", "tgtplus",
+     "order = np.lexsort((np.arange(p.size), -p))", "order = np.lexsort((np.arange(p.size), p))"),
+    ("tgtplus", "Eq. 13 constant 4", "tgtplus",
+     "r = 8.0 * chi * chi", "r = 4.0 * chi * chi"),
+    ("tgtplus", "Eq. 13 union bound over m / delta", "tgtplus",
+     "math.log(2.0 * m / delta)", "math.log(m / delta)"),
+    ("tgtplus", "walk counts its start node", "tgtplus",
+     "        cur = col_idx[row_ptr[cur] + idx]\n        total += p[cur]\n",
+     "        total += p[cur]\n        cur = col_idx[row_ptr[cur] + idx]\n"),
+    ("tgtplus", "walk estimate sign", "tgtplus",
+     "return float(np.mean(si - sj))", "return float(np.mean(sj - si))"),
+    ("tgtplus", "source column pushed over the sender's degree", "tgtplus",
+     "            q[nb] += p[v] / deg[nb]\n        p = q\n    return p",
+     "            q[nb] += p[v] / deg[v]\n        p = q\n    return p"),
+    ("tgtplus", "Eq. 15 without the factor L", "tgtplus",
+     "return 2.0 * L * (p.max() - p.min())", "return 2.0 * (p.max() - p.min())"),
+    # learned.py
+    ("learned", "triangles counted twice", "learned", "        tri //= 2", "        tri //= 1"),
+    ("learned", "largest neighbour degree", "learned",
+     "F[i, 1] = math.log(deg[nb].min())", "F[i, 1] = math.log(deg[nb].max())"),
+    ("learned", "p2 feature without 1/d_i", "learned",
+     "F[i, 4] = np.sum(1.0 / deg[nb]) / d", "F[i, 4] = np.sum(1.0 / deg[nb])"),
+    ("learned", "volume feature over m", "learned",
+     "F[i, 3] = math.log(deg[nb].sum() / two_m)", "F[i, 3] = math.log(2.0 * deg[nb].sum() / two_m)"),
+    ("learned", "backprop through W2 transposed", "learned",
+     "dh1 = (dh2 @ W2) * (z1 > 0)", "dh1 = (dh2 @ W2.T) * (z1 > 0)"),
+    ("learned", "ReLU gate of layer 2 dropped", "learned",
+     "dh2 = np.outer(dy, W3) * (z2 > 0)", "dh2 = np.outer(dy, W3)"),
+    ("learned", "Adam without bias correction", "learned",
+     "mhat = m / (1 - b1 ** t)", "mhat = m"),
+    ("learned", "certificate from one term", "learned",
+     "(factor * (full[:, t - 1] + full[:, t]) <= eps)", "(factor * full[:, t] <= eps)"),
+]
+
+
+# ---------------------------------------------------------------- machinery
+
+def _edit(src, old, new):
+    assert src.count(old) == 1, f"mutation anchor must occur once: {old!r}"
+    return src.replace(old, new)
+
+
+def _swap_module(monkeypatch, orig, mutant):
+    """Point every loaded oracle and test module at the mutant: module globals
+    bound to ``orig`` and functions imported from it by name."""
+    monkeypatch.setitem(sys.modules, orig.__name__, mutant)
+    monkeypatch.setattr(oracle, orig.__name__.rsplit(".", 1)[1], mutant)
+    for mod in list(sys.modules.values()):
+        name = getattr(mod, "__name__", "")
+        if mod is mutant or not (name.startswith("oracle") or name.startswith("test_")):
+            continue
+        for k, v in list(vars(mod).items()):
+            if v is orig:
+                monkeypatch.setattr(mod, k, mutant)
+            elif callable(v) and getattr(v, "__module__", None) == orig.__name__ and getattr(orig, k, None) is v:
+                monkeypatch.setattr(mod, k, getattr(mutant, k))
+
+
+def _py_mutant(orig, old, new):
+    src = _edit(inspect.getsource(orig), old, new)
+    mod = types.ModuleType(orig.__name__)
+    mod.__file__ = orig.__file__
+    mod.__package__ = "oracle"
+    exec(compile(src, orig.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def c_source():
+    with open(os.path.join(os.path.dirname(oracle.__file__), "csrc", "oracle.c")) as fh:
+        return fh.read()
+
+
+@pytest.mark.parametrize("battery", sorted(BATTERIES))
+def test_control_batteries_pass_on_the_oracle(battery):
+    assert _first_kill(BATTERIES[battery]) is None
+
+
+@pytest.mark.parametrize("mid,battery,old,new", C_MUTANTS, ids=[m[0] for m in C_MUTANTS])
+def test_c_mutant_is_killed(mid, battery, old, new, c_source, tmp_path, monkeypatch):
+    src = tmp_path / "oracle_mutant.c"
+    src.write_text(_edit(c_source, old, new))
+    so = str(tmp_path / "liboracle_mutant.so")
+    _native.compile_to(str(src), so)
+    monkeypatch.setattr(_native, "_lib", _native.bind(so))
+    assert _first_kill(BATTERIES[battery]) is not None, f"no pin fails for C mutant: {mid}"
+
+
+MODULES = {"series": series, "truncation": truncation, "exact": exact, "philox": philox,
+           "tgtplus": tgtplus, "learned": learned}
+
+
+@pytest.mark.parametrize("module,mid,battery,old,new", PY_MUTANTS, ids=[m[1] for m in PY_MUTANTS])
+def test_py_mutant_is_killed(module, mid, battery, old, new, monkeypatch):
+    orig = MODULES[module]
+    _swap_module(monkeypatch, orig, _py_mutant(orig, old, new))
+    assert _first_kill(BATTERIES[battery]) is not None, f"no pin fails for mutant of {module}: {mid}"

@@ -150,6 +150,45 @@ def test_theorem_3_2_eps_guarantee(eps, seed):
     assert np.array_equal(tau, tau[rev]) and np.all(tau % 2 == 1)
 
 
+def test_per_entry_lengths_match_global_runs():
+    """Truncation is per edge: an entry with length t holds exactly the value a
+    run with the one global length t gives it (both halves at the same t),
+    whatever the lengths of the other edges of its endpoints."""
+    g = gg.tree_plus_gnp(60, 4.0, 6)
+    rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
+    rng = np.random.default_rng(6)
+    tau = 2 * rng.integers(0, 5, g.nnz) + 1
+    tau = np.where(np.arange(g.nnz) < rev, tau, tau[rev])  # one length per undirected edge
+    s_mix, q_mix = _entries(g, tau)
+    for t in np.unique(tau):
+        s_t, q_t = _entries(g, int(t))
+        sel = tau == t
+        assert np.max(np.abs(s_mix[sel] - s_t[sel])) < 1e-15
+        assert np.max(np.abs(q_mix[sel] - q_t[sel])) < 1e-15
+
+
+def test_tail_bounds_are_tight_at_large_tau():
+    """For odd tau the tail is sum_k c_k lambda_k^(tau+1) / (1 - lambda_k) and the
+    observed pair q = sum_k c_k (1 + lambda_k) lambda_k^(tau+1) (c_k >= 0, proof
+    of Theorem 3.2). As tau grows the modes of largest |lambda_k| dominate both,
+    so tail / bound tends to 1 on an edge those modes reach: the plain bound
+    q / (1 - lambda_star^2) and, on a bipartite graph (lambda = -1 cancelled,
+    lambda_plus the slowest mode left), the end-corrected q / (2 (1 - lambda_plus))
+    are asymptotically exact, not merely valid."""
+    g = gg.tree_plus_gnp(200, 6.0, 0)
+    r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
+    lam_plus, _, lam_star = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
+    s, q = _entries(g, 41)
+    ratio = (r - s) / series.tail_bound(q, lam_star, lam_plus, False)
+    assert 0.95 <= np.max(ratio) <= 1.0 + 1e-6
+    h = gg.perturbed_grid(8, 9, 0.05, 3)
+    r = exact.exact_dense(h.n, h.row_ptr, h.col_idx)
+    lam_plus, _, _ = truncation.spectrum_extremes(h.n, h.row_ptr, h.col_idx)
+    s_hat, q = _entries(h, 101, end_corrected=True)
+    ratio = (r - s_hat) / series.tail_bound(q, 1.0, lam_plus, True)
+    assert 0.95 <= np.max(ratio) <= 1.0 + 1e-6
+
+
 def test_tau_is_smallest_odd_meeting_the_bound():
     """Eq. (6) inverted: tau is the least odd t >= 1 whose a-priori tail bound
     X_e lam^(t+1) / (1 - lam^2) is <= eps (proof of Thm. 3.2)."""
@@ -181,8 +220,11 @@ def test_spectrum_cycle(n):
 def test_spectrum_named():
     lp, lm, _ = truncation.spectrum_extremes(*_csr(gg.complete(9)))
     assert abs(lp + 1 / 8) < 1e-12 and abs(lm + 1 / 8) < 1e-12
-    lp, lm, _ = truncation.spectrum_extremes(*_csr(gg.petersen()))
+    lp, lm, ls = truncation.spectrum_extremes(*_csr(gg.petersen()))
     assert abs(lp - 1 / 3) < 1e-12 and abs(lm + 2 / 3) < 1e-12
+    assert abs(ls - 2 / 3) < 1e-12  # lambda_star is the larger modulus, here the negative end
+    _, _, ls = truncation.spectrum_extremes(*_csr(gg.cycle(9)))
+    assert abs(ls - np.cos(np.pi / 9)) < 1e-12  # odd cycle: |cos(2 pi 4 / 9)| > cos(2 pi / 9)
     lp, lm, _ = truncation.spectrum_extremes(*_csr(gg.hypercube(4)))
     assert abs(lp - 0.5) < 1e-12 and abs(lm + 1.0) < 1e-12
 

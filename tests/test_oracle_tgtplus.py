@@ -62,6 +62,7 @@ def test_lemma_4_1_and_unbiased_walk_estimator():
     g_tau = sum(Pl[l][i, i] - Pl[l][j, i] for l in range(tau + 1))
     g_tt = sum(Pl[l][i, i] - Pl[l][j, i] for l in range(tt + 1))
     p = Pl[tt][:, i]  # p_tt(x, v_i)
+    assert np.allclose(tgtplus.source_column(g.n, g.row_ptr, g.col_idx, i, tt), p, rtol=0, atol=1e-15)
     # Eq. 10 (times d_i): sum_x p_tt(x,i) sum_{l=1}^{tau-tt} (p_l(i,x) - p_l(j,x))
     g_tail = sum(p[x] * (Pl[l][i, x] - Pl[l][j, x]) for x in range(g.n) for l in range(1, tau - tt + 1))
     assert abs(g_tau - (g_tt + g_tail)) < 1e-14
@@ -135,11 +136,13 @@ def test_eq15_gamma_zero():
 
 
 def test_walk_count_formula_and_hoeffding():
-    # Eq. 13 is the Hoeffding count for deviation eps/4 with range chi/d_i
-    chi, d, m, delta, eps = 0.02, 7, 1000, 1e-3, 0.01
-    R = tgtplus.walk_count(chi, d, m, delta, eps)
-    assert 2 * math.exp(-2 * R * (eps / 4) ** 2 / (chi / d) ** 2) <= delta / m * (1 + 1e-9)
-    assert 2 * math.exp(-2 * (R - 1) * (eps / 4) ** 2 / (chi / d) ** 2) > delta / m
+    # Eq. 13 is the least Hoeffding count for deviation eps/4 with range chi/d_i
+    # and failure probability delta/m per half-edge estimate
+    for chi, d, m, delta, eps in ((0.02, 7, 1000, 1e-3, 0.01), (0.05, 7, 1000, 1e-3, 0.01),
+                                  (0.3, 2, 50_000, 2e-5, 1e-3), (1e-3, 40, 10, 0.1, 0.05)):
+        R = tgtplus.walk_count(chi, d, m, delta, eps)
+        assert 2 * math.exp(-2 * R * (eps / 4) ** 2 / (chi / d) ** 2) <= delta / m * (1 + 1e-9)
+        assert R == 1 or 2 * math.exp(-2 * (R - 1) * (eps / 4) ** 2 / (chi / d) ** 2) > delta / m
     # empirical: over many seeds the estimate stays within eps/4 of its mean
     g = gg.tree_plus_gnp(40, 5.0, 4)
     i = 3
