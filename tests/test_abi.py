@@ -94,6 +94,51 @@ def test_struct_layouts_match_c(tmp_path):
             assert getattr(py[sname], field).offset == int(val), key
 
 
+CONSTS_C = r"""
+#include <stdio.h>
+#include "sc.h"
+#define P(x) printf("%s %lld\n", #x, (long long)(x));
+int main(void) {
+  P(SC_OK) P(SC_ERR_INVALID_ARG) P(SC_ERR_BAD_CSR) P(SC_ERR_NOT_SYMMETRIC) P(SC_ERR_SELF_LOOP)
+  P(SC_ERR_DUPLICATE_EDGE) P(SC_ERR_ISOLATED_NODE) P(SC_ERR_DISCONNECTED) P(SC_ERR_BIPARTITE)
+  P(SC_ERR_LAMBDA_NOT_CONVERGED) P(SC_ERR_BOUND_UNMET) P(SC_ERR_TIMEOUT) P(SC_ERR_OOM) P(SC_ERR_CUDA)
+  P(SC_ERR_UNSUPPORTED)
+  P(SC_PTRS_HOST) P(SC_PTRS_DEVICE) P(SC_FLAG_REJECT_BIPARTITE)
+  P(SC_ELL_GLOBAL) P(SC_ELL_PER_EDGE) P(SC_ELL_FIXED) P(SC_ELL_LEARNED)
+  P(SC_PREC_FP64) P(SC_PREC_FP32) P(SC_PREC_BF16) P(SC_EST_PLAIN) P(SC_EST_END_CORRECTED)
+  P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER)
+  P(SC_OUT_DEVICE) P(SC_OPT_RECORD_TAIL) P(SC_OPT_TIME_KERNELS) P(SC_OPT_WINDOWS_OFF) P(SC_OPT_WINDOWS_FORCE)
+  P(SC_MLP_PARAMS) P(SC_MLP_FEATURES) P(SC_MLP_MODEL_FLOATS)
+  return 0;
+}
+"""
+
+
+def test_header_constants_match_binding(tmp_path):
+    """Every status, flag and enum value the binding mirrors equals the header's."""
+    src = tmp_path / "consts.c"
+    src.write_text(CONSTS_C)
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {k: int(v) for k, v in (line.split() for line in out if line.strip())}
+    for code, name in binding.STATUS_NAMES.items():
+        assert c[name] == code, name
+    assert len(binding.STATUS_NAMES) == sum(1 for k in c if k == "SC_OK" or k.startswith("SC_ERR_"))
+    assert (c["SC_PTRS_HOST"], c["SC_PTRS_DEVICE"], c["SC_FLAG_REJECT_BIPARTITE"]) == (
+        binding.SC_PTRS_HOST, binding.SC_PTRS_DEVICE, binding.SC_FLAG_REJECT_BIPARTITE)
+    for table, prefix in ((binding.ELL, "SC_ELL_"), (binding.PREC, "SC_PREC_"), (binding.EST, "SC_EST_"),
+                          (binding.MODE, "SC_MODE_")):
+        assert {k.upper(): v for k, v in table.items()} == {k[len(prefix):]: v for k, v in c.items()
+                                                            if k.startswith(prefix)}, prefix
+    assert (c["SC_SWITCH_COST"], c["SC_SWITCH_PAPER"]) == (0, 1)  # the binding's switch="cost" / "paper"
+    for name in ("SC_OUT_DEVICE", "SC_OPT_RECORD_TAIL", "SC_OPT_TIME_KERNELS", "SC_OPT_WINDOWS_OFF",
+                 "SC_OPT_WINDOWS_FORCE"):
+        assert c[name] == getattr(binding, name), name
+    assert (c["SC_MLP_PARAMS"], c["SC_MLP_FEATURES"], c["SC_MLP_MODEL_FLOATS"]) == (
+        binding.MLP_PARAMS, binding.MLP_FEATURES, binding.MLP_MODEL_FLOATS)
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError, match="libsc.so not found"):
