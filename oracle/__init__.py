@@ -11,7 +11,8 @@ Modules:
               theorem, grounded-Laplacian Cholesky, sparse LU, CG)
   series      truncated series of Eq. (2) by Algorithm 2, half sums of Eq. (9),
               end-corrected estimator and a-posteriori tail bounds
-  truncation  eigenvalue extremes and the truncation length of Eq. (5)-(6)
+  truncation  eigenvalue extremes and the truncation length of Eq. (5)-(6);
+              CalTau (Algorithm 1) with omega eigenpairs, Eq. (7)-(8)
   philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
   tgtplus     the TGT+ pieces: CalChi (Alg. 3), walk counts (Eq. 13), walk
               estimator (Eq. 11), switch rule (Eq. 14)

@@ -30,6 +30,7 @@ import graphgen as gg
 import oracle
 from oracle import _native, exact, learned, philox, series, tgtplus, truncation
 
+import test_oracle_caltau as tc
 import test_oracle_exact as te
 import test_oracle_learned as tl
 import test_oracle_series as ts
@@ -93,8 +94,20 @@ LEARNED = [
     ("Adam first step", tl.test_adam_first_step_closed_form),
 ]
 
+CALTAU = [
+    ("eigenpairs reproduce Eq. 2", lambda: tc.test_eigenpairs_reproduce_the_series_terms(lambda: gg.lollipop(5, 3))),
+    ("omega = 2 is Eq. 6", lambda: tc.test_omega_two_is_eq6(lambda: gg.lollipop(8, 3), 1e-2)),
+    ("bound exact at omega = n", lambda: tc.test_bound_is_the_exact_tail_with_every_eigenpair(
+        lambda: gg.tree_plus_gnp(40, 4.0, 3))),
+    ("bound holds from t", lambda: tc.test_bound_holds_for_every_odd_tau_from_t(5)),
+    ("Theorem 3.2, bottleneck", lambda: tc.test_theorem_3_2_with_caltau(lambda: gg.barbell(12, 1), 1e-2)),
+    ("Theorem 3.2, G(n,p)", lambda: tc.test_theorem_3_2_with_caltau(lambda: gg.gnp_lcc(200, 5.0, 2), 1e-3)),
+    ("bottleneck", tc.test_bottleneck_needs_far_fewer_hops),
+    ("direct search", lambda: tc.test_caltau_matches_a_direct_search(lambda: gg.lollipop(8, 3), 3)),
+]
+
 BATTERIES = {"series": SERIES, "truncation": TRUNCATION, "exact": EXACT, "tgtplus": TGTPLUS,
-             "learned": LEARNED}
+             "learned": LEARNED, "caltau": CALTAU}
 
 
 def _first_kill(battery):
@@ -164,7 +177,8 @@ PY_MUTANTS = [
     ("truncation", "Eq. 6 over 1 - lambda", "truncation",
      "(eps * (1.0 - lam * lam))", "(eps * (1.0 - lam))"),
     ("truncation", "X_e sign", "truncation",
-     "x_e = 1.0 / d_i + 1.0 / d_j - 2.0 / (d_i * d_j)", "x_e = 1.0 / d_i + 1.0 / d_j + 2.0 / (d_i * d_j)"),
+     "d_j = np.asarray(d_j, dtype=np.float64)\n    x_e = 1.0 / d_i + 1.0 / d_j - 2.0 / (d_i * d_j)",
+     "d_j = np.asarray(d_j, dtype=np.float64)\n    x_e = 1.0 / d_i + 1.0 / d_j + 2.0 / (d_i * d_j)"),
     ("truncation", "rounded to even", "truncation",
      "np.where(t % 2 == 0, t + 1, t)", "np.where(t % 2 == 1, t + 1, t)"),
     ("truncation", "lambda_plus = 1 (trivial mode kept)", "truncation",
@@ -173,6 +187,28 @@ PY_MUTANTS = [
      "lam_star = max(abs(lam_plus), abs(lam_minus))", "lam_star = max(lam_plus, lam_minus)"),
     ("truncation", "ARPACK: lambda_minus from the wrong end", "truncation",
      'which="SA"', 'which="LA"'),
+    # truncation.py: CalTau with omega eigenpairs (Algorithm 1, Eq. 6-8)
+    ("truncation", "eigenvalues sorted by value", "caltau",
+     "order = np.lexsort((-w, -np.abs(w)))[:omega]", "order = np.argsort(-w)[:omega]"),
+    ("truncation", "f_k without sqrt(2m)", "caltau",
+     "F = np.sqrt(deg.sum()) * (vec[:, order]", "F = (vec[:, order]"),
+    ("truncation", "Eq. 7 without 1 + lambda", "caltau",
+     "ups = ((1.0 + mid) @ c) / two_m", "ups = (np.ones_like(mid) @ c) / two_m"),
+    ("truncation", "Eq. 8 at lambda^t", "caltau",
+     "delta = ((mid ** (t + 1) / (1.0 - mid)) @ c[:, idx]) / two_m",
+     "delta = ((mid ** t / (1.0 - mid)) @ c[:, idx]) / two_m"),
+    ("truncation", "Eq. 8 over 1 + lambda", "caltau",
+     "delta = ((mid ** (t + 1) / (1.0 - mid)) @ c[:, idx]) / two_m",
+     "delta = ((mid ** (t + 1) / (1.0 + mid)) @ c[:, idx]) / two_m"),
+    ("truncation", "lambda_omega one place early", "caltau",
+     "lam_w = abs(lam[omega - 1])", "lam_w = abs(lam[omega - 2])"),
+    ("truncation", "spent budget read as nothing left", "caltau",
+     "spent = (budget < 0.0) | (~none_left & (budget == 0.0))", "spent = ~none_left & (budget <= 0.0)"),
+    ("truncation", "CalTau returns the previous t", "caltau",
+     "out[idx[stop]] = t\n", "out[idx[stop]] = t - 2\n"),
+    ("truncation", "X_e sign in CalTau", "caltau",
+     "d_i, d_j = deg[rows], deg[cols]\n    x_e = 1.0 / d_i + 1.0 / d_j - 2.0 / (d_i * d_j)",
+     "d_i, d_j = deg[rows], deg[cols]\n    x_e = 1.0 / d_i + 1.0 / d_j + 2.0 / (d_i * d_j)"),
     # exact.py
     ("exact", "resistance without the cross factor 2", "exact",
      "dg[rows] + dg[cols] - 2.0 * m[rows, cols]", "dg[rows] + dg[cols] - m[rows, cols]"),
