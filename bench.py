@@ -14,6 +14,7 @@ preprocessing from the run). The plain global-length arms (FP32 and FP64) are
 timed beside it for comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --mode tgt_plus --policy global     # Algorithm 4 on the same workload
 
 Prints one JSON line on rank 0. With N > 1 (torchrun) every rank runs an
 independent replica on its own GPU (the method has no exchange step between
@@ -287,7 +288,7 @@ def run_batch(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -308,7 +309,16 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    args = ap.parse_args()
+    ap.add_argument("--mode", default="tgt", choices=["tgt", "tgt_plus"],
+                    help="tgt: Algorithm 2; tgt_plus: Algorithm 4 (with --policy global, per_edge or fixed)")
+    args = ap.parse_args(argv)
+    if args.mode == "tgt_plus" and args.policy == "learned":
+        ap.error("--mode tgt_plus takes --policy global, per_edge or fixed (TGT+ sets its own lengths, Eq. 6 at eps/2)")
+    return args
+
+
+def main():
+    args = parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     world, rank, local = dist_setup()
@@ -335,7 +345,7 @@ def main():
     stream = torch.cuda.current_stream()
     run_kw = dict(eps=args.eps, precision=args.precision, policy=args.policy, block_width=args.block_width,
                   rows_split=args.rows_split, heavy_threshold=args.heavy_threshold, ell_fixed=args.ell,
-                  estimator=args.estimator)
+                  estimator=args.estimator, mode=args.mode)
 
     G = Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), stream=stream)
     lam = G.estimate_lambda(allow_unconverged=True)
@@ -413,12 +423,13 @@ def main():
                "ms_per_step": e2e_step,
                "includes": "graph create + validation + Lanczos + model load + features + all edges + D2H"}
 
-    # comparison arms: the plain global length in FP32 and FP64 (one warm-up, one timed step each)
+    # comparison arms: TGT (traversal only) at the plain global length in FP32 and FP64
+    # (one warm-up, one timed step each)
     arms = {}
     if not args.no_arms:
         arm_policy = "global" if args.policy == "learned" else args.policy
         for name, prec in ((f"{arm_policy}_fp32", "fp32"), (f"{arm_policy}_fp64", "fp64")):
-            kw = dict(run_kw, policy=arm_policy, precision=prec)
+            kw = dict(run_kw, policy=arm_policy, precision=prec, mode="tgt")
             G.all_edges(out=out, **kw)
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -444,7 +455,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "m": g.m, "eps": args.eps,
-                   "policy": args.policy, "estimator": args.estimator, "windowed": bool(rep0["windowed"]),
+                   "mode": args.mode, "policy": args.policy, "estimator": args.estimator,
+                   "windowed": bool(rep0["windowed"]),
                    "precision": f"{args.precision} blocks, fp64 accumulation",
                    "batching": f"{rep0['slices']} block(s) of {rep0['block_width']} sources per launch, "
                                f"{rep0['blocks']} blocks",
@@ -457,6 +469,10 @@ def main():
                     "edges_extended": rep0["edges_extended"], "max_tail_bound": rep0["max_tail_bound"],
                     "model": "trained on Barabasi-Albert n=50000 m0=10 seed 101, 400 Adam steps"}
         if args.policy == "learned" else None,
+        "tgt_plus": {"switch_after_hops": [rep0["tt_min"], rep0["tt_max"]], "walk_pairs": rep0["walks"],
+                     "walk_steps": rep0["walk_steps"], "switch_tests": rep0["switch_tests"],
+                     "switch_ms": rep0["switch_ms"], "walk_ms": rep0["walk_ms"]}
+        if args.mode == "tgt_plus" else None,
         "clocks": clk.summary(), "gpu_launches": int(sum(r["launches"] for r in reports)),
         "foster_mean_abs_error": ((g.n - 1) - rep0["foster_sum"]) / g.m,
     }

@@ -72,3 +72,15 @@ def test_reference_arm_other_ranks_do_nothing():
     with redirect_stdout(buf):
         assert bench.run_reference(Args(), 2, 1) is None
     assert buf.getvalue() == ""
+
+
+def test_arguments_default_and_tgt_plus_mode():
+    import bench
+
+    a = bench.parse_args([])
+    assert (a.gpus, a.mode, a.policy, a.workload, a.impl) == (1, "tgt", "learned", "ba_200k", "ours")
+    assert a.warmup >= 3
+    a = bench.parse_args(["--mode", "tgt_plus", "--policy", "global"])
+    assert (a.mode, a.policy) == ("tgt_plus", "global")
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--mode", "tgt_plus"])  # TGT+ sets its own lengths: no learned policy
