@@ -206,6 +206,36 @@ def replica_value(world: int, m: int, ms_per_step: float) -> float:
     return world * m / (ms_per_step / 1e3)
 
 
+def timed_passes(run_pass, warm: int, timed: int, sync, barrier):
+    """Run `warm` + `timed` passes of run_pass(mark); run_pass calls mark(name)
+    after each of its phases. The warm-up passes synchronize at every mark and
+    return the last one's phase times (ms); the timed passes run without those
+    synchronizations and return their wall times (ms), each bracketed by a
+    barrier and a synchronize."""
+    times, phases = [], {}
+    for i in range(warm + timed):
+        split = i < warm
+        marks = []
+
+        def mark(name):
+            if split:
+                sync()
+                marks.append((name, time.perf_counter()))
+
+        barrier()
+        t0 = time.perf_counter()
+        run_pass(mark)
+        sync()
+        if split:
+            prev, phases = t0, {}
+            for name, t in marks:
+                phases[name] = round((t - prev) * 1e3, 3)
+                prev = t
+        else:
+            times.append((time.perf_counter() - t0) * 1e3)
+    return times, phases
+
+
 def run_reference(args, world, rank):
     """The oracle on the host cores: each step a bounded sample of the workload."""
     if rank != 0:
@@ -405,23 +435,24 @@ def main():
         rp_h = torch.from_numpy(g.row_ptr).pin_memory()
         ci_h = torch.from_numpy(g.col_idx).pin_memory()
         out_h = torch.empty(g.nnz, dtype=torch.float64).pin_memory()
-        e2e_ms = []
-        for i in range(2 + min(args.steps, 3)):
-            barrier()
-            t0 = time.perf_counter()
+        def e2e_pass(mark):
             with Graph(rp_h, ci_h, stream=stream) as Gh:
+                mark("create_validate")
                 Gh.estimate_lambda(allow_unconverged=True)
+                mark("lanczos")
                 if model is not None:
                     binding.mlp_load(Gh, model)
+                mark("model_load")
                 Gh.all_edges(out=out_h, **run_kw)
-            torch.cuda.synchronize()
-            if i >= 2:
-                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                mark("all_edges_d2h")
+
+        e2e_ms, phases = timed_passes(e2e_pass, 2, min(args.steps, 3), torch.cuda.synchronize, barrier)
         e2e_step = max_over_ranks(pg, statistics.mean(e2e_ms), "cuda")
         e2e = {"value": replica_value(world, g.m, e2e_step), "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.nnz), "d2h_bytes_per_step": int(8 * g.nnz),
                "ms_per_step": e2e_step,
-               "includes": "graph create + validation + Lanczos + model load + features + all edges + D2H"}
+               "includes": "graph create + validation + Lanczos + model load + features + all edges + D2H",
+               "phases_ms_of_a_warmup_pass": phases}
 
     # comparison arms: TGT (traversal only) at the plain global length in FP32 and FP64
     # (one warm-up, one timed step each)

@@ -1,0 +1,148 @@
+"""bench.py's main path run on the CPU with the CUDA pieces replaced by fakes:
+the JSON line carries every key the benchmark contract asks for, in both
+modes, so that a mistake in the driver code shows up here rather than on the
+GPU. The numbers are the fakes' and mean nothing. CPU only."""
+import io
+import json
+import sys
+from contextlib import redirect_stdout
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import graphgen as gg  # noqa: E402
+
+
+class _Event:
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        pass
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 25.0
+
+
+def _report(kw):
+    return {"tt_min": 4, "tt_max": 5, "walks": 10, "walk_steps": 40, "switch_tests": 2, "switch_ms": 1.0,
+            "walk_ms": 0.5, "hop_ms": 20.0 if kw.get("time_kernels") else 0.0, "hop_bytes": 4.0e8,
+            "hop_launches": 4, "launches": 12, "foster_sum": 0.0, "ell_global": 7, "block_width": 64,
+            "rows_split": 1, "slices": 1, "blocks": 3, "windowed": 0, "source_hops": 700, "extension_rounds": 0,
+            "edges_extended": 0, "max_tail_bound": 1e-4}
+
+
+class _FakeGraph:
+    calls = []
+
+    def __init__(self, row_ptr, col_idx, stream=None, **kw):
+        self.n = len(row_ptr) - 1
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def close(self):
+        pass
+
+    def estimate_lambda(self, **kw):
+        return {"lambda_star": 0.43, "lambda_plus": 0.43, "lambda_minus": -0.3}
+
+    def all_edges(self, out=None, **kw):
+        _FakeGraph.calls.append(kw)
+        rep = _report(kw)
+        rep["foster_sum"] = float(self.n - 1)
+        return out, None, rep
+
+
+class _Clock:
+    def __init__(self, dev):
+        pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def summary(self):
+        return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+
+@pytest.fixture
+def fake_cuda(monkeypatch):
+    import bench
+    import paper_2305_16086_gb300 as pkg
+    from paper_2305_16086_gb300 import binding
+
+    real_empty = torch.empty
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda *a, **k: 0)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda.nvtx, "range_push", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda.nvtx, "range_pop", lambda *a, **k: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: real_empty(*a, **k) if not a or a[0] < (1 << 20)
+                        else real_empty(16, dtype=k.get("dtype")))
+    monkeypatch.setattr(pkg, "Graph", _FakeGraph)
+    monkeypatch.setattr(binding, "mlp_load", lambda *a, **k: None)
+    monkeypatch.setattr(bench, "train_model", lambda *a, **k: np.zeros(binding.MLP_MODEL_FLOATS, np.float32))
+    monkeypatch.setattr(bench, "ClockSampler", _Clock)
+    monkeypatch.setattr(bench, "cpu_baseline", lambda g, ell, target_s=10.0: {
+        "value": 1.0, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": "fake"})
+    monkeypatch.setitem(bench.WORKLOADS, "ba_200k", dict(desc="tiny stand-in", make=lambda g: gg.barabasi_albert(300, 3, 1)))
+    _FakeGraph.calls = []
+    return bench
+
+
+def _run(bench, argv):
+    buf = io.StringIO()
+    old = sys.argv
+    sys.argv = ["bench.py"] + argv
+    try:
+        with redirect_stdout(buf):
+            bench.main()
+    finally:
+        sys.argv = old
+    lines = [l for l in buf.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+CONTRACT = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"}
+
+
+def test_default_line_has_every_contract_key(fake_cuda):
+    d = _run(fake_cuda, ["--steps", "2", "--warmup", "3"])
+    assert CONTRACT <= set(d)
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
+    assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"} and d["cpu_baseline"]["kind"] == "oracle"
+    assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert list(d["e2e"]["phases_ms_of_a_warmup_pass"]) == ["create_validate", "lanczos", "model_load", "all_edges_d2h"]
+    assert d["value"] == pytest.approx(fake_cuda.replica_value(1, gg.barabasi_albert(300, 3, 1).m, d["ms_per_step"]))
+    assert d["config"]["mode"] == "tgt" and d["tgt_plus"] is None and d["learned"] is not None
+    assert d["gpu_launches"] == 2 * 12
+    json.dumps(d)
+
+
+def test_tgt_plus_mode_line(fake_cuda):
+    d = _run(fake_cuda, ["--mode", "tgt_plus", "--policy", "global", "--steps", "1", "--warmup", "3", "--no-e2e"])
+    assert d["config"]["mode"] == "tgt_plus" and d["learned"] is None
+    assert d["tgt_plus"]["switch_after_hops"] == [4, 5] and d["tgt_plus"]["walk_pairs"] == 10
+    timed = [kw for kw in _FakeGraph.calls if kw.get("time_kernels")]
+    assert timed and all(kw["mode"] == "tgt_plus" for kw in timed)
+    arms = [kw for kw in _FakeGraph.calls if kw.get("precision") == "fp64"]
+    assert arms and all(kw["mode"] == "tgt" for kw in arms)  # the comparison arms stay TGT

@@ -84,3 +84,30 @@ def test_arguments_default_and_tgt_plus_mode():
     assert (a.mode, a.policy) == ("tgt_plus", "global")
     with pytest.raises(SystemExit):
         bench.parse_args(["--mode", "tgt_plus"])  # TGT+ sets its own lengths: no learned policy
+
+
+def test_timed_passes_split_only_the_warmups():
+    import time as _time
+
+    import bench
+
+    calls = {"sync": 0, "barrier": 0, "passes": 0}
+
+    def run_pass(mark):
+        calls["passes"] += 1
+        _time.sleep(0.002)
+        mark("a")
+        _time.sleep(0.001)
+        mark("b")
+
+    def sync():
+        calls["sync"] += 1
+
+    def barrier():
+        calls["barrier"] += 1
+
+    times, phases = bench.timed_passes(run_pass, 2, 3, sync, barrier)
+    assert calls["passes"] == 5 and calls["barrier"] == 5
+    assert calls["sync"] == 2 * 3 + 3  # warm-ups: two marks + the end; timed: the end only
+    assert len(times) == 3 and all(t >= 3.0 for t in times)
+    assert list(phases) == ["a", "b"] and phases["a"] >= 2.0 and phases["b"] >= 1.0
