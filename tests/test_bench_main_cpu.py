@@ -146,3 +146,16 @@ def test_tgt_plus_mode_line(fake_cuda):
     assert timed and all(kw["mode"] == "tgt_plus" for kw in timed)
     arms = [kw for kw in _FakeGraph.calls if kw.get("precision") == "fp64"]
     assert arms and all(kw["mode"] == "tgt" for kw in arms)  # the comparison arms stay TGT
+
+
+def test_reference_arm_line(monkeypatch):
+    """The reference arm times the oracle itself (real, on a tiny stand-in graph)."""
+    import bench
+
+    monkeypatch.setitem(bench.WORKLOADS, "ba_200k", dict(desc="tiny stand-in", make=lambda g: gg.barabasi_albert(300, 3, 1)))
+    d = _run(bench, ["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-step-seconds", "0.05"])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "edges/s"
+    assert {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "cpu_baseline",
+            "e2e", "config"} <= set(d)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
