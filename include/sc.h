@@ -368,7 +368,7 @@ sc_status sc_mlp_train(sc_graph *const *graphs, int32_t count, const sc_mlp_trai
 sc_status sc_mlp_load(sc_graph *g, const float *model);
 
 /* sc_mlp_predict -- the per-source lengths the loaded model gives (host int32[n]),
- * the odd integer nearest to exp(output), 2 floor(exp(output) / 2) + 1, clipped to [1, cap] */
+ * the smallest odd integer >= exp(output) - 1/4, clipped to [1, cap] */
 sc_status sc_mlp_predict(sc_graph *g, int32_t cap, int32_t *lengths);
 
 /*

@@ -28,9 +28,9 @@ Network: inputs standardised with the training set's mean and standard
 deviation, then 6 -> 32 -> 32 -> 1 with ReLU after the two hidden layers; the
 output is log L. Loss: mean over sources of (y - log L*)^2 / 2. Optimiser:
 Adam (Kingma and Ba, ICLR 2015) with bias correction. Prediction: the
-odd integer nearest to exp(y), 2 floor(exp(y) / 2) + 1, clipped to [1, cap]
-(the labels are odd; a prediction below the label costs an extension round,
-one above it wasted hops).
+smallest odd integer >= exp(y) - 1/4, clipped to [1, cap]: the labels are
+odd, and a prediction at most 1/4 above one takes it (a prediction below the
+label costs its source a rerun, one above it wasted hops).
 
 Flat parameter layout (float32, 1313 entries): W1[32][6], b1[32], W2[32][32],
 b2[32], W3[32], b3[1].
@@ -191,7 +191,6 @@ def standardise(F):
 def predict_lengths(theta, F, mu, sd, cap):
     y, _ = forward(theta, (F - mu) / sd)
     with np.errstate(over="ignore"):
-        h = np.floor(0.5 * np.exp(y))
-    top = cap if cap % 2 == 1 else cap + 1  # the largest admissible odd length
-    h = np.clip(np.nan_to_num(h, nan=0.0, posinf=float(top)), 0.0, (top - 1) // 2)
-    return (2 * h + 1).astype(np.int64)
+        e = np.ceil(np.exp(y) - 0.25)
+    L = np.clip(np.nan_to_num(e, nan=1.0, posinf=float(cap)), 1, cap).astype(np.int64)
+    return np.where(L % 2 == 0, np.minimum(L + 1, cap if cap % 2 == 1 else cap + 1), L)

@@ -231,9 +231,9 @@ __global__ void k_adam(float *__restrict__ params, const float *__restrict__ gra
     params[p] -= lr * mhat / (sqrtf(vhat) + eps);
 }
 
-// per-source length: the odd integer nearest to exp(y), 2 floor(exp(y) / 2) + 1,
-// clipped to [1, cap] (labels are odd; a short prediction costs an extension
-// round, a long one wasted hops)
+// per-source length: the smallest odd integer >= exp(y) - 1/4, clipped to
+// [1, cap]. Labels are odd: a prediction at most 1/4 above one takes it (a
+// short prediction costs its source a rerun, a long one wasted hops)
 __global__ void k_mlp_predict(const float *__restrict__ model, const float *__restrict__ F, int32_t n, int32_t cap,
                               int32_t *__restrict__ L) {
     __shared__ float w[kP + 2 * kF];
@@ -245,11 +245,12 @@ __global__ void k_mlp_predict(const float *__restrict__ model, const float *__re
 #pragma unroll
     for (int f = 0; f < kF; ++f) x[f] = (F[static_cast<int64_t>(i) * kF + f] - w[kP + f]) / w[kP + kF + f];
     const float y = mlp_forward(w, x, z1, h1, z2, h2);
-    double h = floor(0.5 * exp(static_cast<double>(y)));
-    if (!(h >= 0.0)) h = 0.0;                        // also catches NaN
-    const int32_t top = (cap & 1) ? cap : cap + 1;  // the largest admissible odd length
-    if (h > 0.5 * static_cast<double>(top - 1)) h = 0.5 * static_cast<double>(top - 1);
-    L[i] = 2 * static_cast<int32_t>(h) + 1;
+    double e = ceil(exp(static_cast<double>(y)) - 0.25);
+    if (!(e >= 1.0)) e = 1.0;  // also catches NaN
+    if (e > static_cast<double>(cap)) e = static_cast<double>(cap);
+    int32_t l = static_cast<int32_t>(e);
+    if ((l & 1) == 0) l = min(l + 1, (cap & 1) ? cap : cap + 1);
+    L[i] = l;
 }
 
 // ---------------------------------------------------------------------------

@@ -116,13 +116,13 @@ def test_adam_first_step_closed_form():
     assert np.allclose(theta, -0.1 * g / (np.abs(g) + 1e-8))
 
 
-def test_prediction_is_the_nearest_odd_length():
+def test_prediction_rounds_to_an_odd_length_with_a_quarter_slack():
     """With every weight zero the network outputs its last bias b3: exp(b3)
-    maps to the nearest odd integer, clipped to [1, cap]."""
+    maps to the smallest odd integer >= exp(b3) - 1/4, clipped to [1, cap]."""
     F = np.zeros((1, learned.NF))
     mu, sd = np.zeros(learned.NF), np.ones(learned.NF)
-    for e, cap, want in ((0.3, 9, 1), (1.99, 9, 1), (2.0, 9, 3), (3.9, 9, 3), (4.0, 9, 5), (5.99, 9, 5), (6.0, 9, 7),
-                         (8.5, 7, 7), (1e6, 7, 7), (40.0, 8, 9)):
+    for e, cap, want in ((0.3, 9, 1), (1.2, 9, 1), (1.3, 9, 3), (3.2, 9, 3), (3.3, 9, 5), (4.76, 9, 5), (5.2, 9, 5),
+                         (5.3, 9, 7), (8.5, 7, 7), (1e6, 7, 7), (40.0, 8, 9)):
         theta = np.zeros(learned.NPARAM)
         theta[-1] = np.log(e)
         assert learned.predict_lengths(theta, F, mu, sd, cap)[0] == want, (e, cap)

@@ -92,7 +92,7 @@ LEARNED = [
     ("certified lengths", lambda: tl.test_certified_lengths(lambda: gg.tree_plus_gnp(500, 8.0, 2), 1e-2)),
     ("gradient vs finite differences", tl.test_mlp_gradient_matches_finite_differences),
     ("Adam first step", tl.test_adam_first_step_closed_form),
-    ("nearest odd prediction", tl.test_prediction_is_the_nearest_odd_length),
+    ("odd prediction with slack", tl.test_prediction_rounds_to_an_odd_length_with_a_quarter_slack),
 ]
 
 CALTAU = [
@@ -269,8 +269,8 @@ PY_MUTANTS = [
      "dh2 = np.outer(dy, W3) * (z2 > 0)", "dh2 = np.outer(dy, W3)"),
     ("learned", "Adam without bias correction", "learned",
      "mhat = m / (1 - b1 ** t)", "mhat = m"),
-    ("learned", "prediction rounded up to odd", "learned",
-     "h = np.floor(0.5 * np.exp(y))", "h = np.ceil(0.5 * (np.exp(y) - 1.0))"),
+    ("learned", "prediction rounded up without slack", "learned",
+     "e = np.ceil(np.exp(y) - 0.25)", "e = np.ceil(np.exp(y))"),
     ("learned", "certificate from one term", "learned",
      "(factor * (full[:, t - 1] + full[:, t]) <= eps)", "(factor * full[:, t] <= eps)"),
 ]
