@@ -1,7 +1,7 @@
 """bench.py's main path run on the CPU with the CUDA pieces replaced by fakes:
 the JSON line carries every key the benchmark contract asks for, in both
-modes, so that a mistake in the driver code shows up here rather than on the
-GPU. The numbers are the fakes' and mean nothing. CPU only."""
+modes, so that a mistake in the benchmark's own code shows up here rather
+than on the GPU. The numbers are the fakes' and mean nothing. CPU only."""
 import io
 import json
 import sys

@@ -1,9 +1,11 @@
 """GPU parity of the TGT path (Algorithm 2) through the C ABI against the oracle.
 
-Tolerances (derivation in DESIGN.md, "Tolerances"):
+Tolerances:
   * FP64 probability blocks vs the FP64 series oracle at the same tau: 1e-12
-    (only summation order differs).
-  * FP32 blocks with FP64 accumulation: 2e-6 absolute on s_hat.
+    (only summation order differs; each p carries O(l u) relative error,
+    u = 2^-53, and s_hat sums at most 2 (tau + 1) terms of magnitude <= 1).
+  * FP32 blocks with FP64 accumulation: 2e-6 absolute on s_hat (each stored p
+    has relative error <= (l + 1) 2^-24 plus the chunked summation's).
   * BF16 blocks: 3e-2 absolute on s_hat (reported variant).
   * Any precision vs the exact resistance (O1): the method's eps (Thm. 3.2).
   * Integer outputs (tau per entry, structural flags): exact.
