@@ -148,6 +148,11 @@ __global__ void k_scale_into(const double *__restrict__ src, const double *__res
     dst[i] = src[i] / sqrt(*nrm2);
 }
 
+// alpha of a Lanczos step: the coefficients of V_vj in the two orthogonalisation passes, summed
+__global__ void k_alpha_of(const double *__restrict__ c, int nbasis, int vj, double *__restrict__ alpha) {
+    *alpha = c[vj] + c[nbasis + vj];
+}
+
 // locked vectors: sqrt(d_x)/sqrt(2m), and (bipartite) the same with sign (-1)^level
 __global__ void k_locked_vectors(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ level, int32_t n,
                                  double inv_sqrt_2m, int bipartite, double *__restrict__ v0, double *__restrict__ v1,
@@ -283,21 +288,15 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
                                            V.get() + ldv, isd.get());
         SC_LAUNCH_CHECK();
 
-        // orthogonalise w against V[0..nv) twice (CGS2); the coefficients of
-        // both passes are summed into cdst[0..nv)
-        auto reorth = [&](int nv, double *cdst) {
+        // orthogonalise w against V[0..nv) twice (CGS2); the coefficients of the
+        // two passes are c[0..nv) and c[nbasis..nbasis + nv)
+        auto reorth = [&](int nv) {
             for (int pass = 0; pass < 2; ++pass) {
                 double *cc = c.get() + (pass ? nbasis : 0);
                 k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
                 k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), cc);
                 k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, cc, w.get(), n);
                 SC_LAUNCH_CHECK();
-            }
-            if (cdst) {
-                std::vector<double> h(2 * nbasis);
-                SC_CUDA(cudaMemcpyAsync(h.data(), c.get(), 2 * nbasis * sizeof(double), cudaMemcpyDeviceToHost, s));
-                SC_CUDA(cudaStreamSynchronize(s));
-                for (int q = 0; q < nv; ++q) cdst[q] = h[q] + h[nbasis + q];
             }
         };
         auto norm2_into = [&](double *dst) {  // dst = <w, w> on the device
@@ -309,13 +308,22 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
         // start vector
         k_start_vector<<<nb, tb, 0, s>>>(w.get(), n, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
         SC_LAUNCH_CHECK();
-        reorth(nlock, nullptr);
+        reorth(nlock);
         double *nrm_dev = c.get() + 2 * nbasis;
         norm2_into(nrm_dev);
         k_scale_into<<<nb, tb, 0, s>>>(w.get(), nrm_dev, V.get() + nlock * ldv, n);
         SC_LAUNCH_CHECK();
 
-        std::vector<double> alpha, beta(1, 0.0), coef(nbasis);
+        // alpha_j and |w_j|^2 of every step stay on the device; the host reads
+        // them only at the steps where it checks convergence (every 4th from
+        // step 8, and the last possible one), so the steps in between run with
+        // no synchronisation. A breakdown (|w_j| <= 1e-12) between two checks is
+        // found at the next one and the steps after it are discarded, which
+        // gives the same steps and result as stopping at the breakdown itself.
+        DevBuf<double> ab;
+        ab.reserve(2 * static_cast<size_t>(max_iter));
+        double *d_alpha = ab.get(), *d_nrm2 = ab.get() + max_iter;
+        std::vector<double> alpha, beta(1, 0.0), h_alpha, h_nrm2;
         double theta_max = 0, theta_min = 0, res_max = INFINITY, res_min = INFINITY;
         int k = 0;
         bool converged = false;
@@ -324,16 +332,30 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
             k_spmv_norm<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), isd.get(),
                                                         V.get() + vj * ldv, w.get(), n);
             SC_LAUNCH_CHECK();
-            reorth(vj + 1, coef.data());
-            alpha.push_back(coef[vj]);
-            norm2_into(nrm_dev);
-            double nrm2 = 0.0;
-            SC_CUDA(cudaMemcpyAsync(&nrm2, nrm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-            SC_CUDA(cudaStreamSynchronize(s));
-            const double bnext = std::sqrt(std::max(nrm2, 0.0));
-            k = j + 1;
-            const bool exhausted = !(bnext > 1e-12) || k == n - nlock;
-            if (exhausted || k == max_iter || (k >= 8 && k % 4 == 0)) {
+            reorth(vj + 1);
+            k_alpha_of<<<1, 1, 0, s>>>(c.get(), nbasis, vj, d_alpha + j);  // both passes' coefficient of V_vj
+            norm2_into(d_nrm2 + j);
+            const int kk = j + 1;
+            if (kk == max_iter || kk == n - nlock || (kk >= 8 && kk % 4 == 0)) {
+                h_alpha.resize(kk);
+                h_nrm2.resize(kk);
+                SC_CUDA(cudaMemcpyAsync(h_alpha.data(), d_alpha, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+                SC_CUDA(cudaMemcpyAsync(h_nrm2.data(), d_nrm2, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+                SC_CUDA(cudaStreamSynchronize(s));
+                bool exhausted = kk == n - nlock;
+                int stop = kk;
+                for (int q = static_cast<int>(alpha.size()); q < kk; ++q) {
+                    alpha.push_back(h_alpha[q]);
+                    const double b = std::sqrt(std::max(h_nrm2[q], 0.0));
+                    if (!(b > 1e-12)) {  // breakdown at step q: the Krylov space is exhausted
+                        stop = q + 1;
+                        exhausted = true;
+                        break;
+                    }
+                    if (q + 1 < kk) beta.push_back(b);
+                }
+                k = stop;
+                const double bnext = std::sqrt(std::max(h_nrm2[stop - 1], 0.0));
                 // extreme Ritz values and their residuals bnext * |y_k|
                 theta_max = bisect_eig(alpha, beta, k, k - 1, -1.0 - 1e-9, 1.0 + 1e-9);
                 theta_min = bisect_eig(alpha, beta, k, 0, -1.0 - 1e-9, 1.0 + 1e-9);
@@ -343,10 +365,11 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
                     converged = true;
                     break;
                 }
+                if (exhausted) break;
+                beta.push_back(bnext);
             }
-            if (exhausted) break;
-            beta.push_back(bnext);
-            k_scale_into<<<nb, tb, 0, s>>>(w.get(), nrm_dev, V.get() + (vj + 1) * ldv, n);
+            k = kk;
+            k_scale_into<<<nb, tb, 0, s>>>(w.get(), d_nrm2 + j, V.get() + (vj + 1) * ldv, n);
             SC_LAUNCH_CHECK();
         }
         out->lambda_plus = theta_max;
