@@ -190,17 +190,30 @@ def _eq6(num, budget, lam_w):
     return out
 
 
-def caltau(n, row_ptr, col_idx, eps: float, lam, F):
+def caltau(n, row_ptr, col_idx, eps: float, lam, F, lam_rest=None):
     """Algorithm 1 (CalTau) for every CSR entry with the omega = len(lam)
-    eigenpairs of eigenpairs_by_modulus (lambda_1 = 1 first)."""
+    eigenpairs of eigenpairs_by_modulus (lambda_1 = 1 first).
+
+    lam_rest None: the paper's form, modes 2 .. omega-1 taken exactly and
+    |lambda_omega| bounding the modulus of every mode after them.
+    lam_rest = r: every given pair 2 .. omega is taken exactly and r bounds the
+    modulus of every nontrivial mode that is not given. The proof of Theorem
+    3.2 needs no more than that (each left-out term c_k lambda_k^(t+1) /
+    (1 - lambda_k) is at most r^(t+1) / (1 - r^2) c_k (1 + lambda_k)), so the
+    given pairs need not be the leading ones nor all copies of a repeated
+    eigenvalue; this is the paper's form with r in the last place."""
     lam = np.asarray(lam, dtype=np.float64)
+    if lam_rest is not None:
+        lam = np.append(lam, float(lam_rest))
+        F = np.vstack([np.asarray(F, dtype=np.float64), np.zeros((1, n))])
     omega = lam.size
     if omega < 2:
         raise ValueError("CalTau needs lambda_2")
-    if abs(lam[1]) >= 1.0:
+    lam_top = float(np.max(np.abs(lam[1:])))  # lambda_star: the largest nontrivial modulus
+    if lam_top >= 1.0:
         raise ValueError("|lambda_2| >= 1: the series does not converge (bipartite or disconnected)")
     deg, rows, cols = _entry_terms(n, row_ptr, col_idx)
-    tau0 = odd_ceil(f_edge(deg[rows], deg[cols], eps, abs(lam[1])))  # Eq. 6 with lambda_2 alone
+    tau0 = odd_ceil(f_edge(deg[rows], deg[cols], eps, lam_top))  # Eq. 6 with lambda_star alone
     if omega == 2:
         return tau0
     d_i, d_j = deg[rows], deg[cols]

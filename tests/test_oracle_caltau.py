@@ -200,3 +200,90 @@ def test_arpack_path_matches_dense():
     for eps in (1e-2, 1e-3):
         assert np.array_equal(truncation.caltau(*_csr(g), eps, lam_d, F_d),
                               truncation.caltau(*_csr(g), eps, lam_s, F_s))
+
+
+def _caltau_brute_subset(g, eps, used):
+    """The remainder form by direct search: the modes `used` (positions in the
+    whole spectrum sorted by modulus, 1 = lambda_2) taken exactly, r = the
+    largest modulus of every other nontrivial mode, the remainder weight
+    sum_{k not used} c_k (1 + lambda_k) / 2m straight from the spectrum, and
+    each candidate length found by trying tau = -1, 0, 1, ..."""
+    lam, F = truncation.eigenpairs_by_modulus(*_csr(g), g.n)
+    c = _c(g, F)
+    two_m = 2.0 * g.m
+    rest = [k for k in range(1, g.n) if k not in used]
+    r = float(np.max(np.abs(lam[rest]))) if rest else 0.0
+    rest_w = (1 + lam[rest]) @ c[rest] / two_m
+    lam_top = float(np.max(np.abs(lam[1:])))
+    x_e = (1 + lam[1:]) @ c[1:] / two_m
+    u = np.asarray(used)
+
+    def least_tau(delta, weight, lam_a):
+        for tau in range(-1, 100_000):
+            if delta + lam_a ** (tau + 1) / (1 - lam_a * lam_a) * weight <= eps:
+                return tau
+        raise AssertionError("no length found")
+
+    out = np.empty(g.nnz, dtype=np.int64)
+    for k in range(g.nnz):
+        tau0 = least_tau(0.0, x_e[k], lam_top)
+        tau0 = max(tau0 + (tau0 % 2 == 0), 1)
+        t = 1
+        while t < tau0:
+            delta = (lam[u] ** (t + 1) / (1 - lam[u])) @ c[u, k] / two_m
+            if delta > eps:
+                f = np.inf
+            elif rest_w[k] <= 1e-15 or r == 0.0:
+                f = -np.inf
+            else:
+                f = least_tau(delta, rest_w[k], r)
+            if t > f:
+                break
+            t += 2
+        out[k] = min(t, tau0)
+    return out, lam, F, r
+
+
+@pytest.mark.parametrize("maker", [lambda: gg.tree_plus_gnp(60, 4.0, 5), lambda: gg.lollipop(8, 3),
+                                   lambda: gg.barbell(6, 1)])
+@pytest.mark.parametrize("used", [[1, 2], [1, 3, 4], [2], [1, 2, 3, 5, 8]])
+def test_remainder_form_matches_a_direct_search(maker, used):
+    """Any set of exact modes with r bounding the others: the leading mode left
+    out, a gap in the set, the paper's contiguous set."""
+    g = maker()
+    for eps in (1e-2, 1e-3):
+        want, lam, F, r = _caltau_brute_subset(g, eps, used)
+        sel = [0] + used
+        got = truncation.caltau(*_csr(g), eps, lam[sel], F[sel], lam_rest=r)
+        assert np.array_equal(got, want)
+
+
+def test_remainder_form_with_the_paper_set_is_the_paper_form():
+    g = gg.lollipop(8, 3)
+    lam, F = truncation.eigenpairs_by_modulus(*_csr(g), 6)
+    for eps in (1e-2, 1e-4):
+        assert np.array_equal(truncation.caltau(*_csr(g), eps, lam[:5], F[:5], lam_rest=abs(lam[5])),
+                              truncation.caltau(*_csr(g), eps, lam, F))
+
+
+def test_remainder_form_with_one_copy_of_a_repeated_eigenvalue():
+    """Two K_12 joined by an edge: -1/11 has a 20-fold eigenspace. A
+    single-vector Krylov method sees one vector of it; with that one vector
+    taken exactly (with the two modes above it) and r = 1/11 for the rest,
+    Theorem 3.2 still holds, and
+    still needs far fewer hops than Eq. 6."""
+    g = gg.barbell(12, 1)
+    lam, F = truncation.eigenpairs_by_modulus(*_csr(g), g.n)
+    copies = np.flatnonzero(np.abs(lam + 1.0 / 11.0) < 1e-9)
+    assert copies.size >= 18
+    sel = [0, 1, 2, int(copies[0])]  # 1, 0.987, -0.161 and one copy of -1/11
+    rest = np.setdiff1d(np.arange(1, g.n), sel)
+    r = float(np.max(np.abs(lam[rest])))
+    assert abs(r - 1.0 / 11.0) < 1e-9
+    ex = exact.exact_dense(*_csr(g))
+    _, _, lam_star = truncation.spectrum_extremes(*_csr(g))
+    for eps in (1e-2, 1e-3):
+        tau = truncation.caltau(*_csr(g), eps, lam[sel], F[sel], lam_rest=r)
+        s, _ = series.series_entries(*_csr(g), tau)
+        assert np.max(np.abs(s - ex)) <= eps
+        assert tau.mean() < 0.05 * truncation.tau_entries(*_csr(g), eps, lam_star).mean()

@@ -105,6 +105,10 @@ CALTAU = [
     ("Theorem 3.2, G(n,p)", lambda: tc.test_theorem_3_2_with_caltau(lambda: gg.gnp_lcc(200, 5.0, 2), 1e-3)),
     ("bottleneck", tc.test_bottleneck_needs_far_fewer_hops),
     ("direct search", lambda: tc.test_caltau_matches_a_direct_search(lambda: gg.lollipop(8, 3), 3)),
+    ("remainder form, leading mode left out", lambda: tc.test_remainder_form_matches_a_direct_search(
+        lambda: gg.lollipop(8, 3), [2])),
+    ("remainder form, a gap", lambda: tc.test_remainder_form_matches_a_direct_search(
+        lambda: gg.barbell(6, 1), [1, 3, 4])),
 ]
 
 BATTERIES = {"series": SERIES, "truncation": TRUNCATION, "exact": EXACT, "tgtplus": TGTPLUS,
@@ -210,6 +214,10 @@ PY_MUTANTS = [
     ("truncation", "X_e sign in CalTau", "caltau",
      "d_i, d_j = deg[rows], deg[cols]\n    x_e = 1.0 / d_i + 1.0 / d_j - 2.0 / (d_i * d_j)",
      "d_i, d_j = deg[rows], deg[cols]\n    x_e = 1.0 / d_i + 1.0 / d_j + 2.0 / (d_i * d_j)"),
+    ("truncation", "remainder modulus from the last given pair", "caltau",
+     "lam = np.append(lam, float(lam_rest))", "lam = np.append(lam, float(abs(lam[-1])))"),
+    ("truncation", "lambda_star from the first given pair", "caltau",
+     "lam_top = float(np.max(np.abs(lam[1:])))", "lam_top = float(abs(lam[1]))"),
     # exact.py
     ("exact", "resistance without the cross factor 2", "exact",
      "dg[rows] + dg[cols] - 2.0 * m[rows, cols]", "dg[rows] + dg[cols] - m[rows, cols]"),
