@@ -28,11 +28,12 @@ import pytest
 
 import graphgen as gg
 import oracle
-from oracle import _native, exact, learned, philox, series, tgtplus, truncation
+from oracle import _native, exact, learned, meet, philox, series, tgtplus, truncation
 
 import test_oracle_caltau as tc
 import test_oracle_exact as te
 import test_oracle_learned as tl
+import test_oracle_meet as tm
 import test_oracle_series as ts
 import test_oracle_tgtplus as tt
 
@@ -111,7 +112,13 @@ CALTAU = [
         lambda: gg.barbell(6, 1), [1, 3, 4])),
 ]
 
-BATTERIES = {"series": SERIES, "truncation": TRUNCATION, "exact": EXACT, "tgtplus": TGTPLUS,
+MEET = [
+    ("equals Algorithm 2, lollipop", lambda: tm.test_equals_algorithm_2_at_per_entry_lengths(lambda: gg.lollipop(7, 4))),
+    ("K_n closed form", lambda: tm.test_complete_graph_closed_form(7)),
+    ("matrix powers, even terms", tm.test_terms_equal_matrix_powers_and_even_terms_are_non_negative),
+]
+
+BATTERIES = {"series": SERIES, "truncation": TRUNCATION, "exact": EXACT, "tgtplus": TGTPLUS, "meet": MEET,
              "learned": LEARNED, "caltau": CALTAU}
 
 
@@ -218,6 +225,13 @@ PY_MUTANTS = [
      "lam = np.append(lam, float(lam_rest))", "lam = np.append(lam, float(abs(lam[-1])))"),
     ("truncation", "lambda_star from the first given pair", "caltau",
      "lam_top = float(np.max(np.abs(lam[1:])))", "lam_top = float(abs(lam[1]))"),
+    # meet.py
+    ("meet", "odd hop split as a + a", "meet", "        b = ell - a\n", "        b = a\n"),
+    ("meet", "inner product without D^-1", "meet",
+     "np.sum(U[a] * U[b] / deg[None, :], axis=1)", "np.sum(U[a] * U[b], axis=1)"),
+    ("meet", "u from one endpoint", "meet", "U = [Rh[rows] - Rh[cols] for Rh in R]", "U = [Rh[rows] for Rh in R]"),
+    ("meet", "columns of P^h for distributions", "meet", "U = [Rh[rows] - Rh[cols] for Rh in R]",
+     "U = [(Rh[:, rows] - Rh[:, cols]).T for Rh in R]"),
     # exact.py
     ("exact", "resistance without the cross factor 2", "exact",
      "dg[rows] + dg[cols] - 2.0 * m[rows, cols]", "dg[rows] + dg[cols] - m[rows, cols]"),
@@ -338,7 +352,7 @@ def test_c_mutant_is_killed(mid, battery, old, new, c_source, tmp_path, monkeypa
 
 
 MODULES = {"series": series, "truncation": truncation, "exact": exact, "philox": philox,
-           "tgtplus": tgtplus, "learned": learned}
+           "tgtplus": tgtplus, "learned": learned, "meet": meet}
 
 
 @pytest.mark.parametrize("module,mid,battery,old,new", PY_MUTANTS, ids=[m[1] for m in PY_MUTANTS])
