@@ -403,6 +403,39 @@ def rmat(scale: int, edge_factor: int = 16, abcd=(0.57, 0.19, 0.19, 0.05), seed:
     return largest_component(g, name=f"rmat_s{scale}_ef{edge_factor}_s{seed}")
 
 
+def planted_partition(k: int = 8, size: int = 500, d_in: float = 10.0, d_out: float = 0.5,
+                      seed: int = 6) -> CSRGraph:
+    """k communities of `size` nodes (community c holds nodes c*size .. (c+1)*size - 1).
+    Inside each: a uniform random spanning tree united with G(size, p_in), p_in
+    set for an expected internal degree d_in. Between them: a ring of k edges
+    (community c to c+1 mod k, random endpoints) keeps the graph connected, and
+    G(n, p_out) restricted to pairs in different communities adds an expected
+    d_out external neighbours per node. With d_out << d_in the walk leaves a
+    community rarely: k - 1 eigenvalues of N lie close to 1 (a bottleneck
+    family, where Eq. 6 with lambda_2 alone asks very long lengths)."""
+    rng = np.random.default_rng(seed)
+    n = k * size
+    us, vs = [], []
+    for c in range(k):
+        tu, tv = _prufer_tree_edges(size, rng)
+        p_in = max((size * d_in / 2.0 - (size - 1)) / (size * (size - 1) / 2.0), 0.0)
+        gu, gv = _gnp_pairs(size, p_in, rng)
+        us += [c * size + tu, c * size + gu]
+        vs += [c * size + tv, c * size + gv]
+    if k > 1:
+        ring = np.arange(k)
+        us.append(ring * size + rng.integers(0, size, size=k))
+        vs.append(((ring + 1) % k) * size + rng.integers(0, size, size=k))
+        p_out = d_out / max(n - size, 1)
+        ou, ov = _gnp_pairs(n, p_out, rng)
+        cross = ou // size != ov // size
+        us.append(ou[cross])
+        vs.append(ov[cross])
+    return from_edges(n, np.concatenate(us), np.concatenate(vs),
+                      name=f"planted_k{k}_s{size}_din{d_in:g}_dout{d_out:g}_s{seed}",
+                      meta={"family": "planted_partition", "seed": seed})
+
+
 def batch_graphs(count: int = 512, nmin: int = 1000, nmax: int = 50000, base_seed: int = 4):
     """Many independent graphs of uneven size. Graph g uses seed base_seed+g,
     n_g = round(exp(U[ln nmin, ln nmax])), and its family cycles with g mod 3:
@@ -436,4 +469,7 @@ def workload(name: str, **kw) -> CSRGraph:
         return perturbed_grid(kw.get("rows", 1000), kw.get("cols", 1000), 0.05, kw.get("seed", 2))
     if name == "rmat_22":
         return rmat(kw.get("scale", 22), 16, seed=kw.get("seed", 5))
+    if name == "planted_200k":
+        return planted_partition(kw.get("k", 40), kw.get("size", 5000), kw.get("d_in", 10.0), kw.get("d_out", 0.2),
+                                 kw.get("seed", 6))
     raise KeyError(name)

@@ -26,6 +26,7 @@ def _check_csr(g):
 
 @pytest.mark.parametrize("make", [
     lambda: gg.tree_plus_gnp(500, 10.0, 3),
+    lambda: gg.planted_partition(6, 150, 8.0, 0.4, 2),
     lambda: gg.barabasi_albert(3000, 5, 2),
     lambda: gg.perturbed_grid(30, 40, 0.05, 1),
     lambda: gg.gnp_lcc(2000, 8.0, 4),
@@ -63,3 +64,22 @@ def test_batch_recipe_cycles_families_and_sizes():
         _check_csr(g)
         assert bool(g.meta.get("bipartite")) == (i % 3 == 2)  # lattices every third graph
         assert 100 <= g.n <= 2100
+
+
+def test_planted_partition_communities_and_slow_modes():
+    """Nodes c*size .. (c+1)*size - 1 form community c; about d_in of a node's
+    neighbours are inside and d_out outside; k - 1 eigenvalues of N lie near 1
+    and the k-th below them is far lower (the bottleneck the recipe is for)."""
+    k, size, d_in, d_out = 5, 200, 10.0, 0.3
+    g = gg.planted_partition(k, size, d_in, d_out, 3)
+    assert g.n == k * size
+    rows = g.entry_rows()
+    inside = (rows // size) == (g.col_idx // size)
+    assert abs(inside.sum() / g.n - d_in) < 0.6 and abs((~inside).sum() / g.n - d_out) < 0.15
+    d = g.degree.astype(np.float64)
+    nmat = np.zeros((g.n, g.n))
+    nmat[rows, g.col_idx] = 1.0 / np.sqrt(d[rows] * d[g.col_idx])
+    ev = np.sort(np.linalg.eigvalsh(nmat))[::-1]
+    assert abs(ev[0] - 1.0) < 1e-12 and np.all(ev[1:k] > 0.9) and ev[k] < 0.75
+    h = gg.planted_partition(k, size, d_in, d_out, 3)
+    assert np.array_equal(g.row_ptr, h.row_ptr) and np.array_equal(g.col_idx, h.col_idx)
