@@ -24,7 +24,8 @@ walk length for the entry (i -> j).
 * Eq. 11: X = (sum_{t=1..L} p(W_i[t]) - sum_{t=1..L} p(W_j[t])) / d_i, walks
   W_i from v_i and W_j from v_j; positions 1..L, the start excluded.
 * Eq. 14: switch to walks after hop l when
-  sum_{x: p_l(x, v_i) != 0} d(x) > sum_j R(e_ij, tau_ij - l).
+  sum_{x: p_l(x, v_i) != 0} d(x) > sum_j R(e_ij, tau_ij - l);
+  ``switch_hop`` tests it per source from l = 0, as Algorithm 4 prints it.
 
 Random numbers: walk w of entry k takes its step t (t = 1..L) from word
 (t-1) mod 4 of Philox4x32-10 with counter (k, w, side * 2^31 + (t-1) div 4,
@@ -145,6 +146,36 @@ def source_column(n, row_ptr, col_idx, i, hops):
             q[nb] += p[v] / deg[nb]
         p = q
     return p
+
+
+def switch_hop(n, row_ptr, col_idx, i, tau_row, eps, delta, gamma, m):
+    """Algorithm 4's switch length for source v_i, Eq. 14 tested per source as
+    printed: from l = 0 (p_0 = e_i), while the frontier volume of p_l(., v_i) is
+    at most sum_j R(e_ij, tau_ij - l) over the neighbours with tau_ij - l > 0
+    (chi from Alg. 3 on p_l, R from Eq. 13), take one more hop; the l at which
+    it first exceeds it is tau-tilde. Once every tau_ij <= l the right side is
+    empty, so tau-tilde <= max_j tau_ij."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    nbr = col_idx[row_ptr[i]:row_ptr[i + 1]]
+    d_i = len(nbr)
+    deg = np.diff(row_ptr)
+    p = np.zeros(n)
+    p[i] = 1.0
+    ell = 0
+    while True:
+        rhs = 0
+        for t, j in enumerate(nbr):
+            L = int(tau_row[t]) - ell
+            if L > 0:
+                rhs += walk_count(calchi(row_ptr, col_idx, p, i, int(j), L, gamma), d_i, m, delta, eps)
+        if frontier_volume(row_ptr, p) > rhs:
+            return ell
+        q = np.zeros(n)
+        for v in np.flatnonzero(p > 0):
+            nb = col_idx[row_ptr[v]:row_ptr[v + 1]]
+            q[nb] += p[v] / deg[nb]
+        p = q
+        ell += 1
 
 
 def tgt_plus_half(n, row_ptr, col_idx, i, tau_row, tt, eps, delta, gamma, seed, m):

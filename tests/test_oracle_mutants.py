@@ -83,6 +83,9 @@ TGTPLUS = [
     ("Eq. 15", tt.test_eq15_gamma_zero),
     ("Eq. 13 Hoeffding", tt.test_walk_count_formula_and_hoeffding),
     ("TGT+ within eps", tt.test_full_tgt_plus_within_eps_on_small_graph),
+    ("frontier = degree of the exact reach", lambda: tt.test_frontier_volume_is_the_degree_of_the_exact_reach(
+        lambda: gg.lollipop(6, 4))),
+    ("per-source switch", tt.test_per_source_switch_is_the_first_hop_where_eq14_holds),
 ]
 
 LEARNED = [
@@ -225,6 +228,12 @@ PY_MUTANTS = [
      "lam = np.append(lam, float(lam_rest))", "lam = np.append(lam, float(abs(lam[-1])))"),
     ("truncation", "lambda_star from the first given pair", "caltau",
      "lam_top = float(np.max(np.abs(lam[1:])))", "lam_top = float(abs(lam[1]))"),
+    # tgtplus.py: Algorithm 4's per-source switch (Eq. 14)
+    ("tgtplus", "Eq. 14's walks at the full length", "tgtplus",
+     "            L = int(tau_row[t]) - ell\n            if L > 0:\n                rhs +=",
+     "            L = int(tau_row[t])\n            if L > 0:\n                rhs +="),
+    ("tgtplus", "frontier counts nodes, not degrees", "tgtplus", "return int(deg[p != 0].sum())",
+     "return int((p != 0).sum())"),
     # meet.py
     ("meet", "odd hop split as a + a", "meet", "        b = ell - a\n", "        b = a\n"),
     ("meet", "inner product without D^-1", "meet",

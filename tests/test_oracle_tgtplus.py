@@ -177,3 +177,81 @@ def test_full_tgt_plus_within_eps_on_small_graph():
     rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
     s = ghat + ghat[rev]
     assert np.max(np.abs(s - r)) <= eps
+
+
+def _reach_exactly(g, i, ell):
+    """Nodes at the end of some walk of exactly ell steps from v_i (boolean
+    matrix powers, no probabilities)."""
+    a = np.zeros((g.n, g.n), dtype=bool)
+    a[g.entry_rows(), g.col_idx] = True
+    cur = np.zeros(g.n, dtype=bool)
+    cur[i] = True
+    for _ in range(ell):
+        cur = a[cur].any(axis=0)
+    return cur
+
+
+@pytest.mark.parametrize("maker", [lambda: gg.tree_plus_gnp(50, 4.0, 2), lambda: gg.grid(5, 6),
+                                   lambda: gg.lollipop(6, 4)])
+def test_frontier_volume_is_the_degree_of_the_exact_reach(maker):
+    """Eq. 14's left side: the support of p_l(., v_i) is the set reached by a
+    walk of exactly l steps (on a bipartite graph one side of the ball only)."""
+    g = maker()
+    for i in (0, g.n // 2, g.n - 1):
+        for ell in range(0, 7):
+            p = tgtplus.source_column(g.n, g.row_ptr, g.col_idx, i, ell)
+            assert tgtplus.frontier_volume(g.row_ptr, p) == int(g.degree[_reach_exactly(g, i, ell)].sum())
+
+
+def test_per_source_switch_is_the_first_hop_where_eq14_holds():
+    """tgtplus.switch_hop against Eq. 14 evaluated from columns of matrix
+    powers of P: it fails at every earlier hop and holds at the switch, which
+    is never past the source's longest length; a large eps switches sooner."""
+    from oracle import truncation
+
+    g = gg.tree_plus_gnp(70, 5.0, 4)
+    _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
+    P = np.zeros((g.n, g.n))
+    P[g.entry_rows(), g.col_idx] = 1.0 / g.degree[g.entry_rows()]
+    for eps in (0.02, 0.2):
+        tau = truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam)
+        tts = []
+        for i in range(0, g.n, 7):
+            a, b = g.row_ptr[i], g.row_ptr[i + 1]
+            tt = tgtplus.switch_hop(g.n, g.row_ptr, g.col_idx, i, tau[a:b], eps, 1.0 / g.n, 10, g.m)
+            assert 0 <= tt <= tau[a:b].max()
+            col = np.zeros(g.n)
+            col[i] = 1.0
+            for ell in range(tt + 1):
+                lhs = int(g.degree[col != 0].sum())
+                rhs = sum(tgtplus.walk_count(tgtplus.calchi(g.row_ptr, g.col_idx, col, i, int(g.col_idx[k]),
+                                                            int(tau[k]) - ell, 10), g.degree[i], g.m, 1.0 / g.n, eps)
+                          for k in range(a, b) if tau[k] - ell > 0)
+                assert (lhs > rhs) == (ell == tt), (i, ell, tt)
+                col = P @ col  # p_{ell+1}(x, v_i) = P^(ell+1)[x, v_i] = sum_y P[x, y] p_ell(y, v_i)
+            tts.append(tt)
+        if eps == 0.02:
+            tts_small = tts
+    assert np.mean(tts) <= np.mean(tts_small)
+
+
+def test_tgt_plus_with_per_source_switch_within_eps():
+    """Theorem 4.4 with Algorithm 4's per-source switch (fixed seeds)."""
+    from oracle import truncation
+
+    g = gg.tree_plus_gnp(60, 6.0, 5)
+    r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
+    _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
+    eps = 0.05
+    tau = truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam)
+    ghat = np.zeros(g.nnz)
+    walks = 0
+    for i in range(g.n):
+        a, b = g.row_ptr[i], g.row_ptr[i + 1]
+        tt = tgtplus.switch_hop(g.n, g.row_ptr, g.col_idx, i, tau[a:b], eps, 1.0 / g.n, 10, g.m)
+        gi, R, _ = tgtplus.tgt_plus_half(g.n, g.row_ptr, g.col_idx, i, tau[a:b], tt, eps, 1.0 / g.n, 10, 13, g.m)
+        ghat[a:b] = gi / g.degree[i]
+        walks += int(R.sum())
+    rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
+    assert walks > 0
+    assert np.max(np.abs(ghat + ghat[rev] - r)) <= eps
