@@ -419,6 +419,17 @@ sc_status sc_mlp_loss_grad(const float *model, const float *features, const floa
 sc_status sc_all_edges_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                                int32_t ell, double *s_hat, void *stream);
 
+/* ---- self-test -------------------------------------------------------------- */
+/* sc_selftest_bounded_waits -- the library's bounded device waits giving up as
+ * designed (no fault and no hang): a wait on an mbarrier phase that never
+ * completes (the wait the TMA hop kernel uses for its row gathers) and a spin
+ * on a device flag that is never set, each limited to limit_us microseconds
+ * (1 .. 1,000,000), on the current device's default stream.
+ * Returns SC_ERR_TIMEOUT when both gave up and reported it through their
+ * status word (the expected outcome; the CUDA context stays usable),
+ * SC_ERR_CUDA if one did not, SC_ERR_INVALID_ARG for a limit out of range. */
+sc_status sc_selftest_bounded_waits(uint32_t limit_us);
+
 /* ---- status --------------------------------------------------------------- */
 const char *sc_status_string(sc_status s);
 const char *sc_last_error_detail(void);

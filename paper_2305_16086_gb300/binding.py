@@ -37,7 +37,7 @@ EXPORTS = [
     "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
-    "sc_batch_all_edges",
+    "sc_batch_all_edges", "sc_selftest_bounded_waits",
 ]
 MLP_PARAMS, MLP_FEATURES = 1313, 6
 MLP_MODEL_FLOATS = MLP_PARAMS + 2 * MLP_FEATURES
@@ -155,6 +155,8 @@ def load(path: str = LIB_PATH):
     L.sc_mlp_predict.restype = ctypes.c_int
     L.sc_mlp_loss_grad.argtypes = [f32p, f32p, f32p, i32, f32p, f32p, vp]
     L.sc_mlp_loss_grad.restype = ctypes.c_int
+    L.sc_selftest_bounded_waits.argtypes = [ctypes.c_uint32]
+    L.sc_selftest_bounded_waits.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -408,3 +410,12 @@ def mlp_loss_grad(model, features, targets):
                                    grad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_handle(None)),
            "sc_mlp_loss_grad")
     return float(loss.value), grad
+
+
+def selftest_bounded_waits(limit_us: int = 2000) -> tuple[int, str]:
+    """Runs the library's bounded-wait self-test (a wait that nothing
+    completes, limited to limit_us); returns (status, detail). SC_ERR_TIMEOUT
+    is the expected status: both waits gave up and said so."""
+    L = load()
+    st = int(L.sc_selftest_bounded_waits(int(limit_us)))
+    return st, L.sc_last_error_detail().decode(errors="replace")

@@ -143,3 +143,10 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError, match="libsc.so not found"):
         binding.load(str(tmp_path / "libsc.so"))
+
+
+def test_selftest_rejects_a_limit_out_of_range():
+    """Argument checks come before any CUDA call, so they run without a GPU."""
+    for bad in (0, 1000001):
+        st, detail = binding.selftest_bounded_waits(bad)
+        assert binding.STATUS_NAMES[st] == "SC_ERR_INVALID_ARG" and "limit_us" in detail
