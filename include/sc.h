@@ -152,6 +152,97 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
                                int32_t *ell_global_out, int32_t *per_source_out,
                                int32_t *per_entry_out);
 
+/* ---- CalTau with omega eigenpairs (Algorithm 1, Eq. 6-8) ------------------- */
+
+#define SC_OMEGA_MAX 257    /* eigenpairs per call, lambda_1 = 1 included */
+
+typedef struct sc_eig_opts {
+    int32_t omega;           /* eigenpairs wanted, lambda_1 = 1 included, 2..SC_OMEGA_MAX */
+    int32_t max_iter;        /* Lanczos steps of the first run (0 = min(n - 1, 3 omega + 64)) */
+    double tol;              /* Ritz residual a pair must meet to be taken exactly (0 = 1e-8) */
+    double rest_tol;         /* residual of the second run's extreme Ritz pairs (0 = 1e-6) */
+    int32_t rest_max_iter;   /* Lanczos steps of the second run (0 = 500) */
+    int32_t reserved;
+    uint64_t seed;           /* start vectors (Philox4x32-10 streams; the second run uses seed + 1) */
+} sc_eig_opts;
+
+typedef struct sc_eig_report {
+    int32_t used;            /* pairs taken exactly, lambda_1 included (<= omega) */
+    int32_t iterations;      /* steps of the first run */
+    int32_t rest_iterations; /* steps of the second run (0 when every mode is taken) */
+    int32_t rest_converged;  /* 1 if the second run's residuals met rest_tol */
+    double max_residual;     /* largest Ritz residual among the pairs taken */
+    double rest_residual;    /* larger residual of the second run's two extreme Ritz pairs */
+    double lambda_rest;      /* r: bound on the modulus of every nontrivial mode not taken */
+} sc_eig_report;
+
+/*
+ * sc_eigenpairs -- eigenpairs of N = D^-1/2 A D^-1/2 of largest modulus for
+ * CalTau (Algorithm 1): lambda_k and f_k = sqrt(2m) D^-1/2 phi_k (Eq. 7-8's
+ * vectors, the notation of Theorem 3.2's proof), and a bound r on the modulus
+ * of every other nontrivial mode. Two FP64 Lanczos runs with full
+ * reorthogonalisation on the device: the first, with sqrt(d)/sqrt(2m)
+ * deflated, gives Ritz pairs; those of the omega - 1 largest moduli whose
+ * residual meets tol are taken (U). The second runs on the complement of U
+ * from a fresh start vector, so it also sees the copies of a repeated
+ * eigenvalue that a single Krylov sequence cannot; r = its larger extreme
+ * modulus plus its residual and the largest residual in U (the margin of
+ * sc_estimate_lambda). The pairs and r are kept in the graph for sc_caltau.
+ *
+ *   opts     : may be NULL (omega 129 and the defaults above)
+ *   lam_out  : host double[omega]; lam_out[0] = 1, then U by decreasing
+ *              modulus (the larger value first on a tie), zeros past `used`
+ *   F_out    : host double[omega * n] (may be NULL); row k = f_k (row 0 all
+ *              ones), rows past `used` zero; the sign of a row is arbitrary
+ *   report   : may be NULL
+ * Errors: SC_ERR_UNSUPPORTED for a bipartite graph (lambda = -1 is a mode of
+ * modulus 1: no length meets Theorem 3.2); SC_ERR_LAMBDA_NOT_CONVERGED (with
+ * the outputs filled) when the second run's residual stays above rest_tol;
+ * SC_ERR_INVALID_ARG for omega outside 2..SC_OMEGA_MAX or above n.
+ */
+sc_status sc_eigenpairs(sc_graph *g, const sc_eig_opts *opts, double *lam_out, double *F_out,
+                        sc_eig_report *report);
+
+/*
+ * sc_caltau -- Algorithm 1 (CalTau) for every CSR entry: with the pairs of U
+ * taken exactly and r for the rest, Upsilon = sum_U c_k (1 + lambda_k) / 2m
+ * (Eq. 7) and Delta_t = sum_U c_k lambda_k^(t+1) / (1 - lambda_k) / 2m (Eq. 8),
+ * c_k = (f_k[i] - f_k[j])^2; starting from tau0 = Eq. 6 with
+ * lambda_star = max(max_U |lambda|, r), t = 1, 3, 5, ... until t exceeds Eq. 6
+ * with X_e - Upsilon, eps - Delta_t and r in place of X_e, eps and lambda; the
+ * length is min(t, tau0). The proof of Theorem 3.2 bounds each left-out term by
+ * r^(t+1) / (1 - r^2) c_k (1 + lambda_k), so any U with such an r meets eps.
+ * The lengths are kept in the graph for SC_ELL_CALTAU.
+ *
+ *   eps       : 0 < eps < 1
+ *   count     : pairs in lam / F, lambda_1 = 1 included (2..SC_OMEGA_MAX);
+ *               0 = the pairs of the graph's last sc_eigenpairs (lam, F and
+ *               lam_rest are then ignored)
+ *   lam       : host double[count], lam[0] = 1 (ignored), |lam[k]| < 1
+ *   F         : host double[count * n], row k = f_k (row 0 ignored)
+ *   lam_rest  : r, 0 <= r < 1
+ *   tau_out   : host int32[nnz] (may be NULL); both directions of an edge equal
+ *   ell_out   : host int32, the largest length (may be NULL)
+ * Errors: SC_ERR_INVALID_ARG (no pairs, or a modulus >= 1); SC_ERR_UNSUPPORTED
+ * for a bipartite graph or when Eq. 6's length passes 2^20 (the Delta_t loop
+ * would take more than 2^19 steps per edge).
+ */
+sc_status sc_caltau(sc_graph *g, double eps, int32_t count, const double *lam, const double *F,
+                    double lam_rest, int32_t *tau_out, int32_t *ell_out);
+
+/*
+ * sc_tridiag_eig -- every eigenpair of the symmetric tridiagonal matrix with
+ * diagonal alpha[0..k) and off-diagonal beta[0..k-1) (beta[i] couples i and
+ * i + 1), by the implicit symmetric QR algorithm with Wilkinson shifts: the
+ * host-side step of sc_eigenpairs, exported for testing. Host only, no GPU.
+ *   theta : host double[k], ascending
+ *   Z     : host double[k * k] (may be NULL); column q (Z[q * k .. q * k + k))
+ *           = the unit eigenvector of theta[q]
+ * Errors: SC_ERR_INVALID_ARG (k < 1, NULL arrays); SC_ERR_LAMBDA_NOT_CONVERGED
+ * if an eigenvalue needs more than 60 QR steps.
+ */
+sc_status sc_tridiag_eig(int32_t k, const double *alpha, const double *beta, double *theta, double *Z);
+
 /* ---- the all-edge computation --------------------------------------------- */
 
 /* truncation policy */
@@ -161,6 +252,8 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam,
 #define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP (sc_mlp_load); every edge
                                is then certified by the bound of sc_certified_lengths and, if it
                                fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed */
+#define SC_ELL_CALTAU 4     /* the per-edge lengths of the graph's last sc_caltau (same eps; TGT only);
+                               sources run the longest of their edges */
 
 /* storage precision of the propagated probability block */
 #define SC_PREC_FP64 0

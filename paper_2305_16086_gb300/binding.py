@@ -24,7 +24,7 @@ STATUS_NAMES = {
     14: "SC_ERR_UNSUPPORTED",
 }
 SC_PTRS_HOST, SC_PTRS_DEVICE, SC_FLAG_REJECT_BIPARTITE = 0, 1, 2
-ELL = {"global": 0, "per_edge": 1, "fixed": 2, "learned": 3}
+ELL = {"global": 0, "per_edge": 1, "fixed": 2, "learned": 3, "caltau": 4}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 EST = {"plain": 0, "end_corrected": 1}
 MODE = {"tgt": 0, "tgt_plus": 1}
@@ -37,8 +37,9 @@ EXPORTS = [
     "sc_truncation_length", "sc_options_default", "sc_all_edges", "sc_status_string",
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
-    "sc_batch_all_edges", "sc_selftest_bounded_waits",
+    "sc_batch_all_edges", "sc_selftest_bounded_waits", "sc_eigenpairs", "sc_caltau", "sc_tridiag_eig",
 ]
+OMEGA_MAX = 257
 MLP_PARAMS, MLP_FEATURES = 1313, 6
 MLP_MODEL_FLOATS = MLP_PARAMS + 2 * MLP_FEATURES
 
@@ -90,6 +91,18 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class EigOpts(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("rest_tol", ctypes.c_double), ("rest_max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class EigReport(ctypes.Structure):
+    _fields_ = [("used", ctypes.c_int32), ("iterations", ctypes.c_int32), ("rest_iterations", ctypes.c_int32),
+                ("rest_converged", ctypes.c_int32), ("max_residual", ctypes.c_double),
+                ("rest_residual", ctypes.c_double), ("lambda_rest", ctypes.c_double)]
+
+
 class MlpTrainOpts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("precision", ctypes.c_int32),
@@ -117,6 +130,7 @@ def load(path: str = LIB_PATH):
     L = ctypes.CDLL(path)
     vp, i32, i64, u32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
     i32p = ctypes.POINTER(ctypes.c_int32)
+    f64p = ctypes.POINTER(ctypes.c_double)
     L.sc_graph_create.argtypes = [ctypes.POINTER(vp), i32, i64, vp, vp, u32, vp]
     L.sc_graph_create.restype = ctypes.c_int
     L.sc_graph_get_info.argtypes = [vp, ctypes.POINTER(GraphInfo)]
@@ -155,6 +169,12 @@ def load(path: str = LIB_PATH):
     L.sc_mlp_predict.restype = ctypes.c_int
     L.sc_mlp_loss_grad.argtypes = [f32p, f32p, f32p, i32, f32p, f32p, vp]
     L.sc_mlp_loss_grad.restype = ctypes.c_int
+    L.sc_eigenpairs.argtypes = [vp, ctypes.POINTER(EigOpts), f64p, f64p, ctypes.POINTER(EigReport)]
+    L.sc_eigenpairs.restype = ctypes.c_int
+    L.sc_caltau.argtypes = [vp, f64, i32, f64p, f64p, f64, i32p, i32p]
+    L.sc_caltau.restype = ctypes.c_int
+    L.sc_tridiag_eig.argtypes = [i32, f64p, f64p, f64p, f64p]
+    L.sc_tridiag_eig.restype = ctypes.c_int
     L.sc_selftest_bounded_waits.argtypes = [ctypes.c_uint32]
     L.sc_selftest_bounded_waits.restype = ctypes.c_int
     _lib = L
@@ -243,6 +263,35 @@ class Graph:
         if not (allow_unconverged and st == 9):
             _check(st, "sc_estimate_lambda")
         return {name: getattr(out, name) for name, _ in Lambda._fields_}
+
+    def eigenpairs(self, omega: int = 128, max_iter: int = 0, tol: float = 0.0, rest_tol: float = 0.0,
+                   rest_max_iter: int = 0, seed: int = 0x1a2b3c4d, allow_unconverged: bool = False):
+        """sc_eigenpairs: (lam float64[omega], F float64[omega, n], report dict); lam[0] = 1, F[0] = 1,
+        the pairs taken exactly in rows 1 .. used - 1, zeros after them."""
+        opts = EigOpts(omega, max_iter, tol, rest_tol, rest_max_iter, 0, seed)
+        lam = np.zeros(omega, dtype=np.float64)
+        F = np.zeros((omega, self.n), dtype=np.float64)
+        rep = EigReport()
+        st = load().sc_eigenpairs(self._h, ctypes.byref(opts), _f64p(lam), _f64p(F), ctypes.byref(rep))
+        if not (allow_unconverged and st == 9):
+            _check(st, "sc_eigenpairs")
+        return lam, F, {name: getattr(rep, name) for name, _ in EigReport._fields_}
+
+    def caltau(self, eps: float, lam=None, F=None, lam_rest: float = 0.0):
+        """sc_caltau: (tau int32[nnz], longest length). lam / F None: the pairs of the last eigenpairs()."""
+        tau = np.empty(self.nnz, dtype=np.int32)
+        ell = ctypes.c_int32()
+        if lam is None:
+            st = load().sc_caltau(self._h, eps, 0, None, None, 0.0, _i32p(tau), ctypes.byref(ell))
+        else:
+            lam = np.ascontiguousarray(lam, dtype=np.float64)
+            F = np.ascontiguousarray(F, dtype=np.float64)
+            if F.shape != (lam.size, self.n):
+                raise ValueError(f"F must be {lam.size} x {self.n}")
+            st = load().sc_caltau(self._h, eps, lam.size, _f64p(lam), _f64p(F), float(lam_rest), _i32p(tau),
+                                  ctypes.byref(ell))
+        _check(st, "sc_caltau")
+        return tau, int(ell.value)
 
     def truncation_length(self, eps: float, lam: dict | None = None):
         """(ell_global, per_source int32[n], per_entry int32[nnz]) on the host."""
@@ -353,6 +402,23 @@ def all_edges_noalloc(row_ptr, col_idx, ell: int, out, stream=None):
 def _f32(a):
     a = np.ascontiguousarray(a, dtype=np.float32)
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def tridiag_eig(alpha, beta):
+    """sc_tridiag_eig (host only): eigenvalues ascending and eigenvectors as columns."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    k = a.size
+    if b.size != max(k - 1, 0):
+        raise ValueError("beta must hold k - 1 values")
+    theta = np.empty(k, dtype=np.float64)
+    Z = np.empty((k, k), dtype=np.float64)  # row q = eigenvector q (the C column q)
+    _check(load().sc_tridiag_eig(k, _f64p(a), _f64p(b) if k > 1 else None, _f64p(theta), _f64p(Z)), "sc_tridiag_eig")
+    return theta, Z.T.copy()
 
 
 def _i32p(a):

@@ -171,6 +171,17 @@ struct sc_graph {
     bool has_lambda = false;
     sc_lambda lam{};
 
+    // CalTau: the pairs of the last sc_eigenpairs (f_k node-major, n x eig_P,
+    // their eigenvalues and the bound r on the rest) and the last sc_caltau lengths
+    sc::DevBuf<double> eig_Fn;
+    std::vector<double> eig_lam;
+    double eig_rest = 1.0;
+    int32_t eig_P = 0;
+    bool eig_ready = false;
+    sc::DevBuf<int32_t> caltau_tau;
+    double caltau_eps = 0.0;
+    bool caltau_ready = false;
+
     // work buffers (grow-only)
     sc::DevBuf<unsigned char> xa, xb;   // probability blocks
     sc::DevBuf<double> acc_g, acc_t1, acc_t2;

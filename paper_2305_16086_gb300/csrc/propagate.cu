@@ -1100,7 +1100,11 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ takes the plain estimator, no tail records and an Eq. 6 length");
     const int gamma = o.gamma < 0 ? 10 : o.gamma;
     if (plus && gamma > kGammaMax) SC_FAIL(SC_ERR_UNSUPPORTED, "gamma %d above %d", gamma, kGammaMax);
-    if (o.ell_policy < SC_ELL_GLOBAL || o.ell_policy > SC_ELL_LEARNED) SC_FAIL(SC_ERR_INVALID_ARG, "length policy %d", o.ell_policy);
+    if (o.ell_policy < SC_ELL_GLOBAL || o.ell_policy > SC_ELL_CALTAU) SC_FAIL(SC_ERR_INVALID_ARG, "length policy %d", o.ell_policy);
+    const bool caltau = o.ell_policy == SC_ELL_CALTAU;
+    if (caltau && plus) SC_FAIL(SC_ERR_UNSUPPORTED, "the CalTau lengths serve TGT");
+    if (caltau && (!g->caltau_ready || g->caltau_eps != o.eps))
+        SC_FAIL(SC_ERR_INVALID_ARG, "no CalTau lengths for eps %g: call sc_caltau with it first", o.eps);
     if (o.ell_policy == SC_ELL_FIXED && o.ell_fixed < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_fixed < 0");
     if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
     const bool learned = o.ell_policy == SC_ELL_LEARNED;
@@ -1110,7 +1114,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     const bool out_dev = (o.flags & SC_OUT_DEVICE) != 0;
     const bool time_kernels = (o.flags & SC_OPT_TIME_KERNELS) != 0;
     const bool record_after = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
-    const bool need_lambda = o.ell_policy != SC_ELL_FIXED || record_after;
+    const bool need_lambda = (o.ell_policy != SC_ELL_FIXED && !caltau) || record_after;
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
     const int64_t nnz = g->nnz;
@@ -1134,7 +1138,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         sc_status st = estimate_lambda_impl(g, nullptr, &lam);
         if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
     }
-    if (o.ell_policy != SC_ELL_FIXED && (g->bipartite || g->lam.lambda_star >= 1.0))
+    if (o.ell_policy != SC_ELL_FIXED && !caltau && (g->bipartite || g->lam.lambda_star >= 1.0))
         SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1 (bipartite graph): no finite length meets eps; use a fixed "
                                     "length with the end-corrected estimator");
     const double lam_star = g->lam.lambda_star;
@@ -1149,6 +1153,15 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         ell_global = o.ell_fixed;
         std::fill(len.begin(), len.end(), o.ell_fixed);
         fill_i32(g->tau_entry.get(), nnz, o.ell_fixed, s);
+    } else if (caltau) {
+        // Algorithm 1's per-edge lengths; each source runs the longest of its edges
+        SC_CUDA(cudaMemcpyAsync(g->tau_entry.get(), g->caltau_tau.get(), nnz * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, s));
+        k_row_max<<<ceil_div(n, 256), 256, 0, s>>>(g->row_ptr.get(), g->tau_entry.get(), n, tau_src.get());
+        SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+        ell_global = *std::max_element(len.begin(), len.end());
     } else {
         // TGT+ (Algorithm 4) asks for a tail of at most eps/2 and leaves eps/2 to the walks
         tau_entries_device(g, plus ? 0.5 * o.eps : o.eps, lam_star, g->tau_entry.get(), tau_src.get(), &ell_global);

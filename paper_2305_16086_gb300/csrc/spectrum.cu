@@ -418,3 +418,568 @@ sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam, in
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// CalTau with omega eigenpairs (Algorithm 1, Eq. 6-8)
+// ===========================================================================
+//
+// Eigenpairs: Lanczos run 1 (lambda_1's vector locked) keeps its basis; the
+// tridiagonal Ritz problem is solved whole on the host (implicit symmetric QR);
+// the Ritz pairs among the omega - 1 largest moduli whose residual meets the
+// tolerance are the set U taken exactly. Their Ritz vectors (basis times the
+// tridiagonal eigenvectors) are locked into Lanczos run 2, which starts from a
+// fresh vector and so sees every mode outside U, the copies of a repeated
+// eigenvalue that run 1's single Krylov sequence holds one vector of included:
+// its extreme Ritz values give r, the bound on every mode left out. The proof
+// of Theorem 3.2 bounds each left-out term by r^(t+1) / (1 - r^2) c_k (1 +
+// lambda_k), which is what makes any such U admissible.
+//
+// CalTau per edge: one warp per edge (i < j), lanes over the modes of U
+// (f_k node-major, so an edge reads two contiguous rows): c_k, Upsilon (Eq.
+// 7), then Delta_t (Eq. 8) for t = 1, 3, 5, ... with one fixed-order warp sum
+// per t until Eq. 6 with the remainder no longer reaches t.
+#include <limits>
+#include <numeric>
+
+namespace sc {
+
+constexpr int kOmegaMax = SC_OMEGA_MAX;              // pairs, lambda_1 included
+constexpr int kModesPerLane = (kOmegaMax - 1 + 31) / 32;  // nontrivial modes per lane
+constexpr int32_t kCalTauMaxLen = 1 << 20;
+
+// Every eigenpair of the symmetric tridiagonal matrix with diagonal a[0..k)
+// and off-diagonal e[0..k-1) (e[i] couples i and i + 1) by the implicit
+// symmetric QR algorithm (Golub and Van Loan, Section 8.3): a Wilkinson shift
+// from the trailing 2 x 2 block of the unreduced block [lo, hi], one Givens
+// similarity on the shifted first column, then the bulge chased down by a
+// rotation per row; an off-diagonal at or below machine precision times its two
+// diagonal neighbours splits the matrix. Z (k x k, column-major, may be null)
+// accumulates the rotations from the identity, so column q ends as the unit
+// eigenvector of a[q]. Returns false when one eigenvalue takes more than 60 steps.
+static bool tridiag_qr(int k, std::vector<double> &a, std::vector<double> &e, double *Z) {
+    if (Z) {
+        std::fill(Z, Z + static_cast<size_t>(k) * k, 0.0);
+        for (int q = 0; q < k; ++q) Z[static_cast<size_t>(q) * k + q] = 1.0;
+    }
+    const double ulp = std::numeric_limits<double>::epsilon();
+    auto negligible = [&](int i) {  // e[i] against a[i], a[i + 1]
+        return std::fabs(e[i]) <= ulp * (std::fabs(a[i]) + std::fabs(a[i + 1])) || std::fabs(e[i]) < 1e-300;
+    };
+    int hi = k - 1, steps = 0;
+    while (hi > 0) {
+        if (negligible(hi - 1)) {
+            e[hi - 1] = 0.0;
+            --hi;
+            steps = 0;
+            continue;
+        }
+        if (++steps > 60) return false;
+        int lo = hi - 1;
+        while (lo > 0 && !negligible(lo - 1)) --lo;
+        if (lo > 0) e[lo - 1] = 0.0;
+        const double d = 0.5 * (a[hi - 1] - a[hi]);
+        const double eh = e[hi - 1];
+        const double mu = a[hi] - eh * eh / (d + std::copysign(std::hypot(d, eh), d));
+        double x = a[lo] - mu, z = e[lo];
+        for (int i = lo; i < hi; ++i) {
+            const double r = std::hypot(x, z);
+            const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? z / r : 0.0;
+            if (i > lo) e[i - 1] = r;  // the bulge at (i - 1, i + 1) is now zero
+            const double p = a[i], q = a[i + 1], b = e[i];
+            a[i] = c * c * p + 2.0 * c * s * b + s * s * q;
+            a[i + 1] = s * s * p - 2.0 * c * s * b + c * c * q;
+            e[i] = c * s * (q - p) + (c * c - s * s) * b;
+            if (i + 1 < hi) {  // the new bulge at (i, i + 2)
+                x = e[i];
+                z = s * e[i + 1];
+                e[i + 1] *= c;
+            }
+            if (Z) {
+                double *zi = Z + static_cast<size_t>(i) * k, *zj = zi + k;
+                for (int row = 0; row < k; ++row) {
+                    const double u = zi[row], v = zj[row];
+                    zi[row] = c * u + s * v;
+                    zj[row] = -s * u + c * v;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// tridiag_qr, then the pairs in ascending order of eigenvalue
+static bool tridiag_eig_sorted(int k, const double *alpha, const double *beta_off, std::vector<double> &theta,
+                               std::vector<double> *Z) {
+    std::vector<double> a(alpha, alpha + k), e(k > 1 ? k - 1 : 1, 0.0);
+    for (int i = 0; i + 1 < k; ++i) e[i] = beta_off[i];
+    std::vector<double> Zw;
+    if (Z) Zw.resize(static_cast<size_t>(k) * k);
+    if (!tridiag_qr(k, a, e, Z ? Zw.data() : nullptr)) return false;
+    std::vector<int> ord(k);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return a[u] < a[v]; });
+    theta.resize(k);
+    for (int q = 0; q < k; ++q) theta[q] = a[ord[q]];
+    if (Z) {
+        Z->resize(static_cast<size_t>(k) * k);
+        for (int q = 0; q < k; ++q)
+            std::copy(Zw.begin() + static_cast<size_t>(ord[q]) * k, Zw.begin() + static_cast<size_t>(ord[q] + 1) * k,
+                      Z->begin() + static_cast<size_t>(q) * k);
+    }
+    return true;
+}
+
+// Lanczos on N restricted to the complement of V[0..nlock) (orthonormal on
+// entry), CGS2 against the whole basis; V[nlock..nlock + k) receives the
+// basis. The host reads the step coefficients at the checks (every 4th step
+// from step 8, and the last). tol > 0: stops when both extreme Ritz pairs meet
+// tol; tol = 0: runs max_iter steps. A breakdown (|w| <= 1e-12) ends the run
+// at that step (the Krylov space is exhausted).
+struct LanczosOut {
+    std::vector<double> alpha, beta;  // T: alpha[0..k), beta[1..k) (beta[0] = 0 unused)
+    int k = 0;
+    double bnext = 0.0;  // |w| after step k: the Ritz residual of pair q is bnext |z_q[k - 1]|
+    bool exhausted = false, converged = false;
+    double theta_max = 0, theta_min = 0, res_max = INFINITY, res_min = INFINITY;
+};
+
+static LanczosOut lanczos_run(sc_graph *g, double *V, int64_t ldv, int nlock, int max_iter, double tol, uint64_t seed,
+                              const double *isd) {
+    LanczosOut L;
+    const int32_t n = g->n;
+    cudaStream_t s = g->stream;
+    const int nbasis = nlock + max_iter + 1;
+    DevBuf<double> w, c, partial, ab;
+    w.reserve(n);
+    c.reserve(2 * static_cast<size_t>(nbasis) + 8);
+    const int ts_ctas = 2 * (g->num_sms > 0 ? g->num_sms : 148);
+    const int32_t ts_chunk = (ceil_div(n, ts_ctas) + 31) / 32 * 32;
+    partial.reserve(static_cast<size_t>(nbasis) * std::max(kDotBlocks, ts_ctas));
+    ab.reserve(2 * static_cast<size_t>(max_iter));
+    const int tb = 256, nb = ceil_div(n, tb);
+    auto reorth = [&](int nv) {
+        for (int pass = 0; pass < 2; ++pass) {
+            double *cc = c.get() + (pass ? nbasis : 0);
+            k_tsdot_partial<<<ts_ctas, kTsThreads, 0, s>>>(V, ldv, nv, w.get(), n, ts_chunk, partial.get());
+            k_tsdot_final<<<ceil_div(nv, 8), 256, 0, s>>>(partial.get(), ts_ctas, nv, cc);
+            k_sub_combination<<<nb, tb, 0, s>>>(V, ldv, nv, cc, w.get(), n);
+            SC_LAUNCH_CHECK();
+        }
+    };
+    auto norm2_into = [&](double *dst) {
+        k_multidot_partial<<<dim3(kDotBlocks, 1), kDotThreads, 0, s>>>(w.get(), ldv, 1, w.get(), n, partial.get());
+        k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), dst);
+        SC_LAUNCH_CHECK();
+    };
+    k_start_vector<<<nb, tb, 0, s>>>(w.get(), n, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    SC_LAUNCH_CHECK();
+    reorth(nlock);
+    double *nrm_dev = c.get() + 2 * nbasis;
+    norm2_into(nrm_dev);
+    k_scale_into<<<nb, tb, 0, s>>>(w.get(), nrm_dev, V + nlock * ldv, n);
+    SC_LAUNCH_CHECK();
+    double *d_alpha = ab.get(), *d_nrm2 = ab.get() + max_iter;
+    std::vector<double> h_alpha, h_nrm2;
+    L.beta.assign(1, 0.0);
+    int k = 0;
+    for (int j = 0; j < max_iter; ++j) {
+        const int vj = nlock + j;
+        k_spmv_norm<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), isd, V + vj * ldv, w.get(), n);
+        SC_LAUNCH_CHECK();
+        reorth(vj + 1);
+        k_alpha_of<<<1, 1, 0, s>>>(c.get(), nbasis, vj, d_alpha + j);
+        norm2_into(d_nrm2 + j);
+        const int kk = j + 1;
+        const bool last = kk == max_iter || kk == n - nlock;
+        if (last || (kk >= 8 && kk % 4 == 0)) {
+            h_alpha.resize(kk);
+            h_nrm2.resize(kk);
+            SC_CUDA(cudaMemcpyAsync(h_alpha.data(), d_alpha, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaMemcpyAsync(h_nrm2.data(), d_nrm2, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            bool exhausted = kk == n - nlock;
+            int stop = kk;
+            for (int q = static_cast<int>(L.alpha.size()); q < kk; ++q) {
+                L.alpha.push_back(h_alpha[q]);
+                const double b = std::sqrt(std::max(h_nrm2[q], 0.0));
+                if (!(b > 1e-12)) {
+                    stop = q + 1;
+                    exhausted = true;
+                    break;
+                }
+                if (q + 1 < kk) L.beta.push_back(b);
+            }
+            k = stop;
+            L.bnext = std::sqrt(std::max(h_nrm2[stop - 1], 0.0));
+            L.exhausted = exhausted;
+            if (tol > 0.0) {
+                L.theta_max = bisect_eig(L.alpha, L.beta, k, k - 1, -1.0 - 1e-9, 1.0 + 1e-9);
+                L.theta_min = bisect_eig(L.alpha, L.beta, k, 0, -1.0 - 1e-9, 1.0 + 1e-9);
+                L.res_max = exhausted ? 0.0 : L.bnext * std::fabs(ritz_last_component(L.alpha, L.beta, k, L.theta_max));
+                L.res_min = exhausted ? 0.0 : L.bnext * std::fabs(ritz_last_component(L.alpha, L.beta, k, L.theta_min));
+                if (L.res_max <= tol && L.res_min <= tol) {
+                    L.converged = true;
+                    break;
+                }
+            }
+            if (exhausted || last) break;
+            L.beta.push_back(L.bnext);
+        }
+        k = kk;
+        k_scale_into<<<nb, tb, 0, s>>>(w.get(), d_nrm2 + j, V + (vj + 1) * ldv, n);
+        SC_LAUNCH_CHECK();
+    }
+    L.k = k;
+    L.alpha.resize(k);
+    L.beta.resize(k);
+    return L;
+}
+
+// Y_p = sum_j V[j] Zu[j, p] for p < P (Ritz vectors), into Y + p * ldv; thread
+// per row, 32 columns of Zu per grid row, j in order
+constexpr int kRitzCols = 32;
+__global__ void k_ritz_vectors(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ Zu, int P,
+                               int32_t n, double *__restrict__ Y) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int p0 = blockIdx.y * kRitzCols;
+    if (i >= n) return;
+    const int np = min(kRitzCols, P - p0);
+    double acc[kRitzCols];
+#pragma unroll
+    for (int u = 0; u < kRitzCols; ++u) acc[u] = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const double v = V[j * ldv + i];
+        const double *z = Zu + static_cast<int64_t>(j) * P + p0;
+#pragma unroll
+        for (int u = 0; u < kRitzCols; ++u)
+            if (u < np) acc[u] += v * z[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kRitzCols; ++u)
+        if (u < np) Y[(p0 + u) * ldv + i] = acc[u];
+}
+
+// Frow[p * n + i] = sqrt(2m) isd[i] Y_p[i]: f_k = sqrt(2m) D^-1/2 phi_k
+__global__ void k_f_rows(const double *__restrict__ Y, int64_t ldv, int P, const double *__restrict__ isd,
+                         double sqrt_2m, int32_t n, double *__restrict__ Frow) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int p = blockIdx.y;
+    if (i >= n || p >= P) return;
+    Frow[static_cast<int64_t>(p) * n + i] = sqrt_2m * isd[i] * Y[p * ldv + i];
+}
+
+// Fn[i * P + p] = Frow[p * n + i] (32 x 32 tiles through shared memory)
+__global__ void k_rows_to_nodes(const double *__restrict__ Frow, int32_t n, int P, double *__restrict__ Fn) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int p0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int p = p0 + r;
+        const int64_t i = i0 + threadIdx.x;
+        if (p < P && i < n) tile[r][threadIdx.x] = Frow[static_cast<int64_t>(p) * n + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r;
+        const int p = p0 + threadIdx.x;
+        if (p < P && i < n) Fn[i * P + p] = tile[threadIdx.x][r];
+    }
+}
+
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;  // every lane holds the same value (each butterfly stage adds a pair in both orders)
+}
+
+// Algorithm 1 per edge, one warp per row (grid-stride), its entries (i -> j),
+// j > i, one at a time; the length goes to both directions of the edge.
+__global__ void k_caltau(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                         const int32_t *__restrict__ rev, int32_t n, const double *__restrict__ Fn,
+                         const double *__restrict__ lam, int P, double lam_rest, double lam_top, double eps,
+                         double two_m, int32_t *__restrict__ tau, int32_t *ell_max) {
+    const int lane = threadIdx.x & 31;
+    const double denom0 = __dmul_rn(eps, __dsub_rn(1.0, __dmul_rn(lam_top, lam_top)));
+    const double log_inv_top = log(__ddiv_rn(1.0, lam_top));
+    const double rest_scale = __dsub_rn(1.0, __dmul_rn(lam_rest, lam_rest));
+    const double log_inv_rest = lam_rest > 0.0 ? log(__ddiv_rn(1.0, lam_rest)) : 0.0;
+    int32_t best = 0;
+    for (int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += gridDim.x * (blockDim.x >> 5)) {
+        const double di = static_cast<double>(row_ptr[r + 1] - row_ptr[r]);
+        for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            const int32_t j = col[k];
+            if (j <= r) continue;  // warp-uniform
+            const double dj = static_cast<double>(row_ptr[j + 1] - row_ptr[j]);
+            const double xe =
+                __dsub_rn(__dadd_rn(__ddiv_rn(1.0, di), __ddiv_rn(1.0, dj)), __ddiv_rn(2.0, __dmul_rn(di, dj)));
+            // Eq. 6 with lambda_star alone: the starting length
+            int32_t tau0 = 1;
+            if (xe > 0.0 && lam_top > 0.0) {
+                const double f = ceil(__dsub_rn(__ddiv_rn(log(__ddiv_rn(xe, denom0)), log_inv_top), 1.0));
+                if (f > 1.0) tau0 = f > static_cast<double>(kCalTauMaxLen) ? kCalTauMaxLen : static_cast<int32_t>(f);
+            }
+            if ((tau0 & 1) == 0) tau0 += 1;
+            // c_q, the Eq. 8 weights lambda^(t+1) / (1 - lambda) at t = 1, and Eq. 7
+            double cq[kModesPerLane], wq[kModesPerLane], l2[kModesPerLane];
+            double ups = 0.0;
+#pragma unroll
+            for (int u = 0; u < kModesPerLane; ++u) {
+                const int q = lane + 32 * u;
+                cq[u] = wq[u] = l2[u] = 0.0;
+                if (q < P) {
+                    const double d = __dsub_rn(Fn[static_cast<int64_t>(r) * P + q], Fn[static_cast<int64_t>(j) * P + q]);
+                    const double lq = lam[q];
+                    cq[u] = __dmul_rn(d, d);
+                    l2[u] = __dmul_rn(lq, lq);
+                    wq[u] = __ddiv_rn(l2[u], __dsub_rn(1.0, lq));
+                    ups = __fma_rn(__dadd_rn(1.0, lq), cq[u], ups);
+                }
+            }
+            ups = __ddiv_rn(warp_sum_fixed(ups), two_m);
+            const double num = __dsub_rn(xe, ups);  // X_e - Upsilon: the remainder's weight
+            const bool none_left = num <= 0.0 || lam_rest == 0.0;
+            int32_t out = tau0;
+            for (int32_t t = 1; t < tau0; t += 2) {
+                double dp = 0.0;
+#pragma unroll
+                for (int u = 0; u < kModesPerLane; ++u) dp = __fma_rn(wq[u], cq[u], dp);
+                const double budget = __dsub_rn(eps, __ddiv_rn(warp_sum_fixed(dp), two_m));
+                const bool spent = budget < 0.0 || (!none_left && budget == 0.0);
+                bool stop;
+                if (spent) stop = false;  // Delta_t alone exceeds eps: a longer t is needed
+                else if (none_left) stop = true;
+                else {
+                    const double f = ceil(__dsub_rn(
+                        __ddiv_rn(log(__ddiv_rn(num, __dmul_rn(budget, rest_scale))), log_inv_rest), 1.0));
+                    stop = static_cast<double>(t) > f;
+                }
+                if (stop) {
+                    out = t;
+                    break;
+                }
+#pragma unroll
+                for (int u = 0; u < kModesPerLane; ++u) wq[u] = __dmul_rn(wq[u], l2[u]);
+            }
+            if (lane == 0) {
+                tau[k] = out;
+                tau[rev[k]] = out;
+            }
+            best = max(best, out);
+        }
+    }
+    if (lane == 0 && best > 0) atomicMax(ell_max, best);
+}
+
+// the longest Eq. 6 length any edge can have (X_e <= 1)
+static double eq6_len_bound(double eps, double lam) {
+    if (!(lam > 0.0)) return 1.0;
+    return std::ceil(std::log(1.0 / (eps * (1.0 - lam * lam))) / std::log(1.0 / lam) - 1.0);
+}
+
+static void caltau_device(sc_graph *g, double eps, const double *Fn_dev, const std::vector<double> &lam_used,
+                          double lam_rest, int32_t *ell_out) {
+    const int P = static_cast<int>(lam_used.size());
+    double lam_top = lam_rest;
+    for (double l : lam_used) lam_top = std::max(lam_top, std::fabs(l));
+    if (!(lam_top < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "a modulus >= 1 among the pairs or the rest bound");
+    if (eq6_len_bound(eps, lam_top) > kCalTauMaxLen)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "Eq. 6's length passes 2^20 at lambda_star %.17g", lam_top);
+    cudaStream_t s = g->stream;
+    DevBuf<double> lam_dev;
+    lam_dev.reserve(std::max(P, 1));
+    if (P > 0)
+        SC_CUDA(cudaMemcpyAsync(lam_dev.get(), lam_used.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
+    g->caltau_tau.reserve(g->nnz);
+    g->status.reserve(4);
+    SC_CUDA(cudaMemsetAsync(g->status.get(), 0, sizeof(int32_t), s));
+    const int grid = std::max(1, std::min(ceil_div(g->n, 8), (g->num_sms > 0 ? g->num_sms : 148) * 8));
+    k_caltau<<<grid, 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->n, Fn_dev, lam_dev.get(), P,
+                                  lam_rest, lam_top, eps, static_cast<double>(g->nnz), g->caltau_tau.get(),
+                                  g->status.get());
+    SC_LAUNCH_CHECK();
+    int32_t ell = 0;
+    SC_CUDA(cudaMemcpyAsync(&ell, g->status.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    g->caltau_eps = eps;
+    g->caltau_ready = true;
+    if (ell_out) *ell_out = ell;
+}
+
+sc_status eigenpairs_impl(sc_graph *g, const sc_eig_opts *opts, double *lam_out, double *F_out, sc_eig_report *rep) {
+    return guarded([&] {
+        if (!g || !lam_out) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or lam_out");
+        const int32_t n = g->n;
+        const int omega = opts ? opts->omega : 128;
+        if (omega < 2 || omega > kOmegaMax || omega > n)
+            SC_FAIL(SC_ERR_INVALID_ARG, "omega %d not in [2, min(%d, n)]", omega, kOmegaMax);
+        if (g->bipartite) SC_FAIL(SC_ERR_UNSUPPORTED, "bipartite graph: lambda = -1 is a mode of modulus 1");
+        const int max_iter = std::min(n - 1, (opts && opts->max_iter > 0) ? opts->max_iter : 3 * omega + 64);
+        const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-8;
+        const double rest_tol = (opts && opts->rest_tol > 0) ? opts->rest_tol : 1e-6;
+        const int rest_iter_opt = (opts && opts->rest_max_iter > 0) ? opts->rest_max_iter : 500;
+        const uint64_t seed = opts ? opts->seed : 0x1a2b3c4dULL;
+        if (max_iter < 1) SC_FAIL(SC_ERR_INVALID_ARG, "graph too small for Lanczos");
+        cudaStream_t s = g->stream;
+        const int64_t ldv = (static_cast<int64_t>(n) + 31) / 32 * 32;
+        const int tb = 256, nb = ceil_div(n, tb);
+        const double two_m = static_cast<double>(g->nnz);
+        DevBuf<double> isd, V;
+        isd.reserve(n);
+        V.reserve(static_cast<size_t>(max_iter + 2) * ldv);
+        k_locked_vectors<<<nb, tb, 0, s>>>(g->row_ptr.get(), g->level.get(), n, 1.0 / std::sqrt(two_m), 0, V.get(),
+                                           V.get() + ldv, isd.get());
+        SC_LAUNCH_CHECK();
+        // run 1: Ritz pairs
+        LanczosOut L1 = lanczos_run(g, V.get(), ldv, 1, max_iter, 0.0, seed, isd.get());
+        const int k = L1.k;
+        std::vector<double> theta, Z;
+        std::vector<double> off(std::max(k - 1, 1), 0.0);
+        for (int i = 0; i + 1 < k; ++i) off[i] = L1.beta[i + 1];
+        if (!tridiag_eig_sorted(k, L1.alpha.data(), off.data(), theta, &Z))
+            SC_FAIL(SC_ERR_LAMBDA_NOT_CONVERGED, "tridiagonal QR did not converge (k = %d)", k);
+        std::vector<int> ord(k);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) {
+            const double au = std::fabs(theta[u]), av = std::fabs(theta[v]);
+            return au != av ? au > av : theta[u] > theta[v];
+        });
+        std::vector<int> U;
+        double max_res = 0.0;
+        for (int q : ord) {
+            if (static_cast<int>(U.size()) == omega - 1) break;
+            const double res = L1.exhausted ? 0.0 : L1.bnext * std::fabs(Z[static_cast<size_t>(q) * k + k - 1]);
+            if (res <= tol) {
+                U.push_back(q);
+                max_res = std::max(max_res, res);
+            }
+        }
+        const int P = static_cast<int>(U.size());
+        // run 2 basis: lambda_1's vector, the Ritz vectors of U, then the new steps
+        const int rest_iter = std::min(rest_iter_opt, n - 1 - P);
+        DevBuf<double> V2;
+        V2.reserve(static_cast<size_t>(1 + P + std::max(rest_iter, 0) + 1) * ldv);
+        SC_CUDA(cudaMemcpyAsync(V2.get(), V.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (P > 0) {
+            std::vector<double> Zu(static_cast<size_t>(k) * P);
+            for (int j = 0; j < k; ++j)
+                for (int p = 0; p < P; ++p) Zu[static_cast<size_t>(j) * P + p] = Z[static_cast<size_t>(U[p]) * k + j];
+            DevBuf<double> Zu_dev;
+            Zu_dev.reserve(Zu.size());
+            SC_CUDA(cudaMemcpyAsync(Zu_dev.get(), Zu.data(), Zu.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_ritz_vectors<<<dim3(nb, ceil_div(P, kRitzCols)), tb, 0, s>>>(V.get() + ldv, ldv, k, Zu_dev.get(), P, n,
+                                                                            V2.get() + ldv);
+            SC_LAUNCH_CHECK();
+            SC_CUDA(cudaStreamSynchronize(s));  // Zu_dev and V are released below
+        }
+        V.release();
+        // run 2: the largest modulus outside U
+        LanczosOut L2;
+        double lam_rest = 0.0;
+        if (rest_iter > 0) {
+            L2 = lanczos_run(g, V2.get(), ldv, 1 + P, rest_iter, rest_tol, seed + 1, isd.get());
+            lam_rest = std::max(std::fabs(L2.theta_max), std::fabs(L2.theta_min)) + std::max(L2.res_max, L2.res_min) +
+                       max_res;
+        } else {
+            L2.converged = true;
+            L2.res_max = L2.res_min = 0.0;
+        }
+        // f_k rows and the node-major copy kept for sc_caltau
+        std::vector<double> lam_used(P);
+        for (int p = 0; p < P; ++p) lam_used[p] = theta[U[p]];
+        DevBuf<double> Frow;
+        Frow.reserve(std::max<size_t>(static_cast<size_t>(P) * n, 1));
+        g->eig_Fn.reserve(std::max<size_t>(static_cast<size_t>(P) * n, 1));
+        if (P > 0) {
+            k_f_rows<<<dim3(nb, P), tb, 0, s>>>(V2.get() + ldv, ldv, P, isd.get(), std::sqrt(two_m), n, Frow.get());
+            k_rows_to_nodes<<<dim3(ceil_div(n, 32), ceil_div(P, 32)), dim3(32, 8), 0, s>>>(Frow.get(), n, P,
+                                                                                          g->eig_Fn.get());
+            SC_LAUNCH_CHECK();
+        }
+        g->eig_lam = lam_used;
+        g->eig_rest = std::min(lam_rest, 1.0);
+        g->eig_P = P;
+        g->eig_ready = true;
+        std::fill(lam_out, lam_out + omega, 0.0);
+        lam_out[0] = 1.0;
+        std::copy(lam_used.begin(), lam_used.end(), lam_out + 1);
+        if (F_out) {
+            std::fill(F_out, F_out + static_cast<size_t>(omega) * n, 0.0);
+            std::fill(F_out, F_out + n, 1.0);
+            if (P > 0)
+                SC_CUDA(cudaMemcpyAsync(F_out + n, Frow.get(), static_cast<size_t>(P) * n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, s));
+        }
+        SC_CUDA(cudaStreamSynchronize(s));
+        if (rep) {
+            rep->used = 1 + P;
+            rep->iterations = k;
+            rep->rest_iterations = rest_iter > 0 ? L2.k : 0;
+            rep->rest_converged = L2.converged ? 1 : 0;
+            rep->max_residual = max_res;
+            rep->rest_residual = std::max(L2.res_max, L2.res_min);
+            rep->lambda_rest = lam_rest;
+        }
+        if (!L2.converged)
+            SC_FAIL(SC_ERR_LAMBDA_NOT_CONVERGED, "second Lanczos run: residuals %.3g / %.3g above %.3g after %d steps",
+                    L2.res_max, L2.res_min, rest_tol, L2.k);
+    });
+}
+
+}  // namespace sc
+
+extern "C" {
+
+sc_status sc_eigenpairs(sc_graph *g, const sc_eig_opts *opts, double *lam_out, double *F_out, sc_eig_report *report) {
+    return sc::eigenpairs_impl(g, opts, lam_out, F_out, report);
+}
+
+sc_status sc_caltau(sc_graph *g, double eps, int32_t count, const double *lam, const double *F, double lam_rest,
+                    int32_t *tau_out, int32_t *ell_out) {
+    return sc::guarded([&] {
+        if (!g) SC_FAIL(SC_ERR_INVALID_ARG, "null graph");
+        if (!(eps > 0.0 && eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1)");
+        if (g->bipartite) SC_FAIL(SC_ERR_UNSUPPORTED, "bipartite graph: lambda = -1 is a mode of modulus 1");
+        cudaStream_t s = g->stream;
+        const int32_t n = g->n;
+        int32_t ell = 0;
+        if (count == 0) {
+            if (!g->eig_ready) SC_FAIL(SC_ERR_INVALID_ARG, "no eigenpairs: call sc_eigenpairs first or pass them");
+            sc::caltau_device(g, eps, g->eig_Fn.get(), g->eig_lam, g->eig_rest, &ell);
+        } else {
+            if (count < 2 || count > sc::kOmegaMax) SC_FAIL(SC_ERR_INVALID_ARG, "count %d not in [2, %d]", count, sc::kOmegaMax);
+            if (!lam || !F) SC_FAIL(SC_ERR_INVALID_ARG, "null lam or F");
+            if (!(lam_rest >= 0.0 && lam_rest < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "lam_rest %g not in [0, 1)", lam_rest);
+            const int P = count - 1;
+            std::vector<double> lam_used(lam + 1, lam + count);
+            for (double l : lam_used)
+                if (!(std::fabs(l) < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "|lambda| = %g is not below 1", l);
+            sc::DevBuf<double> Frow, Fn;
+            Frow.reserve(static_cast<size_t>(P) * n);
+            Fn.reserve(static_cast<size_t>(P) * n);
+            SC_CUDA(cudaMemcpyAsync(Frow.get(), F + n, static_cast<size_t>(P) * n * sizeof(double),
+                                    cudaMemcpyHostToDevice, s));
+            sc::k_rows_to_nodes<<<dim3(sc::ceil_div(n, 32), sc::ceil_div(P, 32)), dim3(32, 8), 0, s>>>(Frow.get(), n, P,
+                                                                                                      Fn.get());
+            SC_LAUNCH_CHECK();
+            sc::caltau_device(g, eps, Fn.get(), lam_used, lam_rest, &ell);
+        }
+        if (ell_out) *ell_out = ell;
+        if (tau_out) {
+            SC_CUDA(cudaMemcpyAsync(tau_out, g->caltau_tau.get(), g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+sc_status sc_tridiag_eig(int32_t k, const double *alpha, const double *beta, double *theta, double *Z) {
+    return sc::guarded([&] {
+        if (k < 1 || !alpha || !theta || (k > 1 && !beta)) SC_FAIL(SC_ERR_INVALID_ARG, "k < 1 or a null array");
+        std::vector<double> th, Zv;
+        if (!sc::tridiag_eig_sorted(k, alpha, beta, th, Z ? &Zv : nullptr))
+            SC_FAIL(SC_ERR_LAMBDA_NOT_CONVERGED, "an eigenvalue took more than 60 QR steps");
+        std::copy(th.begin(), th.end(), theta);
+        if (Z) std::copy(Zv.begin(), Zv.end(), Z);
+    });
+}
+
+}  // extern "C"

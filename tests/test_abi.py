@@ -68,6 +68,9 @@ LAYOUT_C = r"""
 int main(void) {
   printf("sc_graph_info %zu\nsc_lambda %zu\nsc_lambda_opts %zu\nsc_options %zu\nsc_report %zu\n",
          sizeof(sc_graph_info), sizeof(sc_lambda), sizeof(sc_lambda_opts), sizeof(sc_options), sizeof(sc_report));
+  printf("sc_eig_opts %zu\nsc_eig_report %zu\n", sizeof(sc_eig_opts), sizeof(sc_eig_report));
+  F(sc_eig_opts, tol) F(sc_eig_opts, rest_tol) F(sc_eig_opts, rest_max_iter) F(sc_eig_opts, seed)
+  F(sc_eig_report, rest_converged) F(sc_eig_report, max_residual) F(sc_eig_report, lambda_rest)
   F(sc_options, seed) F(sc_options, delta) F(sc_options, gamma) F(sc_options, flags) F(sc_options, bf16_from_hop)
   F(sc_report, algorithmic_bytes) F(sc_report, walks) F(sc_report, edges_extended) F(sc_report, total_ms)
   F(sc_report, hop_ms) F(sc_report, hop_launches) F(sc_report, hop_bytes) F(sc_report, tt_min) F(sc_report, tt_max) F(sc_report, switch_ms) F(sc_report, walk_ms) F(sc_report, source_hops) F(sc_report, extension_rounds) F(sc_report, windowed) F(sc_report, walk_steps) F(sc_report, walk_device_ms)
@@ -85,7 +88,8 @@ def test_struct_layouts_match_c(tmp_path):
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     c = dict(line.split() for line in lines if line.strip())
     py = {"sc_graph_info": binding.GraphInfo, "sc_lambda": binding.Lambda, "sc_lambda_opts": binding.LambdaOpts,
-          "sc_options": binding.Options, "sc_report": binding.Report}
+          "sc_options": binding.Options, "sc_report": binding.Report, "sc_eig_opts": binding.EigOpts,
+          "sc_eig_report": binding.EigReport}
     for name, cls in py.items():
         assert int(c[name]) == ctypes.sizeof(cls), name
     for key, val in c.items():
@@ -104,7 +108,7 @@ int main(void) {
   P(SC_ERR_LAMBDA_NOT_CONVERGED) P(SC_ERR_BOUND_UNMET) P(SC_ERR_TIMEOUT) P(SC_ERR_OOM) P(SC_ERR_CUDA)
   P(SC_ERR_UNSUPPORTED)
   P(SC_PTRS_HOST) P(SC_PTRS_DEVICE) P(SC_FLAG_REJECT_BIPARTITE)
-  P(SC_ELL_GLOBAL) P(SC_ELL_PER_EDGE) P(SC_ELL_FIXED) P(SC_ELL_LEARNED)
+  P(SC_ELL_GLOBAL) P(SC_ELL_PER_EDGE) P(SC_ELL_FIXED) P(SC_ELL_LEARNED) P(SC_ELL_CALTAU) P(SC_OMEGA_MAX)
   P(SC_PREC_FP64) P(SC_PREC_FP32) P(SC_PREC_BF16) P(SC_EST_PLAIN) P(SC_EST_END_CORRECTED)
   P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER)
   P(SC_OUT_DEVICE) P(SC_OPT_RECORD_TAIL) P(SC_OPT_TIME_KERNELS) P(SC_OPT_WINDOWS_OFF) P(SC_OPT_WINDOWS_FORCE)
@@ -135,6 +139,7 @@ def test_header_constants_match_binding(tmp_path):
     for name in ("SC_OUT_DEVICE", "SC_OPT_RECORD_TAIL", "SC_OPT_TIME_KERNELS", "SC_OPT_WINDOWS_OFF",
                  "SC_OPT_WINDOWS_FORCE"):
         assert c[name] == getattr(binding, name), name
+    assert c["SC_OMEGA_MAX"] == binding.OMEGA_MAX
     assert (c["SC_MLP_PARAMS"], c["SC_MLP_FEATURES"], c["SC_MLP_MODEL_FLOATS"]) == (
         binding.MLP_PARAMS, binding.MLP_FEATURES, binding.MLP_MODEL_FLOATS)
 
@@ -150,3 +155,12 @@ def test_selftest_rejects_a_limit_out_of_range():
     for bad in (0, 1000001):
         st, detail = binding.selftest_bounded_waits(bad)
         assert binding.STATUS_NAMES[st] == "SC_ERR_INVALID_ARG" and "limit_us" in detail
+
+
+def test_tridiag_eig_rejects_bad_arguments():
+    lib = binding.load()
+    theta = (ctypes.c_double * 2)()
+    a = (ctypes.c_double * 2)(1.0, 2.0)
+    assert binding.STATUS_NAMES[lib.sc_tridiag_eig(0, a, a, theta, None)] == "SC_ERR_INVALID_ARG"
+    assert binding.STATUS_NAMES[lib.sc_tridiag_eig(2, a, None, theta, None)] == "SC_ERR_INVALID_ARG"
+    assert binding.STATUS_NAMES[lib.sc_tridiag_eig(2, None, a, theta, None)] == "SC_ERR_INVALID_ARG"
