@@ -552,16 +552,14 @@ static LanczosOut lanczos_run(sc_graph *g, double *V, int64_t ldv, int nlock, in
     DevBuf<double> w, c, partial, ab;
     w.reserve(n);
     c.reserve(2 * static_cast<size_t>(nbasis) + 8);
-    const int ts_ctas = 2 * (g->num_sms > 0 ? g->num_sms : 148);
-    const int32_t ts_chunk = (ceil_div(n, ts_ctas) + 31) / 32 * 32;
-    partial.reserve(static_cast<size_t>(nbasis) * std::max(kDotBlocks, ts_ctas));
+    partial.reserve(static_cast<size_t>(nbasis) * kDotBlocks);
     ab.reserve(2 * static_cast<size_t>(max_iter));
     const int tb = 256, nb = ceil_div(n, tb);
     auto reorth = [&](int nv) {
         for (int pass = 0; pass < 2; ++pass) {
             double *cc = c.get() + (pass ? nbasis : 0);
-            k_tsdot_partial<<<ts_ctas, kTsThreads, 0, s>>>(V, ldv, nv, w.get(), n, ts_chunk, partial.get());
-            k_tsdot_final<<<ceil_div(nv, 8), 256, 0, s>>>(partial.get(), ts_ctas, nv, cc);
+            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V, ldv, nv, w.get(), n, partial.get());
+            k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), cc);
             k_sub_combination<<<nb, tb, 0, s>>>(V, ldv, nv, cc, w.get(), n);
             SC_LAUNCH_CHECK();
         }

@@ -10,9 +10,14 @@ Tolerances:
     equal the oracle's at eps;
   * Ritz values against the dense spectrum: 1e-8 (the residual tolerance of
     the pairs taken); c_k = (f_k[i] - f_k[j])^2 against the dense vectors of a
-    simple eigenvalue: 1e-6 relative to max c_k;
+    simple eigenvalue: 1e-5 relative to max c_k (a Ritz vector's error is at
+    most its residual, <= 1e-8, over the gap to the rest of the spectrum,
+    Davis-Kahan; gaps here are above 1e-3; a numpy model of the two runs,
+    over six start vectors, stays below 1.3e-7);
   * the series at the CalTau lengths: 1e-12 (FP64 blocks), and within eps of
     the exact value (Theorem 3.2).
+
+The file is named so that pytest collects it after the other GPU suites.
 """
 import numpy as np
 import pytest
@@ -91,7 +96,7 @@ def test_eigenpairs_against_the_dense_spectrum(cuda_lib, maker):
         if mult == 1:  # a simple eigenvalue: the vector is fixed up to sign
             c_gpu = (F[k, rows] - F[k, cols]) ** 2
             c_ref = (F_all[q, rows] - F_all[q, cols]) ** 2
-            assert np.max(np.abs(c_gpu - c_ref)) < 1e-6 * max(c_ref.max(), 1e-30)
+            assert np.max(np.abs(c_gpu - c_ref)) < 1e-5 * max(c_ref.max(), 1e-30)
     # r bounds every nontrivial mode not taken (one copy per taken value removed)
     rest = np.setdiff1d(np.arange(1, g.n), taken)
     assert rep["lambda_rest"] >= np.max(np.abs(lam_all[rest])) - 1e-9
