@@ -163,3 +163,27 @@ def test_caltau_errors(cuda_lib):
         lam, F = truncation.eigenpairs_by_modulus(*_csr(g), 3)
         with pytest.raises(ScError, match="SC_ERR_INVALID_ARG"):
             G.caltau(1e-2, lam, F, lam_rest=1.0)
+
+
+@pytest.mark.slow
+def test_planted_partition_sampled_within_eps(cuda_lib):
+    """16 communities of 2,500 nodes (15 eigenvalues near 1): the device pairs
+    take the slow modes exactly, every sampled edge is within eps of the CG
+    value, and the lengths are a fraction of Eq. 6's."""
+    from paper_2305_16086_gb300 import Graph
+
+    g = gg.planted_partition(16, 2500, 10.0, 0.3, 7)
+    rng = np.random.default_rng(7)
+    e = g.edges()
+    pick = e[rng.choice(e.shape[0], size=300, replace=False)]
+    k = exact.entry_of_edges(g.n, g.row_ptr, g.col_idx, pick)
+    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, pick)
+    with Graph(g.row_ptr, g.col_idx) as G:
+        lam, _, rep = G.eigenpairs(omega=32)
+        assert rep["used"] >= 16 and np.all(lam[1:16] > 0.9)
+        tau, _ = G.caltau(1e-3)
+        s, _, _ = G.all_edges(eps=1e-3, policy="caltau", precision="fp32")
+        G.estimate_lambda()
+        _, _, pe = G.truncation_length(1e-3)
+    assert np.max(np.abs(s[k] - r)) <= 1e-3
+    assert tau.mean() < 0.2 * pe.mean()
