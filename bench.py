@@ -319,6 +319,49 @@ def run_batch(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_caltau_arm(args, stream):
+    """CalTau with omega eigenpairs on the device (Algorithm 1, Eq. 6-8) on a
+    planted partition of 200,000 nodes (40 communities: 39 eigenvalues near 1),
+    where Eq. 6 with lambda_2 alone asks hundreds of hops: the eigenpairs and
+    CalTau calls timed on the host clock (they synchronise), sc_all_edges with
+    the CalTau lengths by CUDA events after one warm-up; the lengths of Eq. 6
+    reported beside them, not run."""
+    import graphgen as gg
+    import torch
+    from paper_2305_16086_gb300 import Graph
+
+    g = gg.workload("planted_200k")
+    out = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+    with Graph(g.row_ptr, g.col_idx, stream=stream) as G:
+        t0 = time.perf_counter()
+        _, _, rep = G.eigenpairs(omega=args.caltau_omega, allow_unconverged=True)
+        t_eig = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        tau, ell = G.caltau(args.eps)
+        t_ct = (time.perf_counter() - t0) * 1e3
+        kw = dict(eps=args.eps, policy="caltau", precision=args.precision)
+        G.all_edges(out=out, **kw)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, r = G.all_edges(out=out, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        G.estimate_lambda(allow_unconverged=True)
+        ell6, ps6, pe6 = G.truncation_length(args.eps)
+    ps = np.maximum.reduceat(tau, g.row_ptr[:-1].astype(np.int64))
+    return {"workload": "planted partition, 40 communities of 5000 nodes, internal degree 10, external 0.2, seed 6",
+            "n": g.n, "m": g.m, "omega": args.caltau_omega, "pairs_taken": rep["used"],
+            "lambda_rest": rep["lambda_rest"], "eigenpairs_ms": t_eig, "caltau_ms": t_ct,
+            "all_edges_ms": ms, "value": g.m / (ms / 1e3), "unit": UNIT,
+            "value_incl_eigenpairs_and_caltau": g.m / ((ms + t_eig + t_ct) / 1e3),
+            "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m,
+            "mean_length": float(tau.mean()), "longest": int(ell), "source_hops": int(ps.sum()),
+            "eq6": {"mean_length": float(pe6.mean()), "longest": int(ell6), "source_hops": int(ps6.sum()),
+                    "note": "not run: the traversal at these lengths, for comparison"}}
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,6 +383,9 @@ def parse_args(argv=None):
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--caltau-arm", action="store_true",
+                    help="also time CalTau with device eigenpairs (Algorithm 1) on a planted partition, n=200000")
+    ap.add_argument("--caltau-omega", type=int, default=64)
     ap.add_argument("--mode", default="tgt", choices=["tgt", "tgt_plus"],
                     help="tgt: Algorithm 2; tgt_plus: Algorithm 4 (with --policy global, per_edge or fixed)")
     args = ap.parse_args(argv)
@@ -481,6 +527,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(g, rep0["ell_global"], target_s=args.cpu_seconds)
+    caltau_arm = run_caltau_arm(args, stream) if args.caltau_arm else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -505,6 +552,7 @@ def main():
                      "walk_steps": rep0["walk_steps"], "switch_tests": rep0["switch_tests"],
                      "switch_ms": rep0["switch_ms"], "walk_ms": rep0["walk_ms"]}
         if args.mode == "tgt_plus" else None,
+        "caltau": caltau_arm,
         "clocks": clk.summary(), "gpu_launches": int(sum(r["launches"] for r in reports)),
         "foster_mean_abs_error": ((g.n - 1) - rep0["foster_sum"]) / g.m,
     }

@@ -42,6 +42,7 @@ class _FakeGraph:
 
     def __init__(self, row_ptr, col_idx, stream=None, **kw):
         self.n = len(row_ptr) - 1
+        self.nnz = len(col_idx)
 
     def __enter__(self):
         return self
@@ -54,6 +55,16 @@ class _FakeGraph:
 
     def estimate_lambda(self, **kw):
         return {"lambda_star": 0.43, "lambda_plus": 0.43, "lambda_minus": -0.3}
+
+    def eigenpairs(self, omega=128, **kw):
+        return np.zeros(omega), None, {"used": 5, "lambda_rest": 0.6}
+
+    def caltau(self, eps, **kw):
+        self.tau = np.full(self.nnz, 7, dtype=np.int32)
+        return self.tau, 7
+
+    def truncation_length(self, eps, lam=None):
+        return 301, np.full(self.n, 301, dtype=np.int32), np.full(self.nnz, 301, dtype=np.int32)
 
     def all_edges(self, out=None, **kw):
         _FakeGraph.calls.append(kw)
@@ -159,3 +170,14 @@ def test_reference_arm_line(monkeypatch):
             "e2e", "config"} <= set(d)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_caltau_arm_section(fake_cuda, monkeypatch):
+    monkeypatch.setattr(gg, "workload", lambda name, **kw: gg.planted_partition(4, 60, 8.0, 0.3, 1))
+    d = _run(fake_cuda, ["--steps", "1", "--warmup", "3", "--no-e2e", "--no-arms", "--caltau-arm",
+                         "--caltau-omega", "9"])
+    c = d["caltau"]
+    assert c["omega"] == 9 and c["pairs_taken"] == 5 and c["mean_length"] == 7 and c["eq6"]["mean_length"] == 301
+    assert c["source_hops"] == 7 * 240 and c["eq6"]["source_hops"] == 301 * 240 and c["value"] > 0
+    d = _run(fake_cuda, ["--steps", "1", "--warmup", "3", "--no-e2e", "--no-arms"])
+    assert d["caltau"] is None
