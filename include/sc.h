@@ -243,6 +243,22 @@ sc_status sc_caltau(sc_graph *g, double eps, int32_t count, const double *lam, c
  */
 sc_status sc_tridiag_eig(int32_t k, const double *alpha, const double *beta, double *theta, double *Z);
 
+/*
+ * sc_series_meet -- the truncated series S_tau of Eq. 2 per CSR entry by the
+ * meet-in-the-middle form: for each edge (i, j) the column c_0 = e_i/d_i -
+ * e_j/d_j is propagated by P for ceil(tau/2) hops, and the hop-l term is
+ * t_l = sum_x d_x c_a[x] c_b[x], a = floor(l/2), b = l - a (Chapman-Kolmogorov
+ * with reversibility; the deterministic form of the collision view of
+ * Section 2.3). FP64, blocks of 32 edges. It gives what sc_all_edges gives with
+ * the plain estimator at the same lengths, by half the hops per column but one
+ * column per edge instead of per source.
+ *   tau   : host int32[nnz], 0 <= tau <= 2^20, equal in both directions of an edge
+ *   s_out : host double[nnz]
+ * Errors: SC_ERR_INVALID_ARG (null, a length out of range or differing
+ * between the two directions).
+ */
+sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
+
 /* ---- the all-edge computation --------------------------------------------- */
 
 /* truncation policy */

@@ -38,6 +38,7 @@ EXPORTS = [
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
     "sc_batch_all_edges", "sc_selftest_bounded_waits", "sc_eigenpairs", "sc_caltau", "sc_tridiag_eig",
+    "sc_series_meet",
 ]
 OMEGA_MAX = 257
 MLP_PARAMS, MLP_FEATURES = 1313, 6
@@ -173,6 +174,8 @@ def load(path: str = LIB_PATH):
     L.sc_eigenpairs.restype = ctypes.c_int
     L.sc_caltau.argtypes = [vp, f64, i32, f64p, f64p, f64, i32p, i32p]
     L.sc_caltau.restype = ctypes.c_int
+    L.sc_series_meet.argtypes = [vp, i32p, f64p]
+    L.sc_series_meet.restype = ctypes.c_int
     L.sc_tridiag_eig.argtypes = [i32, f64p, f64p, f64p, f64p]
     L.sc_tridiag_eig.restype = ctypes.c_int
     L.sc_selftest_bounded_waits.argtypes = [ctypes.c_uint32]
@@ -292,6 +295,13 @@ class Graph:
                                   ctypes.byref(ell))
         _check(st, "sc_caltau")
         return tau, int(ell.value)
+
+    def series_meet(self, tau):
+        """sc_series_meet: S_tau per CSR entry (host float64[nnz]) at the lengths tau (int32[nnz] or one int)."""
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.int32), (self.nnz,)))
+        out = np.empty(self.nnz, dtype=np.float64)
+        _check(load().sc_series_meet(self._h, _i32p(t), _f64p(out)), "sc_series_meet")
+        return out
 
     def truncation_length(self, eps: float, lam: dict | None = None):
         """(ell_global, per_source int32[n], per_entry int32[nnz]) on the host."""
