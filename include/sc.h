@@ -324,7 +324,12 @@ typedef struct sc_options {
 /* TGT+ switch rules (when to stop the traversal and draw walks) */
 #define SC_SWITCH_COST 0   /* cost: walks once their predicted time (fixed GB300 rates per walk step
                               and per source-hop entry) is below the remaining hops' */
-#define SC_SWITCH_PAPER 1  /* Eq. 14: frontier volume above the sum of walk counts */
+#define SC_SWITCH_PAPER 1  /* Eq. 14: frontier volume above the sum of walk counts, both summed over
+                              the sources of a launch, which switch together */
+#define SC_SWITCH_PER_SOURCE 2  /* Eq. 14 per source, as Algorithm 4's loop is written: after each hop
+                                   a source whose own frontier volume exceeds the sum of its own walk
+                                   counts draws its walks from that hop's column and gathers no later
+                                   hop; the launch continues while any source is still traversing */
 
 /* fills *opts with defaults: eps 1e-3, TGT, FP32, global length, plain estimator, auto B */
 void sc_options_default(sc_options *opts);

@@ -341,7 +341,7 @@ class Graph:
         o.delta = delta
         if gamma is not None:
             o.gamma = gamma
-        o.switch_rule = {"cost": 0, "paper": 1}[switch]
+        o.switch_rule = {"cost": 0, "paper": 1, "per_source": 2}[switch]
         o.bf16_from_hop = bf16_from_hop
         return o
 

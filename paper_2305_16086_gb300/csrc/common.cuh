@@ -194,6 +194,8 @@ struct sc_graph {
     sc::DevBuf<int32_t> tp_eq, tp_ek, tp_chunk_entry, tp_entry_chunk0;
     sc::DevBuf<double> tp_chunk_sum;
     sc::DevBuf<double> tp_srcstat;  // per column: rho_hat, min and max of p over N(s)
+    sc::DevBuf<long long> tp_src_rhs;  // per column: Eq. 14's right side (per-source switch)
+    sc::DevBuf<int32_t> tp_cap_list;   // the sources that switch at a test (per-source switch)
     std::vector<cudaEvent_t> hop_events;  // pairs bracketing timed propagation launches
     ~sc_graph() {
         for (cudaEvent_t e : hop_events) cudaEventDestroy(e);

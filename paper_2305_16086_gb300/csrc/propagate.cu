@@ -22,7 +22,9 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
 void tgtplus_reserve(sc_graph *g, int slices, int B);
 void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, const int32_t *src, const int32_t *h_src,
                    int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
-                   long long *rhs, long long *steps, cudaStream_t s);
+                   long long *rhs, long long *steps, cudaStream_t s, long long *vol_src = nullptr,
+                   long long *rhs_src = nullptr);
+void tgtplus_cap_rows(sc_graph *g, const int32_t *h_list, int count, int32_t cap, int32_t *tau, cudaStream_t s);
 long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32_t *src, const int32_t *h_src,
                         int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s);
 long long tgtplus_last_steps(sc_graph *g);
@@ -741,7 +743,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         // hops 1-2 from the sources alone when X_1 is read by nothing else (no TGT+
         // switch test or walk from X_1, no sparse last hop at 2, one storage type)
         const bool test_at_1 =
-            R.plus && (R.o->switch_rule == SC_SWITCH_PAPER || 1 >= std::max(1, L - kCostRuleHops));
+            R.plus && (R.o->switch_rule != SC_SWITCH_COST || 1 >= std::max(1, L - kCostRuleHops));
         const bool from_mask = !test_at_1 && L >= 3 && prec_at(R, 1) == prec_at(R, 2);
         int ell0 = 2;
         if (from_mask) {
@@ -758,9 +760,59 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         }
         int32_t tt = L;  // hops traversed; TGT+ may switch to walks earlier
         bool last_done = false;
+        // per-source switch (Algorithm 4's loop per source): each source's switch hop, -1 while traversing
+        const bool per_source = R.plus && R.o->switch_rule == SC_SWITCH_PER_SOURCE;
+        std::vector<int32_t> src_tt(per_source ? nsrc : 0, -1), now_list(per_source ? nsrc : 0, -1);
+        std::vector<long long> vol_src(per_source ? nsrc : 0), rhs_src(per_source ? nsrc : 0);
+        int n_active = 0;
+        for (int q = 0; per_source && q < nsrc; ++q) n_active += h_src[first + q] >= 0 ? 1 : 0;
         for (int ell = ell0; ell <= L; ++ell) {
             const bool paper_rule = R.o->switch_rule == SC_SWITCH_PAPER;
-            if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
+            if (per_source) {
+                // Eq. 14 per source after hop ell-1: each source whose frontier volume exceeds the sum
+                // of its own walk counts walks from X_{ell-1} now, and its entries gather no hop after
+                // ell-1 (their tau is capped there once the walk kernel has read it)
+                long long lhs = 0, rhs = 0, steps = 0;
+                const double t0 = wall_ms();
+                tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc,
+                              g->tau_entry.get(), ell - 1, R.gamma, R.o->eps, R.log2md, &lhs, &rhs, &steps, s,
+                              vol_src.data(), rhs_src.data());
+                R.switch_ms += wall_ms() - t0;
+                ++R.switch_tests;
+                R.launches += 4;
+                int nnow = 0;
+                for (int q = 0; q < nsrc; ++q) {
+                    now_list[q] = -1;
+                    const int32_t v = h_src[first + q];
+                    if (v >= 0 && src_tt[q] < 0 && vol_src[q] > rhs_src[q]) {
+                        now_list[q] = v;
+                        src_tt[q] = ell - 1;
+                        ++nnow;
+                    }
+                }
+                if (nnow > 0) {
+                    const double tw = wall_ms();
+                    SC_CUDA(cudaEventRecord(ev_w0, s));
+                    const long long pairs = tgtplus_walks(g, prec_at(R, ell - 1), B, xa, src, now_list.data(), nsrc,
+                                                          g->tau_entry.get(), ell - 1, R.o->seed, g->acc_g.get(), s);
+                    SC_CUDA(cudaEventRecord(ev_w1, s));
+                    SC_CUDA(cudaEventSynchronize(ev_w1));
+                    R.walk_ms += wall_ms() - tw;
+                    R.launches += 3;
+                    R.walks += pairs;
+                    float wms = 0.f;
+                    SC_CUDA(cudaEventElapsedTime(&wms, ev_w0, ev_w1));
+                    R.walk_steps += tgtplus_last_steps(g);
+                    R.walk_device_ms += wms;
+                    tgtplus_cap_rows(g, now_list.data(), nsrc, ell - 1, g->tau_entry.get(), s);
+                    R.launches += 1;
+                    n_active -= nnow;
+                }
+                if (n_active == 0) {
+                    tt = ell - 1;
+                    break;
+                }
+            } else if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
                 // switch test after hop ell-1. Paper rule (Eq. 14): frontier volume against the
                 // sum of walk counts. Cost rule: predicted walk time against the time of the
                 // L - (ell-1) hops the walks would replace.
@@ -813,7 +865,14 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         }
         R.hops += tt;
         R.source_hops += static_cast<int64_t>(tt) * nsrc;
-        if (R.plus) {
+        if (per_source) {
+            for (int q = 0; q < nsrc; ++q) {
+                if (h_src[first + q] < 0) continue;
+                const int32_t t_q = src_tt[q] >= 0 ? src_tt[q] : tt;
+                R.tt_min = std::min(R.tt_min, t_q);
+                R.tt_max = std::max(R.tt_max, t_q);
+            }
+        } else if (R.plus) {
             R.tt_min = std::min(R.tt_min, tt);
             R.tt_max = std::max(R.tt_max, tt);
             if (tt < L) {
@@ -1100,6 +1159,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ takes the plain estimator, no tail records and an Eq. 6 length");
     const int gamma = o.gamma < 0 ? 10 : o.gamma;
     if (plus && gamma > kGammaMax) SC_FAIL(SC_ERR_UNSUPPORTED, "gamma %d above %d", gamma, kGammaMax);
+    if (o.switch_rule < SC_SWITCH_COST || o.switch_rule > SC_SWITCH_PER_SOURCE)
+        SC_FAIL(SC_ERR_INVALID_ARG, "switch rule %d", o.switch_rule);
     if (o.ell_policy < SC_ELL_GLOBAL || o.ell_policy > SC_ELL_CALTAU) SC_FAIL(SC_ERR_INVALID_ARG, "length policy %d", o.ell_policy);
     const bool caltau = o.ell_policy == SC_ELL_CALTAU;
     if (caltau && plus) SC_FAIL(SC_ERR_UNSUPPORTED, "the CalTau lengths serve TGT");

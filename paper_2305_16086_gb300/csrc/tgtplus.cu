@@ -93,16 +93,19 @@ void tgtplus_reserve(sc_graph *g, int slices, int B) {
     g->tp_cmax.reserve(cols);
     g->tp_cvol.reserve(cols);
     g->tp_srcstat.reserve(3 * cols);
+    g->tp_src_rhs.reserve(cols);
+    g->tp_cap_list.reserve(cols);
     g->tp_walks.reserve(g->nnz);
     g->tp_counters.reserve(4);
 }
 
 // Eq. 14 after hop `ell` for the launch's sources: returns the two sides
 // (frontier volume, sum of walk counts); the per-entry walk counts for
-// L = tau_k - ell stay in g->tp_walks for the walk kernel.
+// L = tau_k - ell stay in g->tp_walks for the walk kernel. vol_src / rhs_src
+// (host, nsrc each; may be null): the two sides per source.
 void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, const int32_t *src, const int32_t *h_src,
                    int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
-                   long long *rhs, long long *steps, cudaStream_t s) {
+                   long long *rhs, long long *steps, cudaStream_t s, long long *vol_src, long long *rhs_src) {
     SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, 4 * sizeof(long long), s));
     int max_deg = 0;
     for (int q = 0; q < nsrc; ++q)
@@ -113,7 +116,14 @@ void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, cons
     long long h_cnt[3] = {0, 0, 0};
     SC_CUDA(cudaMemcpyAsync(vol.data(), g->tp_cvol.get(), vol.size() * sizeof(long long), cudaMemcpyDeviceToHost, s));
     SC_CUDA(cudaMemcpyAsync(h_cnt, g->tp_counters.get(), 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    if (rhs_src) {
+        k_walks_per_source<<<nsrc, 32, 0, s>>>(g->row_ptr.get(), src, nsrc, g->tp_walks.get(), g->tp_src_rhs.get());
+        SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(rhs_src, g->tp_src_rhs.get(), nsrc * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    }
     SC_CUDA(cudaStreamSynchronize(s));
+    if (vol_src)
+        for (int q = 0; q < nsrc; ++q) vol_src[q] = h_src[q] >= 0 ? vol[q] : 0;
     long long h_lhs = 0;
     for (int q = 0; q < nsrc; ++q)
         if (h_src[q] >= 0) h_lhs += vol[q];
@@ -185,5 +195,13 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
 }
 
 long long tgtplus_last_steps(sc_graph *g) { return g->last_walk_steps; }
+
+// Caps tau at `cap` on the rows of the listed nodes (host list of count, -1 = skip).
+void tgtplus_cap_rows(sc_graph *g, const int32_t *h_list, int count, int32_t cap, int32_t *tau, cudaStream_t s) {
+    SC_CUDA(cudaMemcpyAsync(g->tp_cap_list.get(), h_list, count * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_cap_rows<<<count, 128, 0, s>>>(g->row_ptr.get(), g->tp_cap_list.get(), count, cap, tau);
+    SC_LAUNCH_CHECK();
+    SC_CUDA(cudaStreamSynchronize(s));  // h_list may be reused by the caller
+}
 
 }  // namespace sc

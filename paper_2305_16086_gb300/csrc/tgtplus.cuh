@@ -427,6 +427,35 @@ static __global__ void k_walk_finish(const int32_t *__restrict__ entry_k, const 
 }
 
 // packs the walk counts of the planned entries
+// Eq. 14's right side for one source: out[q] = the sum of the walk counts of
+// source q's entries (one warp per source; 0 for an empty slot)
+static __global__ void k_walks_per_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ src,
+                                          int32_t nsrc, const long long *__restrict__ walk_count,
+                                          long long *__restrict__ out) {
+    const int32_t q = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (q >= nsrc) return;
+    const int32_t s = src[q];
+    long long acc = 0;
+    if (s >= 0)
+        for (int32_t k = row_ptr[s] + lane; k < row_ptr[s + 1]; k += 32) acc += walk_count[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[q] = acc;
+}
+
+// tau[k] = min(tau[k], cap) over the rows of the listed nodes (entries < 0
+// skipped): a source that switched to walks at hop cap gathers no later hop
+static __global__ void k_cap_rows(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ list,
+                                  int32_t count, int32_t cap, int32_t *__restrict__ tau) {
+    const int32_t q = blockIdx.x;
+    if (q >= count) return;
+    const int32_t v = list[q];
+    if (v < 0) return;
+    for (int32_t k = row_ptr[v] + static_cast<int32_t>(threadIdx.x); k < row_ptr[v + 1]; k += blockDim.x)
+        tau[k] = min(tau[k], cap);
+}
+
 static __global__ void k_pack_counts(const int32_t *__restrict__ entry_k, int32_t nentries,
                               const long long *__restrict__ walk_count, long long *__restrict__ out) {
     const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;

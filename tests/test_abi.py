@@ -110,7 +110,7 @@ int main(void) {
   P(SC_PTRS_HOST) P(SC_PTRS_DEVICE) P(SC_FLAG_REJECT_BIPARTITE)
   P(SC_ELL_GLOBAL) P(SC_ELL_PER_EDGE) P(SC_ELL_FIXED) P(SC_ELL_LEARNED) P(SC_ELL_CALTAU) P(SC_OMEGA_MAX)
   P(SC_PREC_FP64) P(SC_PREC_FP32) P(SC_PREC_BF16) P(SC_EST_PLAIN) P(SC_EST_END_CORRECTED)
-  P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER)
+  P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER) P(SC_SWITCH_PER_SOURCE)
   P(SC_OUT_DEVICE) P(SC_OPT_RECORD_TAIL) P(SC_OPT_TIME_KERNELS) P(SC_OPT_WINDOWS_OFF) P(SC_OPT_WINDOWS_FORCE)
   P(SC_MLP_PARAMS) P(SC_MLP_FEATURES) P(SC_MLP_MODEL_FLOATS)
   return 0;
@@ -135,7 +135,8 @@ def test_header_constants_match_binding(tmp_path):
                           (binding.MODE, "SC_MODE_")):
         assert {k.upper(): v for k, v in table.items()} == {k[len(prefix):]: v for k, v in c.items()
                                                             if k.startswith(prefix)}, prefix
-    assert (c["SC_SWITCH_COST"], c["SC_SWITCH_PAPER"]) == (0, 1)  # the binding's switch="cost" / "paper"
+    assert (c["SC_SWITCH_COST"], c["SC_SWITCH_PAPER"], c["SC_SWITCH_PER_SOURCE"]) == (0, 1, 2)  # switch="cost" / "paper" / "per_source"
+    assert binding.Graph.options(switch="per_source").switch_rule == 2
     for name in ("SC_OUT_DEVICE", "SC_OPT_RECORD_TAIL", "SC_OPT_TIME_KERNELS", "SC_OPT_WINDOWS_OFF",
                  "SC_OPT_WINDOWS_FORCE"):
         assert c[name] == getattr(binding, name), name
