@@ -165,8 +165,30 @@ def cpu_baseline(g, ell: int, target_s: float = 10.0):
     per_source = elapsed / done
     value = g.m / (per_source * g.n)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{done} of {g.n} sources (Algorithm 2 in FP64 C, length {ell}); "
-                      f"full-job rate = m / (n * seconds per source)", "seconds": round(elapsed, 2)}
+            "sample": f"{done} sources drawn from {g.n} (Algorithm 2 in FP64 C, length {ell}); "
+                      f"full-job rate = m / (n * seconds per source)", "seconds": round(elapsed, 2),
+            "sources_timed": done}
+
+
+def exact_check(g, s_hat, edges: int, seed: int = 2024):
+    """The exact resistance (oracle O1: Jacobi-preconditioned FP64 CG on the
+    Laplacian, one solve per edge) on `edges` uniformly sampled edges, timed on
+    the host cores, and the error of the GPU result s_hat (one value per CSR
+    entry) there: max and mean |s_hat - r|. Part of the CPU baseline leg."""
+    from oracle import _native, exact
+
+    e = g.edges()
+    rng = np.random.default_rng(seed)
+    pick = e[rng.choice(e.shape[0], size=min(edges, e.shape[0]), replace=False)]
+    k = exact.entry_of_edges(g.n, g.row_ptr, g.col_idx, pick)
+    t0 = time.perf_counter()
+    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, pick)
+    dt = time.perf_counter() - t0
+    err = np.abs(np.asarray(s_hat)[k] - r)
+    return {"sampled_edges": int(pick.shape[0]), "max_abs_err": float(err.max()), "mean_abs_err": float(err.mean()),
+            "oracle": "FP64 Jacobi-preconditioned CG per sampled edge, relative residual 1e-12",
+            "oracle_seconds": round(dt, 2), "oracle_edges_per_s": pick.shape[0] / dt,
+            "oracle_cores": _native.default_threads(), "sample_seed": seed}
 
 
 def train_model(eps, stream):
@@ -177,7 +199,7 @@ def train_model(eps, stream):
 
     tg = gg.barabasi_albert(50_000, 10, 101)
     with Graph(tg.row_ptr, tg.col_idx, stream=stream) as Gt:
-        Gt.estimate_lambda(allow_unconverged=True)
+        Gt.estimate_lambda()
         init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
         model, _ = binding.mlp_train([Gt], init, epochs=400, lr=1e-2, eps=eps, precision="fp32")
     return model
@@ -238,7 +260,9 @@ def timed_passes(run_pass, warm: int, timed: int, sync, barrier):
 
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores: each step a bounded sample of the workload."""
+    """The oracle on the host cores: each step a bounded sample of the workload
+    (the sources Algorithm 2 runs are drawn at random; the sample is timed and
+    its rate scaled to the unit, edges per second of the whole graph)."""
     if rank != 0:
         return
     import graphgen as gg
@@ -253,12 +277,20 @@ def run_reference(args, world, rank):
         if i >= args.warmup:
             vals.append(r)
     value = statistics.mean(v["value"] for v in vals)
-    ms = g.m / value * 1e3
+    ms = 1e3 * statistics.mean(v["seconds"] for v in vals)
+    sources = statistics.mean(v["sources_timed"] for v in vals)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload]["desc"], "eps": args.eps, "ell_global": ell,
-                      "lambda_star": ls},
+           "step": f"one step = Algorithm 2 for about {sources:.0f} randomly drawn sources of the {g.n} "
+                   f"(a bounded sample); value = the sample's rate in edges of the whole graph per second",
+           "full_job_ms_extrapolated": g.m / value * 1e3,
+           "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "m": g.m, "eps": args.eps,
+                      "mode": "tgt", "policy": "global", "estimator": "plain", "windowed": False,
+                      "precision": "fp64 (the oracle's Algorithm 2 in C)",
+                      "batching": "OpenMP over sources", "ell_global": ell, "lambda_star": ls,
+                      "parallelism": f"{vals[0]['cores']} host threads",
+                      "note": "the plain global-length FP64 traversal, the comparison the metric names"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -380,6 +412,8 @@ def parse_args(argv=None):
     ap.add_argument("--rows-split", type=int, default=0)
     ap.add_argument("--heavy-threshold", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--check-edges", type=int, default=10000,
+                    help="edges whose exact value the CPU baseline leg computes (CG) to report the error")
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -425,7 +459,9 @@ def main():
                   estimator=args.estimator, mode=args.mode)
 
     G = Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), stream=stream)
-    lam = G.estimate_lambda(allow_unconverged=True)
+    # the bound of Eq. 6 needs a converged lambda (its residual is the safety margin): an
+    # unconverged estimate raises here and no value is reported
+    lam = G.estimate_lambda()
     model = None
     if args.policy == "learned":
         model = train_model(args.eps, stream)
@@ -485,7 +521,7 @@ def main():
         def e2e_pass(mark):
             with Graph(rp_h, ci_h, stream=stream) as Gh:
                 mark("create_validate")
-                Gh.estimate_lambda(allow_unconverged=True)
+                Gh.estimate_lambda()
                 mark("lanczos")
                 if model is not None:
                     binding.mlp_load(Gh, model)
@@ -525,8 +561,11 @@ def main():
             pg.destroy_process_group()
         return
     cpu = None
+    accuracy = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(g, rep0["ell_global"], target_s=args.cpu_seconds)
+        if args.check_edges > 0:
+            accuracy = exact_check(g, out.cpu().numpy(), args.check_edges)
     caltau_arm = run_caltau_arm(args, stream) if args.caltau_arm else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -540,6 +579,8 @@ def main():
                    "batching": f"{rep0['slices']} block(s) of {rep0['block_width']} sources per launch, "
                                f"{rep0['blocks']} blocks",
                    "ell_global": rep0["ell_global"], "lambda_star": lam["lambda_star"],
+                   "lambda_converged": bool(lam["converged"]), "lanczos_iterations": lam["iterations"],
+                   "lambda_residuals": [lam["residual_plus"], lam["residual_minus"]],
                    "block_width": rep0["block_width"], "rows_split": rep0["rows_split"],
                    "slices": rep0["slices"], "l2": "working set > L2 and a 512 MB write between steps",
                    "parallelism": f"replicas x{world}"},
@@ -555,6 +596,9 @@ def main():
         "caltau": caltau_arm,
         "clocks": clk.summary(), "gpu_launches": int(sum(r["launches"] for r in reports)),
         "foster_mean_abs_error": ((g.n - 1) - rep0["foster_sum"]) / g.m,
+        "max_abs_err": accuracy["max_abs_err"] if accuracy else None,
+        "mean_abs_err": accuracy["mean_abs_err"] if accuracy else None,
+        "accuracy": accuracy,
     }
     print(json.dumps(line), flush=True)
     if pg is not None:

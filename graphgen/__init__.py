@@ -90,7 +90,11 @@ def from_edges(n: int, u, v, name: str = "", meta: dict | None = None) -> CSRGra
     u, v = u[keep], v[keep]
     rows = np.concatenate([u, v])
     cols = np.concatenate([v, u])
-    key = np.unique(rows * np.int64(n) + cols)
+    # sorted distinct keys (sort + adjacent comparison: the result np.unique
+    # gives, without its hash-based path, which is slow on large inputs)
+    key = np.sort(rows * np.int64(n) + cols, kind="stable")
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     rows = key // n
     cols = key % n
     counts = np.bincount(rows, minlength=n)

@@ -526,9 +526,10 @@ sc_status sc_mlp_loss_grad(const float *model, const float *features, const floa
  * the one array and it keeps the previous call's contents; each call clears
  * what must start at zero itself. Calls that overlap on the GPU (two streams
  * or two host threads at once) race on the array: serialise them. The first
- * call on each device looks up the array's device address (cudaGetSymbolAddress
- * with that device current) and caches it; make that first call before any
- * stream capture.
+ * call in each CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress with that context's device current) and caches it
+ * under the context's unique id; make that first call before any stream
+ * capture. After a device reset the next call looks the address up again.
  */
 sc_status sc_all_edges_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                                int32_t ell, double *s_hat, void *stream);

@@ -28,8 +28,10 @@ def build(force: bool = False) -> str:
 
 
 def compile_to(src: str, out: str) -> None:
-    """gcc -O2 with OpenMP into the shared library ``out``."""
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", out, src, "-lm"]
+    """gcc -O2 with OpenMP into the shared library ``out``; no contraction of
+    a * b + c into fused multiply-adds, so every machine rounds each operation
+    as written."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
 
 
@@ -44,6 +46,8 @@ def bind(path: str):
     L.oracle_cg.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, i32p,
                             ctypes.c_double, ctypes.c_int32, f64p, i32p, ctypes.c_int32]
     L.oracle_cg.restype = ctypes.c_int
+    L.oracle_cg_block.argtypes = L.oracle_cg.argtypes
+    L.oracle_cg_block.restype = ctypes.c_int
     L.oracle_series_terms.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p,
                                       ctypes.POINTER(ctypes.c_int64), f64p, ctypes.c_int32]
     L.oracle_series_terms.restype = ctypes.c_int

@@ -396,16 +396,51 @@ def batch_all_edges(graphs, ell_per_graph=None, outs=None, **kw):
     return res, [r.as_dict() for r in reps]
 
 
+def _noalloc_args(row_ptr, col_idx, out):
+    """Checks the tensors sc_all_edges_noalloc receives as raw pointers, since the
+    library trusts n, nnz and the output length: 1-D contiguous int32 CSR arrays
+    and a float64 output of at least nnz entries, all on one CUDA device.
+    Raises ValueError / TypeError before anything reaches the library."""
+    torch = _torch()
+    for name, t in (("row_ptr", row_ptr), ("col_idx", col_idx), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dim() != 1:
+            raise ValueError(f"{name} must be 1-D")
+    if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+        raise TypeError("row_ptr and col_idx must be int32")
+    if out.dtype != torch.float64:
+        raise TypeError("out must be float64")
+    for name, t in (("row_ptr", row_ptr), ("col_idx", col_idx), ("out", out)):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    n = int(row_ptr.numel()) - 1
+    nnz = int(col_idx.numel())
+    if n < 2 or nnz < 2:
+        raise ValueError("need row_ptr with at least 3 entries (n >= 2) and at least 2 CSR entries")
+    if out.numel() < nnz:
+        raise ValueError(f"out holds {out.numel()} values, fewer than nnz = {nnz}")
+    for name, t in (("row_ptr", row_ptr), ("col_idx", col_idx), ("out", out)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    if not (row_ptr.device == col_idx.device == out.device):
+        raise ValueError("row_ptr, col_idx and out must be on the same CUDA device")
+    return n, nnz
+
+
 def all_edges_noalloc(row_ptr, col_idx, ell: int, out, stream=None):
     """sc_all_edges_noalloc on torch CUDA tensors (int32 CSR, float64 output of
     nnz entries): the traversal for callers that cannot allocate device memory.
-    Works in the library's fixed 64 MiB device array; see include/sc.h."""
-    n = int(row_ptr.shape[0]) - 1
-    nnz = int(col_idx.shape[0])
-    _check(load().sc_all_edges_noalloc(n, nnz, ctypes.c_void_p(row_ptr.data_ptr()),
-                                       ctypes.c_void_p(col_idx.data_ptr()), int(ell),
-                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
-           "sc_all_edges_noalloc")
+    Works in the library's fixed 64 MiB device array; see include/sc.h.
+    The tensors are checked here (dtype, contiguity, sizes, one device) and the
+    call runs with their device current."""
+    n, nnz = _noalloc_args(row_ptr, col_idx, out)
+    torch = _torch()
+    with torch.cuda.device(row_ptr.device):
+        _check(load().sc_all_edges_noalloc(n, nnz, ctypes.c_void_p(row_ptr.data_ptr()),
+                                           ctypes.c_void_p(col_idx.data_ptr()), int(ell),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "sc_all_edges_noalloc")
     return out
 
 

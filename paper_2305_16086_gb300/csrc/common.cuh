@@ -161,7 +161,6 @@ struct sc_graph {
     // autotuned (block width, lane split) per request key, and its measured ms per source-hop
     std::map<long long, std::pair<int, int>> tuned;
     std::map<long long, double> tuned_cost;
-    long long last_walk_steps = 0;
 
     // learned length: features (n x 6) and the loaded model
     sc::DevBuf<float> features, mlp;

@@ -18,12 +18,16 @@
 // issued) race on it and must be serialised by the caller.
 //
 // Host code cannot use the array's name as a device address (it is a host
-// stand-in), so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current and caches it; that first
-// call should be made before any stream capture begins.
+// stand-in), so the first call in each CUDA context looks the address up with
+// cudaGetSymbolAddress while that context's device is current and caches it
+// under the context's unique id; that first call should be made before any
+// stream capture begins. A device reset creates a new context (a new id), so
+// the address is looked up again instead of reusing a stale one.
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
+
+#include <cuda.h>
 
 #include "propagate.cuh"
 
@@ -33,16 +37,45 @@ static_assert(SC_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must keep 256-b
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SC_NOALLOC_SCRATCH_BYTES];
 
 static std::mutex g_noalloc_mu;
-static std::unordered_map<int, unsigned char *> g_noalloc_addr;
+static std::unordered_map<unsigned long long, unsigned char *> g_noalloc_addr;
+
+// unique id of the current context (cuCtxGetCurrent + cuCtxGetId, reached
+// through the runtime's driver entry points) on `device`
+static unsigned long long current_context_id(int device) {
+    using CtxGetCurrent = CUresult (*)(CUcontext *);
+    using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        SC_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa));
+        SC_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb));
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            SC_FAIL(SC_ERR_CUDA, "cuCtxGetCurrent / cuCtxGetId unavailable");
+        get_current = reinterpret_cast<CtxGetCurrent>(a);
+        get_id = reinterpret_cast<CtxGetId>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) SC_FAIL(SC_ERR_CUDA, "cuCtxGetCurrent failed");
+    if (!ctx) {  // no context bound to this thread yet: the runtime's primary context of the device
+        SC_CUDA(cudaSetDevice(device));
+        if (get_current(&ctx) != CUDA_SUCCESS || !ctx) SC_FAIL(SC_ERR_CUDA, "no CUDA context on device %d", device);
+    }
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) SC_FAIL(SC_ERR_CUDA, "cuCtxGetId failed");
+    return id;
+}
 
 static unsigned char *noalloc_scratch_address(int device) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    auto it = g_noalloc_addr.find(device);
+    const unsigned long long ctx = current_context_id(device);
+    auto it = g_noalloc_addr.find(ctx);
     if (it != g_noalloc_addr.end()) return it->second;
     void *ptr = nullptr;
     SC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     if (!ptr) SC_FAIL(SC_ERR_CUDA, "cudaGetSymbolAddress returned a null scratch address");
-    g_noalloc_addr[device] = static_cast<unsigned char *>(ptr);
+    g_noalloc_addr[ctx] = static_cast<unsigned char *>(ptr);
     return static_cast<unsigned char *>(ptr);
 }
 

@@ -26,8 +26,8 @@ void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, cons
                    long long *rhs_src = nullptr);
 void tgtplus_cap_rows(sc_graph *g, const int32_t *h_list, int count, int32_t cap, int32_t *tau, cudaStream_t s);
 long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32_t *src, const int32_t *h_src,
-                        int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s);
-long long tgtplus_last_steps(sc_graph *g);
+                        int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s,
+                        long long *steps_out);
 constexpr int kCostRuleHops = 4;  // the cost rule tests the last hops only
 // TGT+ cost rule rates measured on GB300: a hop costs about this much per
 // source and CSR entry (BA-200k, FP32 blocks: 1.1 us per source over 4.0M
@@ -793,8 +793,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 if (nnow > 0) {
                     const double tw = wall_ms();
                     SC_CUDA(cudaEventRecord(ev_w0, s));
+                    long long wsteps = 0;
                     const long long pairs = tgtplus_walks(g, prec_at(R, ell - 1), B, xa, src, now_list.data(), nsrc,
-                                                          g->tau_entry.get(), ell - 1, R.o->seed, g->acc_g.get(), s);
+                                                          g->tau_entry.get(), ell - 1, R.o->seed, g->acc_g.get(), s,
+                                                          &wsteps);
                     SC_CUDA(cudaEventRecord(ev_w1, s));
                     SC_CUDA(cudaEventSynchronize(ev_w1));
                     R.walk_ms += wall_ms() - tw;
@@ -802,7 +804,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                     R.walks += pairs;
                     float wms = 0.f;
                     SC_CUDA(cudaEventElapsedTime(&wms, ev_w0, ev_w1));
-                    R.walk_steps += tgtplus_last_steps(g);
+                    R.walk_steps += wsteps;
                     R.walk_device_ms += wms;
                     tgtplus_cap_rows(g, now_list.data(), nsrc, ell - 1, g->tau_entry.get(), s);
                     R.launches += 1;
@@ -879,8 +881,9 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 // Algorithm 4's walk phase: walk tails from X_tt with the counts of the last check
                 const double t0 = wall_ms();
                 SC_CUDA(cudaEventRecord(ev_w0, s));
+                long long wsteps = 0;
                 const long long pairs = tgtplus_walks(g, prec_at(R, tt), B, xa, src, h_src.data() + first, nsrc,
-                                                      g->tau_entry.get(), tt, R.o->seed, g->acc_g.get(), s);
+                                                      g->tau_entry.get(), tt, R.o->seed, g->acc_g.get(), s, &wsteps);
                 SC_CUDA(cudaEventRecord(ev_w1, s));
                 SC_CUDA(cudaEventSynchronize(ev_w1));
                 R.walk_ms += wall_ms() - t0;
@@ -888,7 +891,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 R.walks += pairs;
                 float wms = 0.f;
                 SC_CUDA(cudaEventElapsedTime(&wms, ev_w0, ev_w1));
-                R.walk_steps += tgtplus_last_steps(g);
+                R.walk_steps += wsteps;
                 R.walk_device_ms += wms;
             }
         }

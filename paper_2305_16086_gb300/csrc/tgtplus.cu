@@ -130,15 +130,17 @@ void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, cons
     *lhs = h_lhs;
     *rhs = h_cnt[0];
     *steps = h_cnt[2];
-    g->last_walk_steps = h_cnt[2];
 }
 
 // Algorithm 4's walk phase for the launch's sources: the entries' walk pairs are cut
 // into chunks of kWalkChunk (planned on the host from the packed counts), one
 // warp per chunk, and each entry adds its chunk sums in chunk order.
-// Returns the number of walk pairs drawn.
+// Returns the number of walk pairs drawn; *steps_out (nullable) receives their
+// walk steps, 2 R (tau_k - tt) summed over the planned entries.
 long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32_t *src, const int32_t *h_src,
-                        int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s) {
+                        int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s,
+                        long long *steps_out) {
+    if (steps_out) *steps_out = 0;
     std::vector<int32_t> eq, ek;
     for (int q = 0; q < nsrc; ++q) {
         const int32_t v = h_src[q];
@@ -152,14 +154,18 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
     if (ne == 0) return 0;
     g->tp_eq.reserve(ne);
     g->tp_ek.reserve(ne);
-    g->tp_packed.reserve(ne);
+    g->tp_packed.reserve(2 * static_cast<size_t>(ne));
     SC_CUDA(cudaMemcpyAsync(g->tp_eq.get(), eq.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemcpyAsync(g->tp_ek.get(), ek.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    k_pack_counts<<<ceil_div(ne, 256), 256, 0, s>>>(g->tp_ek.get(), ne, g->tp_walks.get(), g->tp_packed.get());
+    k_pack_counts<<<ceil_div(ne, 256), 256, 0, s>>>(g->tp_ek.get(), ne, g->tp_walks.get(), tau, tt,
+                                                    g->tp_packed.get());
     SC_LAUNCH_CHECK();
-    std::vector<long long> R(ne);
-    SC_CUDA(cudaMemcpyAsync(R.data(), g->tp_packed.get(), ne * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    std::vector<long long> R(2 * static_cast<size_t>(ne));
+    SC_CUDA(cudaMemcpyAsync(R.data(), g->tp_packed.get(), 2 * static_cast<size_t>(ne) * sizeof(long long),
+                            cudaMemcpyDeviceToHost, s));
     SC_CUDA(cudaStreamSynchronize(s));
+    if (steps_out)
+        for (int32_t e = 0; e < ne; ++e) *steps_out += R[ne + e];
     std::vector<int32_t> chunk_entry, entry_chunk0(ne + 1);
     std::vector<long long> chunk_w0;
     long long pairs = 0;
@@ -193,8 +199,6 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
     SC_CUDA(cudaStreamSynchronize(s));
     return pairs;
 }
-
-long long tgtplus_last_steps(sc_graph *g) { return g->last_walk_steps; }
 
 // Caps tau at `cap` on the rows of the listed nodes (host list of count, -1 = skip).
 void tgtplus_cap_rows(sc_graph *g, const int32_t *h_list, int count, int32_t cap, int32_t *tau, cudaStream_t s) {

@@ -426,7 +426,6 @@ static __global__ void k_walk_finish(const int32_t *__restrict__ entry_k, const 
     g[k] += t / static_cast<double>(R);
 }
 
-// packs the walk counts of the planned entries
 // Eq. 14's right side for one source: out[q] = the sum of the walk counts of
 // source q's entries (one warp per source; 0 for an empty slot)
 static __global__ void k_walks_per_source(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ src,
@@ -456,10 +455,17 @@ static __global__ void k_cap_rows(const int32_t *__restrict__ row_ptr, const int
         tau[k] = min(tau[k], cap);
 }
 
+// out[e] = R of planned entry e; out[nentries + e] = its walk steps 2 R (tau_k - tt)
 static __global__ void k_pack_counts(const int32_t *__restrict__ entry_k, int32_t nentries,
-                              const long long *__restrict__ walk_count, long long *__restrict__ out) {
+                                     const long long *__restrict__ walk_count, const int32_t *__restrict__ tau,
+                                     int32_t tt, long long *__restrict__ out) {
     const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nentries) out[e] = walk_count[entry_k[e]];
+    if (e >= nentries) return;
+    const int32_t k = entry_k[e];
+    const long long R = walk_count[k];
+    const int32_t L = tau[k] - tt;
+    out[e] = R;
+    out[nentries + e] = (R > 0 && L > 0) ? 2ll * R * static_cast<long long>(L) : 0ll;
 }
 
 }  // namespace sc

@@ -54,7 +54,8 @@ class _FakeGraph:
         pass
 
     def estimate_lambda(self, **kw):
-        return {"lambda_star": 0.43, "lambda_plus": 0.43, "lambda_minus": -0.3}
+        return {"lambda_star": 0.43, "lambda_plus": 0.43, "lambda_minus": -0.3, "converged": 1, "iterations": 40,
+                "residual_plus": 1e-5, "residual_minus": 1e-5}
 
     def eigenpairs(self, omega=128, **kw):
         return np.zeros(omega), None, {"used": 5, "lambda_rest": 0.6}
@@ -146,6 +147,10 @@ def test_default_line_has_every_contract_key(fake_cuda):
     assert d["value"] == pytest.approx(fake_cuda.replica_value(1, gg.barabasi_albert(300, 3, 1).m, d["ms_per_step"]))
     assert d["config"]["mode"] == "tgt" and d["tgt_plus"] is None and d["learned"] is not None
     assert d["gpu_launches"] == 2 * 12
+    # the CPU baseline leg's exact check (real oracle CG on the stand-in graph; the fake s_hat is arbitrary)
+    assert d["accuracy"]["sampled_edges"] == gg.barabasi_albert(300, 3, 1).m
+    assert d["max_abs_err"] == d["accuracy"]["max_abs_err"] and d["mean_abs_err"] <= d["max_abs_err"]
+    assert d["config"]["lambda_converged"] is True
     json.dumps(d)
 
 
@@ -170,6 +175,11 @@ def test_reference_arm_line(monkeypatch):
             "e2e", "config"} <= set(d)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # ms_per_step is the measured sample time; the full-job extrapolation is a key of its own
+    assert d["ms_per_step"] > 0 and d["full_job_ms_extrapolated"] > 0
+    g = gg.barabasi_albert(300, 3, 1)
+    assert {"workload", "n", "m", "eps", "mode", "policy", "estimator", "precision", "ell_global"} <= set(d["config"])
+    assert (d["config"]["n"], d["config"]["m"]) == (g.n, g.m)
 
 
 def test_caltau_arm_section(fake_cuda, monkeypatch):

@@ -149,3 +149,29 @@ def test_cg_and_sparse_lu_match_dense(maker):
     a, b, c = 0, g.n // 2, g.n - 1
     rab, rbc, rac = exact.exact_cg(g.n, g.row_ptr, g.col_idx, [(a, b), (b, c), (a, c)])
     assert rac <= rab + rbc + 1e-12
+
+
+@pytest.mark.parametrize("g", [gg.barabasi_albert(3000, 4, 9), gg.perturbed_grid(30, 41, 0.05, 3),
+                               gg.rmat(12)], ids=lambda g: g.name)
+def test_blocked_cg_matches_dense_and_single_solves(g):
+    """The blocked CG (eight solves side by side per thread) against the dense
+    grounded-Laplacian values to 1e-10, and against one solve per pair bit for
+    bit, on pair counts that leave a partial group of eight."""
+    rng = np.random.default_rng(1)
+    e = g.edges()
+    pick = e[rng.choice(e.shape[0], size=29, replace=False)]
+    blocked, it_b = exact.exact_cg(g.n, g.row_ptr, g.col_idx, pick, blocked=True, return_iters=True)
+    single, it_s = exact.exact_cg(g.n, g.row_ptr, g.col_idx, pick, blocked=False, return_iters=True)
+    dense = exact.exact_dense(g.n, g.row_ptr, g.col_idx)[exact.entry_of_edges(g.n, g.row_ptr, g.col_idx, pick)]
+    assert np.max(np.abs(blocked - dense)) < 1e-10
+    assert np.array_equal(blocked, single) and np.array_equal(it_b, it_s)
+
+
+def test_sparse_lu_worker_processes_give_the_single_process_values():
+    g = gg.perturbed_grid(20, 23, 0.05, 4)
+    rng = np.random.default_rng(2)
+    e = g.edges()
+    pick = e[rng.choice(e.shape[0], size=37, replace=False)]
+    one = exact.exact_sparse_lu(g.n, g.row_ptr, g.col_idx, pick)
+    two = exact.exact_sparse_lu(g.n, g.row_ptr, g.col_idx, pick, processes=3)
+    assert np.array_equal(one, two)

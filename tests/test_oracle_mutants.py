@@ -72,6 +72,8 @@ EXACT = [
     ("bridges", te.test_bridges_are_one),
     ("Foster", lambda: te.test_foster_random(0)),
     ("CG and LU vs dense", lambda: te.test_cg_and_sparse_lu_match_dense(lambda: gg.tree_plus_gnp(300, 6.0, 5))),
+    ("blocked CG vs dense and single solves",
+     lambda: te.test_blocked_cg_matches_dense_and_single_solves(gg.barabasi_albert(3000, 4, 9))),
 ]
 
 TGTPLUS = [
@@ -140,6 +142,10 @@ def _first_kill(battery):
 # otherwise the named oracle module. The old text must occur exactly once.
 
 C_MUTANTS = [
+    ("blocked CG: a converged column keeps iterating", "exact",
+     "alpha[c] = active[c] ? rz[c] / pq[c] : 0.0;", "alpha[c] = rz[c] / pq[c];"),
+    ("blocked CG: the Laplacian product adds the neighbours", "exact",
+     "for (int c = 0; c < CG_W; ++c) acc[c] -= pj[c];", "for (int c = 0; c < CG_W; ++c) acc[c] += pj[c];"),
     ("hop term sign", "series",
      "const double term = p_next[i] / d_i - p_next[j] / d_i;",
      "const double term = p_next[j] / d_i - p_next[i] / d_i;"),
@@ -252,8 +258,11 @@ PY_MUTANTS = [
      "out[e] = 1 - Fraction(_spanning_tree_count(n, rest), total)",
      "out[e] = Fraction(_spanning_tree_count(n, rest), total)"),
     ("exact", "sparse LU: x_u + x_v", "exact",
-     "x[pp[:, 0], np.arange(pp.shape[0])] - x[pp[:, 1], np.arange(pp.shape[0])]",
-     "x[pp[:, 0], np.arange(pp.shape[0])] + x[pp[:, 1], np.arange(pp.shape[0])]"),
+     "out[s:s + chunk] = x[pp[:, 0], cols] - x[pp[:, 1], cols]",
+     "out[s:s + chunk] = x[pp[:, 0], cols] + x[pp[:, 1], cols]"),
+    ("exact", "sparse LU: a mis-grounded matrix", "exact",
+     "grounded = lap[:-1, :-1]  # node n-1 deleted", "grounded = lap[1:, :-1]  # node n-1 deleted"),
+
     # philox.py
     ("philox", "Philox words swapped", "tgtplus",
      "c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]", "c = [hi0 ^ c[1] ^ k0, lo0, hi1 ^ c[3] ^ k1, lo1]"),

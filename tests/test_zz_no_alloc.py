@@ -3,9 +3,10 @@ allocate device memory (a serving arena or a framework allocator that owns the
 device budget, latency-critical paths where cudaMalloc/cudaFree would block).
 
 It must give what sc_all_edges gives for the same options (fixed length, FP64
-blocks of 32, plain estimator), call after call, although every call works in
-the same static device array that keeps the previous call's contents. This
-file is named so that pytest collects it last.
+blocks of 32, plain estimator) and what the oracle's FP64 series gives at the
+same length, call after call, although every call works in the same static
+device array that keeps the previous call's contents. This file is named so
+that pytest collects it after the other GPU suites.
 """
 import ctypes
 
@@ -41,15 +42,27 @@ def _reference(g, ell):
 
 
 def test_noalloc_matches_all_edges_on_consecutive_calls(cuda_lib):
+    """Several calls in a row through the C ABI, each checked against both
+    sc_all_edges (same options) and the oracle's FP64 series at the same length
+    (Algorithm 2): stale scratch from the previous call must not leak in. The
+    lengths reach every branch of the entry point: ell = 0 (no hop), 1 (the
+    gather of X_1 alone), 2 (the last hop straight after the first), >= 3 (full
+    hops); n = 700 and 901 leave a partial last block of 32 sources."""
     import torch
 
+    from oracle import series
+
     stream = torch.cuda.current_stream()
-    cases = [(gg.tree_plus_gnp(700, 8.0, 3), 7), (gg.barabasi_albert(900, 4, 2), 5),
-             (gg.tree_plus_gnp(700, 8.0, 3), 7), (gg.perturbed_grid(9, 11, 0.05, 1), 0)]
-    for g, ell in cases:  # several calls in a row: stale scratch from the previous call must not leak in
+    g_tree = gg.tree_plus_gnp(700, 8.0, 3)
+    g_ba = gg.barabasi_albert(901, 4, 2)
+    cases = [(g_tree, 7), (g_ba, 5), (g_tree, 1), (g_ba, 2), (g_tree, 7), (gg.perturbed_grid(9, 11, 0.05, 1), 0),
+             (g_ba, 1), (g_tree, 2)]
+    for g, ell in cases:
         got = _noalloc(cuda_lib, g, ell, stream)
         want = _reference(g, ell)
         assert np.max(np.abs(got - want)) <= TOL64
+        exact_series, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, ell)
+        assert np.max(np.abs(got - exact_series)) <= TOL64
 
 
 def test_noalloc_rejects_graphs_beyond_the_scratch_limit(cuda_lib):
