@@ -48,7 +48,11 @@ WORKLOADS = {
                               "(bipartite, bandwidth 1000)",
                          make=lambda gg: gg.perturbed_grid(1000, 1000, 0.05, 2)),
 }
-KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh"]
+KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh", "paper_2305_16086_gb300/csrc/hop2_mask.cuh",
+                  "paper_2305_16086_gb300/csrc/sparse_hops.cuh"]
+# kernel classes the library times separately (SC_KC_* order) and their kernels
+KERNEL_CLASSES = {"dense_hop": "k_spmm_hop", "mask_hop": "k_mask_scatter + k_hop2_mask", "sparse_hop": "k_hop_sparse",
+                  "ball_hop": "k_hop_ball", "last_hop": "k_last_diag + k_last_rows"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spmm_hop_ba200k_traffic.json")
 
 
@@ -408,6 +412,7 @@ def parse_args(argv=None):
     ap.add_argument("--ell", type=int, default=0, help="length for --policy fixed")
     ap.add_argument("--estimator", default="plain", choices=["plain", "end_corrected"])
     ap.add_argument("--no-arms", action="store_true")
+    ap.add_argument("--no-tgt-plus-arm", action="store_true", help="leave out the TGT+ arm (Algorithm 4)")
     ap.add_argument("--block-width", type=int, default=0)
     ap.add_argument("--rows-split", type=int, default=0)
     ap.add_argument("--heavy-threshold", type=int, default=0)
@@ -497,19 +502,32 @@ def main():
     ms_per_step = total_ms / args.steps
     value = replica_value(world, g.m, ms_per_step)
 
-    hop_ms = sum(r["hop_ms"] for r in reports)
-    hop_bytes = sum(r["hop_bytes"] for r in reports)
-    hop_launches = sum(r["hop_launches"] for r in reports)
     peak, peak_kind = measured_peaks()
-    achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else 0.0
     rep0 = reports[0]
-    config_key = f"{args.workload}/{args.precision}/B{rep0['block_width']}/v{rep0['rows_split']}"
-    traffic = recorded_traffic(config_key)
+    # every timed kernel class of the traversal; the roofline goes to the one with the most device time
+    classes = {}
+    for name in KERNEL_CLASSES:
+        ms = sum(r["kernel_classes"][name]["ms"] for r in reports)
+        nb = sum(r["kernel_classes"][name]["bytes"] for r in reports)
+        nl = sum(r["kernel_classes"][name]["launches"] for r in reports)
+        classes[name] = {"kernels": KERNEL_CLASSES[name], "ms_per_step": ms / args.steps,
+                         "launches_per_step": nl / args.steps,
+                         "share_of_step": ms / total_ms if total_ms > 0 else None,
+                         "algorithmic_GBps": nb / (ms / 1e3) / 1e9 if ms > 0 and nb > 0 else None,
+                         "_ms": ms, "_bytes": nb, "_launches": nl}
+    top = max(classes, key=lambda k: classes[k]["_ms"])
+    c = classes[top]
+    achieved = c["_bytes"] / (c["_ms"] / 1e3) / 1e9 if c["_ms"] > 0 else 0.0
+    config_key = f"{args.workload}/{args.precision}/B{rep0['block_width']}/v{rep0['rows_split']}/{top}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_spmm_hop", "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": hop_bytes / max(hop_launches, 1),
-                "avg_launch_us": hop_ms * 1e3 / max(hop_launches, 1), "launches_timed": hop_launches,
-                "share_of_step": hop_ms / total_ms if total_ms > 0 else None}
+                "traffic": recorded_traffic(config_key), "kernel": c["kernels"], "kernel_class": top,
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": c["_bytes"] / max(c["_launches"], 1),
+                "avg_launch_us": c["_ms"] * 1e3 / max(c["_launches"], 1), "launches_timed": c["_launches"],
+                "share_of_step": c["share_of_step"]}
+    for v in classes.values():
+        for k in ("_ms", "_bytes", "_launches"):
+            v.pop(k)
 
     # end to end through the public API with host buffers: H2D of the CSR,
     # graph validation, eigenvalue bound, all edges, D2H of s_hat
@@ -555,6 +573,25 @@ def main():
             arms[name] = {"value": world * g.m / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
                           "ms_per_step": e0.elapsed_time(e1), "source_hops": r["source_hops"],
                           "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m}
+        if args.mode == "tgt" and not args.no_tgt_plus_arm:
+            # Algorithm 4 (TGT+: traversal, switch test of Eq. 14 by the cost rule, Philox walks) at
+            # the same eps, FP32 blocks, lengths of Eq. 6 at eps / 2
+            kw = dict(run_kw, policy="global", precision="fp32", mode="tgt_plus")
+            G.all_edges(out=out, **kw)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, r = G.all_edges(out=out, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            arms["tgt_plus_fp32"] = {"value": world * g.m / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                                     "ms_per_step": e0.elapsed_time(e1), "source_hops": r["source_hops"],
+                                     "switch_after_hops": [r["tt_min"], r["tt_max"]], "walk_pairs": r["walks"],
+                                     "walk_steps": r["walk_steps"], "switch_tests": r["switch_tests"],
+                                     "switch_ms": r["switch_ms"], "walk_ms": r["walk_ms"],
+                                     "ell_global": r["ell_global"],
+                                     "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m}
 
     if rank != 0:
         if pg is not None:
@@ -584,7 +621,7 @@ def main():
                    "block_width": rep0["block_width"], "rows_split": rep0["rows_split"],
                    "slices": rep0["slices"], "l2": "working set > L2 and a 512 MB write between steps",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "arms": arms,
+        "roofline": roofline, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e, "arms": arms,
         "learned": {"source_hops": rep0["source_hops"], "extension_rounds": rep0["extension_rounds"],
                     "edges_extended": rep0["edges_extended"], "max_tail_bound": rep0["max_tail_bound"],
                     "model": "trained on Barabasi-Albert n=50000 m0=10 seed 101, 400 Adam steps"}

@@ -135,6 +135,18 @@ typedef struct sc_lambda_opts {
 sc_status sc_estimate_lambda(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
 
 /*
+ * sc_graph_set_lambda -- make the graph use a caller's eigenvalue bound (as
+ * the paper takes lambda from an external eigensolver, Section 5.3.3) in place
+ * of sc_estimate_lambda's: every later call that needs lambda (Eq. 6, the
+ * learned length's checks, the end-corrected bound) reads *lam. The caller
+ * vouches for it: lambda_star must bound the modulus of every eigenvalue of
+ * D^-1/2 A D^-1/2 except 1 (and -1 on a bipartite graph); nothing is checked
+ * beyond 0 <= lambda_star <= 1, |lambda_plus| <= lambda_star and, unless the
+ * graph is bipartite, |lambda_minus| <= lambda_star. Errors: SC_ERR_INVALID_ARG.
+ */
+sc_status sc_graph_set_lambda(sc_graph *g, const sc_lambda *lam);
+
+/*
  * sc_truncation_length -- tau per edge and per source from Eq. (5)-(6)
  * with omega = 2 (Algorithm 1's initial length), Upsilon = Delta_t = 0:
  *   f(e_ij, eps) = ceil( log(X_e / (eps (1 - lambda^2))) / log(1/lambda) - 1 ),
@@ -298,6 +310,25 @@ sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
    same either way. Not with TGT+ or the TMA-gather kernel. */
 #define SC_OPT_WINDOWS_OFF 8u
 #define SC_OPT_WINDOWS_FORCE 16u
+/* Unwindowed TGT blocks compute hop 3 from the non-zero values of X_2 only,
+   and hop L-1 only on the sources' two-hop balls, where the last hop reads it
+   (Algorithm 2's frontier, which visits only nodes it reaches); the values are
+   those of full hops bit for bit. This flag runs every hop between the second
+   and the last as a full hop instead (for comparison). */
+#define SC_OPT_DENSE_HOPS 32u
+/* TGT+ switch tests find each column's gamma largest entries (Algorithm 3's
+   candidates) from the entries at or above the gamma-th largest maximum of its
+   256-row tiles; this flag scans every row of the column instead (the same
+   candidates; for comparison). */
+#define SC_OPT_FULL_TOPGAMMA_SCAN 64u
+
+/* kernel classes of the per-class timing in sc_report (SC_OPT_TIME_KERNELS) */
+#define SC_KC_DENSE_HOP 0   /* full hops (k_spmm_hop, or the TMA-gather hop) */
+#define SC_KC_MASK_HOP 1    /* hops 1-2 from the sources' neighbour bits (k_mask_scatter + k_hop2_mask) */
+#define SC_KC_SPARSE_HOP 2  /* hop 3 from the non-zero values of X_2 (k_hop_sparse) */
+#define SC_KC_BALL_HOP 3    /* hop L-1 on the two-hop balls (k_hop_ball) */
+#define SC_KC_LAST_HOP 4    /* the last hop where its gather reads it (k_last_diag + k_last_rows) */
+#define SC_KC_COUNT 5
 
 typedef struct sc_options {
     double eps;               /* absolute error target of Definition 2.2, 0 < eps < 1 */
@@ -344,7 +375,7 @@ typedef struct sc_report {
     int64_t blocks;            /* source blocks processed */
     int64_t launches;          /* kernel launches issued */
     int64_t hops;              /* sum over blocks of hops run */
-    double algorithmic_bytes;  /* bytes the propagation must move (CSR + block read + write per hop) */
+    double algorithmic_bytes;  /* bytes the propagation's hop launches must move, every kernel class */
     double foster_sum;         /* sum over edges of s_hat; Foster's theorem: n - 1 for exact values */
     double max_tail_bound;     /* with SC_OPT_RECORD_TAIL: max a-posteriori tail bound */
     double lambda_star;        /* lambda used */
@@ -364,6 +395,12 @@ typedef struct sc_report {
     int32_t windowed;          /* 1 if the blocks ran windowed (SC_OPT_WINDOWS_*) */
     int64_t walk_steps;        /* TGT+: walk steps taken (both walks of every pair) */
     double walk_device_ms;     /* TGT+: device time of the walk launches (events) */
+    /* with SC_OPT_TIME_KERNELS, per kernel class SC_KC_*: summed duration (events around
+       each launch), launches, and the algorithmic bytes those launches must move (CSR,
+       1/d, masks, block reads and writes; the dense class is hop_ms / hop_bytes) */
+    double kc_ms[SC_KC_COUNT];
+    int64_t kc_launches[SC_KC_COUNT];
+    double kc_bytes[SC_KC_COUNT];
 } sc_report;
 
 /*
@@ -393,6 +430,29 @@ typedef struct sc_report {
  */
 sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                        sc_report *report);
+
+/*
+ * sc_some_edges -- s_hat for the listed CSR entries only: Definition 2.2's
+ * output restricted to a set of edges. Algorithm 2's loop over sources runs
+ * over the endpoints of the listed entries alone (each edge needs the half sums
+ * of Eq. 9 from both of its endpoints); everything else is sc_all_edges with
+ * the same options. A source's column does not depend on which sources share
+ * its block, so each value equals sc_all_edges's at that entry bit for bit,
+ * except under TGT+ with SC_SWITCH_COST or SC_SWITCH_PAPER, where a block's
+ * switch hop depends on its sources (with SC_SWITCH_PER_SOURCE it does not).
+ * The learned policy checks and extends only entries whose two endpoints ran.
+ *
+ *   opts    : as sc_all_edges (NULL = defaults); SC_OUT_DEVICE applies to s_out
+ *   count   : number of entries, >= 1
+ *   entries : host int64[count], CSR entry indices in [0, nnz) (repeats allowed)
+ *   s_out   : double[count], host or device per SC_OUT_DEVICE: s_hat of entries[t]
+ *   report  : nullable; as sc_all_edges, with foster_sum the sum of the count
+ *             returned values and max_tail_bound the largest over the listed entries
+ * Errors: those of sc_all_edges; SC_ERR_INVALID_ARG for count < 1, NULL arrays
+ * or an entry outside [0, nnz).
+ */
+sc_status sc_some_edges(sc_graph *g, const sc_options *opts, int64_t count, const int64_t *entries, double *s_out,
+                        sc_report *report);
 
 /*
  * sc_batch_all_edges -- sc_all_edges over many independent graphs in one

@@ -213,3 +213,86 @@ def tgt_plus_half(n, row_ptr, col_idx, i, tau_row, tt, eps, delta, gamma, seed, 
         R[t] = walk_count(chi[t], d_i, m, delta, eps)
         g[t] += walk_estimate(row_ptr, col_idx, p, i, j, L, k0 + t, int(R[t]), seed)
     return g, R, chi
+
+
+# ---------------------------------------------------------------------------
+# TGT+ at per-source lengths (the learned length; not in the paper) with the
+# truncation certified after the run.
+#
+# For odd tau and even l <= tau + 1 the tail of Eq. 2 past tau is at most
+# lam*^(tau + 1 - l) / (1 - lam*) t_l(e). The expansion in the proof of
+# Theorem 3.2 writes the tail as sum_k c_k lam_k^(tau+1) / (1 - lam_k) with
+# c_k >= 0, and the hop-l term as t_l(e) = sum_k c_k lam_k^l, whose terms are
+# all >= 0 for even l. Each tail term then splits as c_k lam_k^l (>= 0) times
+# lam_k^(tau+1-l), an even power at most lam*^(tau+1-l), over 1 - lam_k >= 1 - lam*.
+# The bound needs one hop term, and only one the traversal has already reached,
+# so TGT+ can certify a length its walks run past.
+# ---------------------------------------------------------------------------
+
+def even_hop_bound(t_l, ell, tau, lam_star):
+    """lam*^(tau + 1 - ell) / (1 - lam*) * t_l: the power by repeated
+    multiplication (tau odd, ell even, ell <= tau + 1)."""
+    f = 1.0
+    for _ in range(tau + 1 - ell):
+        f *= lam_star
+    return f / (1.0 - lam_star) * t_l
+
+
+def tgt_plus_learned(n, row_ptr, col_idx, L_src, cap, eps, lam_star, delta, gamma, seed, m, depth_cap=16,
+                     max_rounds=64):
+    """TGT+ (Algorithm 4, the switch of Eq. 14 per source as printed) at the
+    per-source lengths L_src (odd, at most cap = Eq. 6's length at eps / 2).
+    tau_e = min(L_i, L_j) for both halves of an edge. After the run each edge
+    is certified with eps / 2 for the truncation (Algorithm 4's split: the
+    walks take the other eps / 2) by ``even_hop_bound`` at
+    l* = the largest even hop <= min(tt_i, tt_j, tau_e + 1, depth_cap) (tt =
+    the source's switch hop: its traversal reached it); an edge that fails
+    takes the least odd tau > tau_e the same bound accepts (at most cap), and
+    both endpoints run again. Returns (s_hat per entry, tau per entry, tt per
+    source, rounds with an extension)."""
+    from . import series
+
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col_idx = np.asarray(col_idx)
+    deg = np.diff(row_ptr)
+    rows = np.repeat(np.arange(n), deg)
+    rev = series.reverse_entries(n, row_ptr, col_idx)
+    L_src = np.asarray(L_src, dtype=np.int64)
+    tau = np.minimum(L_src[rows], L_src[col_idx])
+    half = np.zeros(col_idx.size)           # g_hat(v_i, v_j) / d_i per entry
+    even = np.zeros((col_idx.size, depth_cap // 2 + 1))  # (p_l(i,i) - p_l(j,i)) / d_i at even l
+    tt = np.zeros(n, dtype=np.int64)
+    need = list(range(n))
+    rounds = 0
+    for _ in range(max_rounds + 1):
+        for i in need:
+            a, b = row_ptr[i], row_ptr[i + 1]
+            t_i = switch_hop(n, row_ptr, col_idx, i, tau[a:b], eps, delta, gamma, m)
+            g_i, _, _ = tgt_plus_half(n, row_ptr, col_idx, i, tau[a:b], t_i, eps, delta, gamma, seed, m)
+            half[a:b] = g_i / deg[i]
+            tt[i] = t_i
+            nbr = col_idx[a:b]
+            for ell in range(0, min(t_i, depth_cap) + 1, 2):
+                p = source_column(n, row_ptr, col_idx, i, ell)
+                even[a:b, ell // 2] = (p[i] - p[nbr]) / deg[i]
+        redo = set()
+        for k in range(col_idx.size):
+            i, j = int(rows[k]), int(col_idx[k])
+            if i > j:
+                continue
+            kr = int(rev[k])
+            te = int(tau[k])
+            d = min(int(tt[i]), int(tt[j]), te + 1, depth_cap)
+            ell = d - (d % 2)
+            t_l = even[k, ell // 2] + even[kr, ell // 2]
+            if te < cap and even_hop_bound(t_l, ell, te, lam_star) > 0.5 * eps:
+                t_new = te + 2
+                while t_new < cap and even_hop_bound(t_l, ell, t_new, lam_star) > 0.5 * eps:
+                    t_new += 2
+                tau[k] = tau[kr] = min(t_new, cap)
+                redo.update((i, j))
+        if not redo:
+            break
+        rounds += 1
+        need = sorted(redo)
+    return half + half[rev], tau, tt, rounds

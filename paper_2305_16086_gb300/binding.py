@@ -29,7 +29,8 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 EST = {"plain": 0, "end_corrected": 1}
 MODE = {"tgt": 0, "tgt_plus": 1}
 SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
-SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE = 8, 16
+SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE, SC_OPT_DENSE_HOPS, SC_OPT_FULL_TOPGAMMA_SCAN = 8, 16, 32, 64
+KC_NAMES = ["dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop"]  # SC_KC_* order
 
 # every symbol include/sc.h declares
 EXPORTS = [
@@ -38,7 +39,7 @@ EXPORTS = [
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
     "sc_batch_all_edges", "sc_selftest_bounded_waits", "sc_eigenpairs", "sc_caltau", "sc_tridiag_eig",
-    "sc_series_meet",
+    "sc_series_meet", "sc_some_edges", "sc_graph_set_lambda",
 ]
 OMEGA_MAX = 257
 MLP_PARAMS, MLP_FEATURES = 1313, 6
@@ -86,10 +87,17 @@ class Report(ctypes.Structure):
                 ("tt_min", ctypes.c_int32), ("tt_max", ctypes.c_int32),
                 ("switch_tests", ctypes.c_int32), ("switch_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
                 ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32),
-                ("walk_steps", ctypes.c_int64), ("walk_device_ms", ctypes.c_double)]
+                ("walk_steps", ctypes.c_int64), ("walk_device_ms", ctypes.c_double),
+                ("kc_ms", ctypes.c_double * 5), ("kc_launches", ctypes.c_int64 * 5),
+                ("kc_bytes", ctypes.c_double * 5)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        for name in ("kc_ms", "kc_launches", "kc_bytes"):
+            d[name] = list(d[name])
+        d["kernel_classes"] = {KC_NAMES[c]: {"ms": d["kc_ms"][c], "launches": d["kc_launches"][c],
+                                             "bytes": d["kc_bytes"][c]} for c in range(len(KC_NAMES))}
+        return d
 
 
 class EigOpts(ctypes.Structure):
@@ -174,6 +182,11 @@ def load(path: str = LIB_PATH):
     L.sc_eigenpairs.restype = ctypes.c_int
     L.sc_caltau.argtypes = [vp, f64, i32, f64p, f64p, f64, i32p, i32p]
     L.sc_caltau.restype = ctypes.c_int
+    L.sc_graph_set_lambda.argtypes = [vp, ctypes.POINTER(Lambda)]
+    L.sc_graph_set_lambda.restype = ctypes.c_int
+    L.sc_some_edges.argtypes = [vp, ctypes.POINTER(Options), i64, ctypes.POINTER(ctypes.c_int64), vp,
+                                ctypes.POINTER(Report)]
+    L.sc_some_edges.restype = ctypes.c_int
     L.sc_series_meet.argtypes = [vp, i32p, f64p]
     L.sc_series_meet.restype = ctypes.c_int
     L.sc_tridiag_eig.argtypes = [i32, f64p, f64p, f64p, f64p]
@@ -267,6 +280,11 @@ class Graph:
             _check(st, "sc_estimate_lambda")
         return {name: getattr(out, name) for name, _ in Lambda._fields_}
 
+    def set_lambda(self, lambda_plus: float, lambda_minus: float, lambda_star: float):
+        """sc_graph_set_lambda: use the caller's eigenvalue bound (residuals 0)."""
+        lam = Lambda(lambda_plus, lambda_minus, lambda_star, 0.0, 0.0, 0, 1)
+        _check(load().sc_graph_set_lambda(self._h, ctypes.byref(lam)), "sc_graph_set_lambda")
+
     def eigenpairs(self, omega: int = 128, max_iter: int = 0, tol: float = 0.0, rest_tol: float = 0.0,
                    rest_max_iter: int = 0, seed: int = 0x1a2b3c4d, allow_unconverged: bool = False):
         """sc_eigenpairs: (lam float64[omega], F float64[omega, n], report dict); lam[0] = 1, F[0] = 1,
@@ -320,7 +338,8 @@ class Graph:
     def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
                 record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
-                switch="cost", windows=None, bf16_from_hop=0) -> Options:
+                switch="cost", windows=None, bf16_from_hop=0, dense_hops=False,
+                full_topgamma_scan=False) -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
         o.eps = eps
@@ -336,6 +355,10 @@ class Graph:
         o.flags = (SC_OPT_RECORD_TAIL if record_tail else 0) | (SC_OPT_TIME_KERNELS if time_kernels else 0)
         if windows is not None:  # None: automatic; True / False: force on / off
             o.flags |= SC_OPT_WINDOWS_FORCE if windows else SC_OPT_WINDOWS_OFF
+        if dense_hops:
+            o.flags |= SC_OPT_DENSE_HOPS
+        if full_topgamma_scan:
+            o.flags |= SC_OPT_FULL_TOPGAMMA_SCAN
         if seed is not None:
             o.seed = seed
         o.delta = delta
@@ -369,6 +392,26 @@ class Graph:
                                    ctypes.c_void_p(b.ctypes.data) if b is not None else None,
                                    ctypes.byref(rep)), "sc_all_edges")
         return s, b, rep.as_dict()
+
+
+def some_edges(graph, entries, out=None, **kw):
+    """sc_some_edges: s_hat at the listed CSR entries (int64 indices) only.
+    ``out``: a torch CUDA float64 tensor of len(entries) values (device output)
+    or None (host numpy output). Returns (values, report dict)."""
+    ent = np.ascontiguousarray(entries, dtype=np.int64)
+    o = Graph.options(**kw)
+    rep = Report()
+    if out is not None:
+        o.flags |= SC_OUT_DEVICE
+        dst = ctypes.c_void_p(out.data_ptr())
+        res = out
+    else:
+        res = np.empty(ent.size, dtype=np.float64)
+        dst = ctypes.c_void_p(res.ctypes.data)
+    _check(load().sc_some_edges(graph._h, ctypes.byref(o), ent.size,
+                                ent.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dst, ctypes.byref(rep)),
+           "sc_some_edges")
+    return res, rep.as_dict()
 
 
 def batch_all_edges(graphs, ell_per_graph=None, outs=None, **kw):

@@ -150,8 +150,9 @@ struct sc_graph {
     int32_t bandwidth = -1;
     // per-slice windows of windowed launches
     sc::DevBuf<unsigned char> win_list;
-    // bit mask of the block's first-hop rows (hop 2 from the sources alone)
-    sc::DevBuf<uint32_t> mask;
+    // bit mask of the block's first-hop rows (hop 2 from the sources alone),
+    // and the non-zero columns of X_2 (hop 3 from its non-zero values)
+    sc::DevBuf<uint32_t> mask, mask_nz;
     // X_L at the sources (the last hop, computed where the gather reads it)
     sc::DevBuf<double> last_diag;
     // row runs of about equal CSR entries, one per warp, for the TMA kernel
@@ -187,7 +188,7 @@ struct sc_graph {
     sc::DevBuf<int32_t> tau_entry, src_list, status;
     sc::DevBuf<double> scratch_d;
     // TGT+ work buffers: CalChi partial and per-column statistics, walk counts
-    sc::DevBuf<double> tp_pval, tp_pmin, tp_pmax, tp_cval, tp_cmin, tp_cmax;
+    sc::DevBuf<double> tp_pval, tp_pmin, tp_pmax, tp_cval, tp_cmin, tp_cmax, tp_cthr;
     sc::DevBuf<int32_t> tp_pid, tp_cid;
     sc::DevBuf<long long> tp_pvol, tp_cvol, tp_walks, tp_counters, tp_packed, tp_chunk_w0;
     sc::DevBuf<int32_t> tp_eq, tp_ek, tp_chunk_entry, tp_entry_chunk0;

@@ -42,6 +42,7 @@ struct MaskHopArgs {
     const int32_t *tau;
     double *g, *t1, *t2;
     GatherRec rec;
+    uint32_t *nz;  // nullable: slices x n x B/32 words, bit b of row r set iff the stored X_2[r, b] != 0
 };
 
 
@@ -134,7 +135,15 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
             }
             __syncthreads();
         }
-        if (threadIdx.x < B) xn[static_cast<int64_t>(row) * B + threadIdx.x] = from_acc<T>(total * a.inv_deg[row]);
+        T v = from_acc<T>(Acc(0));
+        if (threadIdx.x < B) {
+            v = from_acc<T>(total * a.inv_deg[row]);
+            xn[static_cast<int64_t>(row) * B + threadIdx.x] = v;
+        }
+        if (a.nz && threadIdx.x < B) {  // B is a multiple of 32: warp w holds columns 32 w ..
+            const uint32_t word = __ballot_sync(0xffffffffu, to_acc(v) != Acc(0));
+            if (lane == 0) a.nz[(static_cast<int64_t>(blockIdx.y) * n + row) * W + warp] = word;
+        }
         return;
     }
     // light rows: one warp per row, chunk by chunk
@@ -161,6 +170,15 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
 #pragma unroll
         for (int c = 0; c < CPL; ++c) out.v[c] = from_acc<T>(acc[c] * sc);
         *reinterpret_cast<Vec *>(xn + static_cast<int64_t>(row) * B + lc0) = out;
+        if (a.nz) {
+            // the lane's CPL bits at lshift of word lw; the GW lanes of a word OR theirs together
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) bits |= (to_acc(out.v[c]) != Acc(0) ? 1u : 0u) << (lshift + c);
+#pragma unroll
+            for (int o = GW / 2; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+            if (lane % GW == 0) a.nz[(static_cast<int64_t>(blockIdx.y) * n + row) * W + lw] = bits;
+        }
     }
 }
 

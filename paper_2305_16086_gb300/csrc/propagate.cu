@@ -13,6 +13,7 @@
 
 #include "hop2_mask.cuh"
 #include "hop_tma.cuh"
+#include "sparse_hops.cuh"
 #include "tgtplus.cuh"
 #include "propagate.cuh"
 
@@ -21,14 +22,15 @@ namespace sc {
 sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
 void tgtplus_reserve(sc_graph *g, int slices, int B);
 void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, const int32_t *src, const int32_t *h_src,
-                   int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
-                   long long *rhs, long long *steps, cudaStream_t s, long long *vol_src = nullptr,
+                   int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, bool full_scan,
+                   long long *lhs, long long *rhs, long long *steps, cudaStream_t s, long long *vol_src = nullptr,
                    long long *rhs_src = nullptr);
 void tgtplus_cap_rows(sc_graph *g, const int32_t *h_list, int count, int32_t cap, int32_t *tau, cudaStream_t s);
 long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32_t *src, const int32_t *h_src,
                         int nsrc, const int32_t *tau, int tt, uint64_t seed, double *acc_g, cudaStream_t s,
                         long long *steps_out);
 constexpr int kCostRuleHops = 4;  // the cost rule tests the last hops only
+constexpr int kEvenDepthCap = 16;  // TGT+ at learned lengths: even hops recorded for the check (hop <= 16)
 // TGT+ cost rule rates measured on GB300: a hop costs about this much per
 // source and CSR entry (BA-200k, FP32 blocks: 1.1 us per source over 4.0M
 // entries), a walk step (three dependent random reads) about kWalkStepNs
@@ -349,7 +351,8 @@ static void last_hop_p(sc_graph *g, int B, const void *x, const int32_t *src, in
 
 template <typename T, int B>
 static void hop2_mask_t(const sc_graph *g, uint32_t *mask, void *x2, int slices, const int32_t *src, int nsrc,
-                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, uint32_t *nz,
+                        cudaStream_t s) {
     k_mask_scatter<B><<<nsrc, 128, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), src, nsrc, mask, g->n);
     MaskHopArgs<T> m{};
     m.row_ptr = g->row_ptr.get();
@@ -370,33 +373,112 @@ static void hop2_mask_t(const sc_graph *g, uint32_t *mask, void *x2, int slices,
     m.t1 = b;
     m.t2 = c;
     m.rec = rec;
+    m.nz = nz;
     dim3 grid(m.gather_ctas + m.n_heavy + m.light_ctas, slices);
     k_hop2_mask<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(m);
 }
 
 template <typename T>
 static void hop2_mask_p(const sc_graph *g, int B, uint32_t *mask, void *x2, int slices, const int32_t *src, int nsrc,
-                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+                        const int32_t *tau, double *a, double *b, double *c, const GatherRec &rec, uint32_t *nz,
+                        cudaStream_t s) {
     switch (B) {
-    case 32: hop2_mask_t<T, 32>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
-    case 64: hop2_mask_t<T, 64>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
-    case 128: hop2_mask_t<T, 128>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, s); break;
+    case 32: hop2_mask_t<T, 32>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, nz, s); break;
+    case 64: hop2_mask_t<T, 64>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, nz, s); break;
+    case 128: hop2_mask_t<T, 128>(g, mask, x2, slices, src, nsrc, tau, a, b, c, rec, nz, s); break;
     default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
     }
 }
 
 // hops 1 and 2 of a block from its sources alone (X_1 is never stored): marks
-// N(s_b) in a bit mask (zeroed here), computes X_2 into x2 and gathers hop 1
+// N(s_b) in a bit mask (zeroed here), computes X_2 into x2 and gathers hop 1;
+// with want_nz also the non-zero columns of X_2 (into g->mask_nz)
 void launch_hop2_mask(sc_graph *g, int prec, int B, void *x2, int slices, const int32_t *src, int nsrc,
-                      const int32_t *tau, double *a, double *b, double *cc, const GatherRec &rec, cudaStream_t s) {
+                      const int32_t *tau, double *a, double *b, double *cc, const GatherRec &rec, bool want_nz,
+                      cudaStream_t s) {
     const size_t words = static_cast<size_t>(slices) * g->n * (B / 32);
     g->mask.reserve(words);
+    uint32_t *nz = nullptr;
+    if (want_nz) {
+        g->mask_nz.reserve(words);
+        nz = g->mask_nz.get();
+    }
     SC_CUDA(cudaMemsetAsync(g->mask.get(), 0, words * sizeof(uint32_t), s));
     switch (prec) {
-    case SC_PREC_FP64: hop2_mask_p<double>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s); break;
-    case SC_PREC_FP32: hop2_mask_p<float>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s); break;
+    case SC_PREC_FP64: hop2_mask_p<double>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, nz, s); break;
+    case SC_PREC_FP32: hop2_mask_p<float>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, nz, s); break;
     case SC_PREC_BF16:
-        hop2_mask_p<__nv_bfloat16>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, s);
+        hop2_mask_p<__nv_bfloat16>(g, B, g->mask.get(), x2, slices, src, nsrc, tau, a, b, cc, rec, nz, s);
+        break;
+    }
+    SC_LAUNCH_CHECK();
+}
+
+template <typename T, int B>
+static void hop_sparse_t(const sc_graph *g, bool ball, const void *xp, void *xn, int slices, const uint32_t *mask,
+                         const int32_t *src, int nsrc, const int32_t *tau, int gather_ell, double *a, double *b,
+                         double *c, const GatherRec &rec, cudaStream_t s) {
+    SparseHopArgs<T> h{};
+    h.row_ptr = g->row_ptr.get();
+    h.col = g->col_idx.get();
+    h.inv_deg = inv_deg_of<T>(g);
+    h.x_prev = static_cast<const T *>(xp);
+    h.x_next = static_cast<T *>(xn);
+    h.mask = mask;
+    h.n = g->n;
+    h.row_order = g->row_order.get();
+    h.n_heavy = g->n_heavy;
+    h.heavy_t = g->heavy_threshold_cached;
+    h.src = src;
+    h.nsrc = nsrc;
+    h.tau = tau;
+    h.gather_ell = gather_ell;
+    h.g = a;
+    h.t1 = b;
+    h.t2 = c;
+    h.rec = rec;
+    h.gather_ctas = gather_ell > 0 ? B : 0;
+    if (ball) {
+        h.heavy_ctas = ceil_div(g->n_heavy, kSpmmWarps);
+        h.light_ctas = ceil_div(g->n, 32 * kSpmmWarps);
+        dim3 grid(h.gather_ctas + h.heavy_ctas + h.light_ctas, slices);
+        k_hop_ball<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
+    } else {
+        h.heavy_ctas = g->n_heavy;
+        h.light_ctas = light_ctas_for(g->n, kSpmmWarps, g->num_sms);  // one light row per warp
+        dim3 grid(h.gather_ctas + g->n_heavy + h.light_ctas, slices);
+        k_hop_sparse<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
+    }
+}
+
+template <typename T>
+static void hop_sparse_p(const sc_graph *g, int B, bool ball, const void *xp, void *xn, int slices,
+                         const uint32_t *mask, const int32_t *src, int nsrc, const int32_t *tau, int gather_ell,
+                         double *a, double *b, double *c, const GatherRec &rec, cudaStream_t s) {
+    switch (B) {
+    case 32: hop_sparse_t<T, 32>(g, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, c, rec, s); break;
+    case 64: hop_sparse_t<T, 64>(g, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, c, rec, s); break;
+    case 128: hop_sparse_t<T, 128>(g, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, c, rec, s); break;
+    default: SC_FAIL(SC_ERR_INVALID_ARG, "block width %d", B);
+    }
+}
+
+// hop `gather_ell + 1` of a block from X_{gather_ell} (xp) into xn with the
+// fused gather of X_{gather_ell}: ball = false: the full hop reading only the
+// non-zero values of xp (mask = their columns, g->mask_nz); ball = true: the
+// values on the sources' two-hop balls only (mask = the neighbour bits, g->mask)
+void launch_hop_sparse(const sc_graph *g, int prec, int B, bool ball, const void *xp, void *xn, int slices,
+                       const uint32_t *mask, const int32_t *src, int nsrc, const int32_t *tau, int gather_ell,
+                       double *a, double *b, double *cc, const GatherRec &rec, cudaStream_t s) {
+    switch (prec) {
+    case SC_PREC_FP64:
+        hop_sparse_p<double>(g, B, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, cc, rec, s);
+        break;
+    case SC_PREC_FP32:
+        hop_sparse_p<float>(g, B, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, cc, rec, s);
+        break;
+    case SC_PREC_BF16:
+        hop_sparse_p<__nv_bfloat16>(g, B, ball, xp, xn, slices, mask, src, nsrc, tau, gather_ell, a, b, cc, rec, s);
         break;
     }
     SC_LAUNCH_CHECK();
@@ -580,16 +662,20 @@ __global__ void k_tau_min_of_sources(const int32_t *__restrict__ row_ptr, const 
 // whose length is below the a-priori cap gets tau <- min(2 tau + 1, cap);
 // its row is marked for a rerun. Both directions of an edge carry the same
 // bound, so both endpoints are marked.
-__global__ void k_extend_failing(const int32_t *__restrict__ row_ptr, const double *__restrict__ bound, int32_t n,
-                                 double eps, int32_t cap, int32_t *__restrict__ tau, int32_t *__restrict__ row_flag,
-                                 unsigned long long *count) {
+// With `active` (a subset of the sources was run), only entries whose two
+// endpoints were both run are checked.
+__global__ void k_extend_failing(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                 const double *__restrict__ bound, int32_t n, double eps, int32_t cap,
+                                 const int32_t *__restrict__ active, int32_t *__restrict__ tau,
+                                 int32_t *__restrict__ row_flag, unsigned long long *count) {
     const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     int any = 0;
     unsigned long long c = 0;
+    const bool row_on = !active || active[r];
     for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
-        if (bound[k] > eps && tau[k] < cap) {
+        if (row_on && (!active || active[col[k]]) && bound[k] > eps && tau[k] < cap) {
             tau[k] = min(2 * tau[k] + 1, cap);
             any = 1;
             ++c;
@@ -616,6 +702,89 @@ __global__ void k_row_max(const int32_t *__restrict__ row_ptr, const int32_t *__
 
 void learned_lengths(sc_graph *g, int32_t cap, int32_t *L_dev, cudaStream_t s);
 
+// lam^e / (1 - lam) * t, the power by repeated multiplication
+__device__ __forceinline__ double even_hop_bound(double t, int32_t e, double lam) {
+    double f = 1.0;
+    for (int32_t q = 0; q < e; ++q) f = __dmul_rn(f, lam);
+    return __dmul_rn(__ddiv_rn(f, __dsub_rn(1.0, lam)), t);
+}
+
+// The truncation check of TGT+ at learned lengths (Algorithm 4 keeps eps/2 for
+// the truncation). For odd tau and even l <= tau + 1 the tail past tau is at
+// most lam*^(tau + 1 - l) / (1 - lam*) t_l(e) (the mode expansion in the proof
+// of Theorem 3.2: t_l(e) = sum_k c_k lam_k^l with every term >= 0 at even l).
+// l = the largest even hop both endpoints' traversals reached (depth, capped
+// at 2 (stride - 1)), at most tau + 1; t_l from the recorded half terms. An
+// entry whose bound exceeds eps_half takes the least odd length the same
+// bound accepts, at most cap; both directions of an edge evaluate the same
+// expression, so both take the same length and mark their rows for a rerun.
+// With `active` (a subset of the sources was run), only entries whose two
+// endpoints were both run are checked.
+__global__ void k_certify_plus(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                               const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                               const double *__restrict__ even, int32_t stride, const int32_t *__restrict__ depth,
+                               const int32_t *__restrict__ active, int32_t n, double lam, double eps_half,
+                               int32_t cap, int32_t *__restrict__ tau, int32_t *__restrict__ row_flag,
+                               unsigned long long *count) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int any = 0;
+    unsigned long long c = 0;
+    const bool row_on = !active || active[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t j = col[k], kr = rev[k], te = tau[k];
+        if (!row_on || (active && !active[j]) || te >= cap) continue;
+        const int32_t d = min(min(depth[r], depth[j]), min(te + 1, 2 * (stride - 1)));
+        const int32_t ell = d & ~1;
+        const double t = __dadd_rn(__dmul_rn(even[static_cast<int64_t>(k) * stride + (ell >> 1)], inv_d[r]),
+                                   __dmul_rn(even[static_cast<int64_t>(kr) * stride + (ell >> 1)], inv_d[j]));
+        if (even_hop_bound(t, te + 1 - ell, lam) > eps_half) {
+            int32_t tn = te + 2;
+            while (tn < cap && even_hop_bound(t, tn + 1 - ell, lam) > eps_half) tn += 2;
+            tau[k] = min(tn, cap);
+            any = 1;
+            ++c;
+        }
+    }
+    any = __any_sync(0xffffffffu, any);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        row_flag[r] = any;
+        if (c) atomicAdd(count, c);
+    }
+}
+
+// active[i] = active[j] = 1 for each listed entry k = (i -> j) (row by binary search)
+__global__ void k_mark_endpoints(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                                 const int64_t *__restrict__ entries, int64_t count, int32_t *__restrict__ active) {
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t >= count) return;
+    const int32_t k = static_cast<int32_t>(entries[t]);
+    int32_t lo = 0, hi = n;  // the row r with row_ptr[r] <= k < row_ptr[r + 1]
+    while (hi - lo > 1) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (row_ptr[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    active[lo] = 1;
+    active[col[k]] = 1;
+}
+
+__global__ void k_gather_entries(const double *__restrict__ x, const int64_t *__restrict__ entries, int64_t count,
+                                 double *__restrict__ out) {
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t < count) out[t] = x[entries[t]];
+}
+
+// the listed CSR entries of sc_some_edges (host array) and where their values go
+struct EdgeSubset {
+    int64_t count;
+    const int64_t *entries;
+    double *out;
+};
+
 // ---------------------------------------------------------------------------
 // the block loop: propagates the given sources in blocks, longest first
 // ---------------------------------------------------------------------------
@@ -631,9 +800,15 @@ struct Run {
     int extra;  // hops beyond the per-source length (records of tau+1, tau+2)
     GatherRec rec;
     int32_t h0 = 0x7fffffff;  // SC_PREC_BF16: first hop stored in bf16 (fp32 before)
+    std::vector<int32_t> *depth = nullptr;  // TGT+: per node, the last hop its traversal reached
     bool capture = false;  // windowed loop: record into one CUDA graph
     // statistics
     int64_t launches = 0, hops = 0, source_hops = 0, hop_launches = 0, walks = 0, graph_launches = 0, walk_steps = 0;
+    // per kernel class (SC_KC_*): event pairs (index into the graph's pool) and algorithmic bytes
+    std::vector<std::pair<int, int64_t>> timed;
+    int64_t event_pairs = 0;
+    int64_t kc_launches[SC_KC_COUNT] = {};
+    double kc_bytes[SC_KC_COUNT] = {};
     double walk_device_ms = 0.0;
     double alg_bytes = 0.0, switch_ms = 0.0, walk_ms = 0.0;
     int32_t ell_min_src = INT32_MAX, ell_max_src = 0, tt_min = INT32_MAX, tt_max = 0, switch_tests = 0;
@@ -683,6 +858,29 @@ static void hop_mixed(const Run &R, HopLaunch h, int32_t ell, size_t elems, cuda
     std::swap(*xa, *xb);
 }
 
+// brackets one launch of kernel class `cls` with a pair of events from the
+// graph's pool (SC_OPT_TIME_KERNELS) and books its algorithmic bytes; the
+// opening call returns the pair's index (-1 when not timing)
+static int64_t timer_open(Run &R, cudaStream_t s) {
+    if (!R.time_kernels) return -1;
+    const int64_t i = R.event_pairs++;
+    while (static_cast<int64_t>(R.g->hop_events.size()) < 2 * (i + 1)) {
+        cudaEvent_t e;
+        SC_CUDA(cudaEventCreate(&e));
+        R.g->hop_events.push_back(e);
+    }
+    SC_CUDA(cudaEventRecord(R.g->hop_events[2 * i], s));
+    return i;
+}
+
+static void timer_close(Run &R, int64_t i, int cls, double bytes, cudaStream_t s) {
+    R.kc_launches[cls] += 1;
+    R.kc_bytes[cls] += bytes;
+    if (i < 0) return;
+    SC_CUDA(cudaEventRecord(R.g->hop_events[2 * i + 1], s));
+    R.timed.push_back({cls, i});
+}
+
 static double wall_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -703,15 +901,6 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
     std::copy(sources.begin(), sources.end(), h_src.begin());
     g->src_list.reserve(h_src.size());
     SC_CUDA(cudaMemcpyAsync(g->src_list.get(), h_src.data(), h_src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    if (R.time_kernels) {
-        int64_t total_hops = 0;
-        for (int64_t sb = 0; sb < nsuper; ++sb) total_hops += std::max(len[sources[sb * S]] + R.extra - 1, 0);
-        while (static_cast<int64_t>(g->hop_events.size()) < 2 * (R.hop_launches + total_hops)) {
-            cudaEvent_t e;
-            SC_CUDA(cudaEventCreate(&e));
-            g->hop_events.push_back(e);
-        }
-    }
     cudaEvent_t ev_w0, ev_w1;
     SC_CUDA(cudaEventCreate(&ev_w0));
     SC_CUDA(cudaEventCreate(&ev_w1));
@@ -723,10 +912,13 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         }
     } evg{ev_w0, ev_w1};
     // algorithmic bytes of hop ell per slice: CSR, 1/d, read X_{ell-1}, write X_ell
+    const double csr_bytes = 4.0 * nnz + 4.0 * (n + 1) + (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n;  // + 1/d
+    const double mask_bytes = static_cast<double>(n) * B / 8.0;
     auto hop_bytes_per_slice = [&](int32_t ell) {
-        return 4.0 * nnz + 4.0 * (n + 1) + (R.prec == SC_PREC_FP64 ? 8.0 : 4.0) * n +
-               static_cast<double>(n) * B * (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
+        return csr_bytes + static_cast<double>(n) * B * (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
     };
+    const bool dense_only = (R.o->flags & SC_OPT_DENSE_HOPS) != 0;
+    const bool full_scan = (R.o->flags & SC_OPT_FULL_TOPGAMMA_SCAN) != 0;
     for (int64_t sb = 0; sb < nsuper; ++sb) {
         const int64_t first = sb * S;
         const int nsrc = static_cast<int>(std::min<int64_t>(S, ns - first));
@@ -745,10 +937,21 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         const bool test_at_1 =
             R.plus && (R.o->switch_rule != SC_SWITCH_COST || 1 >= std::max(1, L - kCostRuleHops));
         const bool from_mask = !test_at_1 && L >= 3 && prec_at(R, 1) == prec_at(R, 2);
+        // hop 3 from X_2's non-zero values (a full hop: L >= 5 keeps it before hop L - 1), and
+        // hop L - 1 on the sources' two-hop balls (read by the sparse last hop only: TGT, whose
+        // traversal nothing else reads; no storage change around it)
+        const bool hop3_sparse = from_mask && !dense_only && L >= 5 && prec_at(R, 2) == prec_at(R, 3);
+        const bool ball_hop = from_mask && !dense_only && !R.plus && L >= 4 && prec_at(R, L - 2) == prec_at(R, L - 1) &&
+                              prec_at(R, L - 1) == prec_at(R, L);
         int ell0 = 2;
         if (from_mask) {
+            const int64_t t = timer_open(R, s);
             launch_hop2_mask(g, prec_at(R, 2), B, xb, used_slices, src, nsrc, g->tau_entry.get(), g->acc_g.get(),
-                             g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+                             g->acc_t1.get(), g->acc_t2.get(), R.rec, hop3_sparse, s);
+            timer_close(R, t, SC_KC_MASK_HOP,
+                        used_slices * (csr_bytes + (hop3_sparse ? 3.0 : 2.0) * mask_bytes +
+                                       static_cast<double>(n) * B * elem_size(prec_at(R, 2))),
+                        s);
             std::swap(xa, xb);
             R.launches += 2;
             ell0 = 3;
@@ -775,8 +978,8 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 long long lhs = 0, rhs = 0, steps = 0;
                 const double t0 = wall_ms();
                 tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc,
-                              g->tau_entry.get(), ell - 1, R.gamma, R.o->eps, R.log2md, &lhs, &rhs, &steps, s,
-                              vol_src.data(), rhs_src.data());
+                              g->tau_entry.get(), ell - 1, R.gamma, R.o->eps, R.log2md, full_scan, &lhs, &rhs,
+                              &steps, s, vol_src.data(), rhs_src.data());
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
                 R.launches += 4;
@@ -821,7 +1024,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 long long lhs = 0, rhs = 0, steps = 0;
                 const double t0 = wall_ms();
                 tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc, g->tau_entry.get(),
-                              ell - 1, R.gamma, R.o->eps, R.log2md, &lhs, &rhs, &steps, s);
+                              ell - 1, R.gamma, R.o->eps, R.log2md, full_scan, &lhs, &rhs, &steps, s);
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
                 R.launches += 3;
@@ -844,18 +1047,36 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                     const int32_t v = h_src[first + q];
                     if (v >= 0) max_deg = std::max(max_deg, g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
                 }
+                const int64_t t = timer_open(R, s);
                 launch_last_hop(g, prec_at(R, ell), B, xa, src, nsrc, max_deg, g->tau_entry.get(), ell,
                                 g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+                timer_close(R, t, SC_KC_LAST_HOP, 0.0, s);
                 R.launches += 2;
                 last_done = true;
                 break;
             }
+            if ((ell == 3 && hop3_sparse) || (ell == L - 1 && ball_hop)) {
+                // hop ell computed where it can be non-zero (hop 3) or is read (hop L - 1), with the
+                // fused gather of X_{ell-1}
+                const bool ball = ell == L - 1 && ball_hop;
+                const int64_t t = timer_open(R, s);
+                launch_hop_sparse(g, prec_at(R, ell), B, ball, xa, xb, used_slices,
+                                  ball ? g->mask.get() : g->mask_nz.get(), src, nsrc, g->tau_entry.get(), ell - 1,
+                                  g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), R.rec, s);
+                timer_close(R, t, ball ? SC_KC_BALL_HOP : SC_KC_SPARSE_HOP,
+                            used_slices * (csr_bytes + mask_bytes +
+                                           (ball ? 0.0 : static_cast<double>(n) * B * elem_size(prec_at(R, ell)))),
+                            s);
+                std::swap(xa, xb);
+                R.launches += 1;
+                continue;
+            }
             // hop ell computes X_ell and, in its first CTAs, gathers X_{ell-1}
             HopLaunch h{xa, xb, used_slices, src, nsrc, g->tau_entry.get(), ell - 1,
                         g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), g->status.get(), R.rec};
-            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], s));
+            const int64_t t = timer_open(R, s);
             hop_mixed(R, h, ell, static_cast<size_t>(used_slices) * n * B, s, &xa, &xb);
-            if (R.time_kernels) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], s));
+            timer_close(R, t, SC_KC_DENSE_HOP, used_slices * hop_bytes_per_slice(ell), s);
             ++R.hop_launches;
             R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;
             R.alg_bytes += used_slices * hop_bytes_per_slice(ell);
@@ -867,6 +1088,9 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         }
         R.hops += tt;
         R.source_hops += static_cast<int64_t>(tt) * nsrc;
+        if (R.depth)
+            for (int q = 0; q < nsrc; ++q)
+                if (h_src[first + q] >= 0) (*R.depth)[h_src[first + q]] = per_source && src_tt[q] >= 0 ? src_tt[q] : tt;
         if (per_source) {
             for (int q = 0; q < nsrc; ++q) {
                 if (h_src[first + q] < 0) continue;
@@ -1040,15 +1264,6 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     SC_CUDA(cudaMemcpyAsync(g->win_list.get(), h_win.data(), h_win.size() * sizeof(SliceWin), cudaMemcpyHostToDevice, s));
     const SliceWin *d_win = reinterpret_cast<const SliceWin *>(g->win_list.get());
     const bool timed = R.time_kernels && !R.capture;
-    if (timed) {
-        int64_t total_hops = 0;
-        for (size_t q = 0; q + 1 < sb_begin.size(); ++q) total_hops += blocks[sb_begin[q]].w.L;
-        while (static_cast<int64_t>(g->hop_events.size()) < 2 * (R.hop_launches + total_hops)) {
-            cudaEvent_t e;
-            SC_CUDA(cudaEventCreate(&e));
-            g->hop_events.push_back(e);
-        }
-    }
     const auto &hrp = g->h_row_ptr;
     // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is replayed on the caller's
@@ -1115,9 +1330,9 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
             h.beta = beta;
             h.win_heavy = heavy_max;
             h.win_rows = rows_max;
-            if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches], is));
+            const int64_t t = timed ? timer_open(R, is) : -1;
             hop_mixed(R, h, ell, bytes / elem, is, &xa, &xb, true);
-            if (timed) SC_CUDA(cudaEventRecord(g->hop_events[2 * R.hop_launches + 1], is));
+            timer_close(R, t, SC_KC_DENSE_HOP, hop_bytes, is);
             ++R.hop_launches;
             R.launches += prec_at(R, ell - 1) != prec_at(R, ell) ? 2 : 1;
             R.alg_bytes += hop_bytes;
@@ -1148,8 +1363,15 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
 // sc_all_edges
 // ---------------------------------------------------------------------------
 static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep,
-                           double *rec_all = nullptr, int rec_stride = 0) {
-    if (!g || !s_hat) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or output");
+                           double *rec_all = nullptr, int rec_stride = 0, const EdgeSubset *sub = nullptr) {
+    if (!g || (!s_hat && !sub)) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or output");
+    if (sub) {
+        if (sub->count < 1 || !sub->entries || !sub->out) SC_FAIL(SC_ERR_INVALID_ARG, "need count >= 1 entries and an output");
+        for (int64_t t = 0; t < sub->count; ++t)
+            if (sub->entries[t] < 0 || sub->entries[t] >= g->nnz)
+                SC_FAIL(SC_ERR_INVALID_ARG, "entries[%lld] = %lld outside [0, nnz)", static_cast<long long>(t),
+                        static_cast<long long>(sub->entries[t]));
+    }
     sc_options o;
     if (o_in) o = *o_in;
     else sc_options_default(&o);
@@ -1158,8 +1380,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     if (o.bf16_from_hop < 0) SC_FAIL(SC_ERR_INVALID_ARG, "bf16_from_hop %d < 0", o.bf16_from_hop);
     if (o.mode != SC_MODE_TGT && o.mode != SC_MODE_TGT_PLUS) SC_FAIL(SC_ERR_INVALID_ARG, "mode %d", o.mode);
     const bool plus = o.mode == SC_MODE_TGT_PLUS;
-    if (plus && (o.estimator != SC_EST_PLAIN || (o.flags & SC_OPT_RECORD_TAIL) || o.ell_policy == SC_ELL_LEARNED))
-        SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ takes the plain estimator, no tail records and an Eq. 6 length");
+    if (plus && (o.estimator != SC_EST_PLAIN || (o.flags & SC_OPT_RECORD_TAIL)))
+        SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ takes the plain estimator and no tail records");
     const int gamma = o.gamma < 0 ? 10 : o.gamma;
     if (plus && gamma > kGammaMax) SC_FAIL(SC_ERR_UNSUPPORTED, "gamma %d above %d", gamma, kGammaMax);
     if (o.switch_rule < SC_SWITCH_COST || o.switch_rule > SC_SWITCH_PER_SOURCE)
@@ -1258,7 +1480,18 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaMemsetAsync(g->status.get(), 0, 4 * sizeof(int32_t), s));
     // rows_split: 0 = automatic, -1 = the TMA-gather kernel, 1/2/4 = SIMT lane split
     const int fixV = o.rows_split == 0 ? -1 : (o.rows_split < 0 ? 0 : o.rows_split);
-    const GatherRec rec{learned ? 1 : 0, rec_all, rec_stride};
+    // TGT+ at learned lengths records the half terms of the even hops its traversal reaches
+    // (hops <= kEvenDepthCap) for the truncation check after the run
+    const bool learned_plus = learned && plus;
+    DevBuf<double> even_rec;
+    int even_stride = 0;
+    if (learned_plus) {
+        even_stride = std::min(ell_global + 1, kEvenDepthCap) / 2 + 1;
+        even_rec.reserve(static_cast<size_t>(nnz) * even_stride);
+        rec_all = even_rec.get();
+        rec_stride = even_stride;
+    }
+    const GatherRec rec{learned_plus ? 2 : (learned ? 1 : 0), rec_all, rec_stride};
     g->acc_g.reserve(nnz);
     g->acc_t1.reserve(nnz);
     g->acc_t2.reserve(nnz);
@@ -1292,6 +1525,11 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     R.log2md = std::log(2.0 * static_cast<double>(nnz / 2) / delta);
     R.extra = record_after ? 2 : 0;
     R.rec = rec;
+    std::vector<int32_t> depth;
+    if (learned_plus) {
+        depth.assign(n, 0);
+        R.depth = &depth;
+    }
     const int64_t nblocks_total = (static_cast<int64_t>(n) + R.B - 1) / R.B;
 
     g->xa.reserve(R.slices * R.slice_bytes);
@@ -1304,37 +1542,69 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
 
     // ---- propagation ----------------------------------------------------------
     SC_CUDA(cudaEventRecord(ev1, s));
-    std::vector<int32_t> all(n);
-    std::iota(all.begin(), all.end(), 0);
+    std::vector<int32_t> all;
+    DevBuf<int32_t> active;   // sc_some_edges: the endpoints of the listed entries
+    DevBuf<int64_t> d_entries;
+    if (sub) {
+        active.reserve(n);
+        d_entries.reserve(sub->count);
+        SC_CUDA(cudaMemsetAsync(active.get(), 0, n * sizeof(int32_t), s));
+        SC_CUDA(cudaMemcpyAsync(d_entries.get(), sub->entries, sub->count * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_mark_endpoints<<<ceil_div(sub->count, 256), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), n,
+                                                                  d_entries.get(), sub->count, active.get());
+        SC_LAUNCH_CHECK();
+        std::vector<int32_t> h_active(n);
+        SC_CUDA(cudaMemcpyAsync(h_active.data(), active.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+        for (int32_t v = 0; v < n; ++v)
+            if (h_active[v]) all.push_back(v);
+        R.launches += 1;
+    } else {
+        all.resize(n);
+        std::iota(all.begin(), all.end(), 0);
+    }
     const std::vector<int32_t> seg_whole{0, n};
     auto run = [&](const std::vector<int32_t> &src, const std::vector<int32_t> &l) {
         if (use_win) run_blocks_win(R, src, l, seg_whole, beta);
         else run_blocks(R, src, l);
     };
+    DevBuf<int32_t> tau_saved;
+    if (learned_plus) {
+        tau_saved.reserve(nnz);
+        SC_CUDA(cudaMemcpyAsync(tau_saved.get(), g->tau_entry.get(), nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
     run(all, len);
 
     // ---- combine, and for the learned lengths the check / extension loop ------
     DevBuf<double> tmp_s, tmp_b;
     double *d_s = s_hat;
     double *d_b = tail_bound;
-    if (!out_dev) {
+    if (sub) {  // every entry's value in scratch; the listed ones are gathered at the end
         tmp_s.reserve(nnz);
         d_s = tmp_s.get();
-        if (tail_bound || learned) {
+        d_b = nullptr;
+        if (learned && !plus) {
             tmp_b.reserve(nnz);
             d_b = tmp_b.get();
         }
-    } else if (learned && !d_b) {
+    } else if (!out_dev) {
+        tmp_s.reserve(nnz);
+        d_s = tmp_s.get();
+        if (tail_bound || (learned && !plus)) {
+            tmp_b.reserve(nnz);
+            d_b = tmp_b.get();
+        }
+    } else if (learned && !plus && !d_b) {
         tmp_b.reserve(nnz);
         d_b = tmp_b.get();
     }
-    const bool have_tail = record_after || learned;
+    const bool have_tail = record_after || (learned && !plus);
     if (!have_tail) d_b = nullptr;
     // bound scales: after-records q = t_{tau+1} + t_{tau+2}: q / (2 (1 - lambda_plus)) (end-corrected) or
     // q / (1 - lambda*^2); learned (records of hops tau-1, tau): lambda*^2 / (1 - lambda*^2) (t_{tau-1} + t_tau).
     // lambda_plus carries its Ritz residual as a safety margin.
     double bound_scale = 0.0;
-    if (learned) {
+    if (learned && !plus) {
         bound_scale = lam_star * lam_star / (1.0 - lam_star * lam_star);
     } else if (record_after) {
         const double lp = g->lam.lambda_plus + std::max(g->lam.residual_plus, 0.0);
@@ -1352,14 +1622,61 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     combine();
     int64_t extended = 0;
     int32_t rounds = 0;
-    if (learned) {
+    if (learned_plus) {
+        // certify each edge's truncation (eps/2) after the run; failing edges take a longer
+        // length and both endpoints run again (their walks included), until every edge passes
+        DevBuf<int32_t> row_flag, rows, d_depth, tau_target;
+        row_flag.reserve(n);
+        d_depth.reserve(n);
+        tau_target.reserve(nnz);
+        g->tp_counters.reserve(4);
+        std::vector<int32_t> h_flag(n);
+        // the per-source switch caps the lengths of switched rows in place: the targets are these
+        SC_CUDA(cudaMemcpyAsync(tau_target.get(), tau_saved.get(), nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        while (true) {
+            SC_CUDA(cudaMemcpyAsync(d_depth.get(), depth.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, sizeof(long long), s));
+            k_certify_plus<<<ceil_div(n, 8), 256, 0, s>>>(
+                g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(), even_rec.get(), even_stride,
+                d_depth.get(), sub ? active.get() : nullptr, n, lam_star, 0.5 * o.eps, ell_global, tau_target.get(),
+                row_flag.get(),
+                reinterpret_cast<unsigned long long *>(g->tp_counters.get()));
+            SC_LAUNCH_CHECK();
+            R.launches += 1;
+            long long failing = 0;
+            SC_CUDA(cudaMemcpyAsync(&failing, g->tp_counters.get(), sizeof(long long), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaMemcpyAsync(h_flag.data(), row_flag.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            if (failing == 0) break;
+            extended += failing / 2;
+            ++rounds;
+            std::vector<int32_t> redo;
+            for (int32_t v = 0; v < n; ++v)
+                if (h_flag[v]) redo.push_back(v);
+            SC_CUDA(cudaMemcpyAsync(g->tau_entry.get(), tau_target.get(), nnz * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+            k_row_max<<<ceil_div(n, 256), 256, 0, s>>>(g->row_ptr.get(), tau_target.get(), n, tau_src.get());
+            SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            rows.reserve(redo.size());
+            SC_CUDA(cudaMemcpyAsync(rows.get(), redo.data(), redo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            k_reset_rows<<<ceil_div(static_cast<int64_t>(redo.size()), 8), 256, 0, s>>>(
+                g->row_ptr.get(), rows.get(), static_cast<int32_t>(redo.size()), g->tau_entry.get(), 2, g->acc_g.get(),
+                g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
+            SC_LAUNCH_CHECK();
+            R.launches += 2;
+            run(redo, len);
+        }
+        combine();
+    } else if (learned) {
         DevBuf<int32_t> row_flag, rows;
         row_flag.reserve(n);
         g->tp_counters.reserve(4);
         std::vector<int32_t> h_flag(n);
         while (true) {
             SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, sizeof(long long), s));
-            k_extend_failing<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), d_b, n, o.eps, ell_global,
+            k_extend_failing<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), d_b, n, o.eps,
+                                                            ell_global, sub ? active.get() : nullptr,
                                                             g->tau_entry.get(), row_flag.get(),
                                                             reinterpret_cast<unsigned long long *>(g->tp_counters.get()));
             SC_LAUNCH_CHECK();
@@ -1392,11 +1709,29 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaEventRecord(ev2, s));
 
     g->scratch_d.reserve(kRedBlocks + 8);
-    const double foster2 = device_reduce(d_s, nnz, false, g->scratch_d.get(), s);
+    DevBuf<double> sub_s, sub_b;
+    int64_t red_count = nnz;
+    if (sub) {  // the listed entries' values (and bounds), in the caller's order
+        red_count = sub->count;
+        sub_s.reserve(sub->count);
+        k_gather_entries<<<ceil_div(sub->count, 256), 256, 0, s>>>(d_s, d_entries.get(), sub->count, sub_s.get());
+        d_s = sub_s.get();
+        if (d_b) {
+            sub_b.reserve(sub->count);
+            k_gather_entries<<<ceil_div(sub->count, 256), 256, 0, s>>>(d_b, d_entries.get(), sub->count, sub_b.get());
+            d_b = sub_b.get();
+        }
+        SC_LAUNCH_CHECK();
+        R.launches += d_b ? 2 : 1;
+    }
+    const double foster2 = device_reduce(d_s, red_count, false, g->scratch_d.get(), s);
     double max_bound = 0.0;
-    if (d_b) max_bound = device_reduce(d_b, nnz, true, g->scratch_d.get(), s);
+    if (d_b) max_bound = device_reduce(d_b, red_count, true, g->scratch_d.get(), s);
     R.launches += 2 + (d_b ? 2 : 0);
-    if (!out_dev) {
+    if (sub) {
+        SC_CUDA(cudaMemcpyAsync(sub->out, d_s, sub->count * sizeof(double),
+                                out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    } else if (!out_dev) {
         SC_CUDA(cudaMemcpyAsync(s_hat, d_s, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (tail_bound && d_b)
             SC_CUDA(cudaMemcpyAsync(tail_bound, d_b, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1409,14 +1744,15 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     SC_CUDA(cudaEventRecord(ev2, s));
     SC_CUDA(cudaEventSynchronize(ev2));
     SC_CUDA(cudaEventElapsedTime(&total_ms, ev0, ev2));
-    double hop_ms = 0.0;
-    if (time_kernels) {
-        for (int64_t i = 0; i < R.hop_launches; ++i) {
-            float ms = 0.f;
-            SC_CUDA(cudaEventElapsedTime(&ms, g->hop_events[2 * i], g->hop_events[2 * i + 1]));
-            hop_ms += ms;
-        }
+    double kc_ms[SC_KC_COUNT] = {};
+    for (const auto &tk : R.timed) {
+        float ms = 0.f;
+        SC_CUDA(cudaEventElapsedTime(&ms, g->hop_events[2 * tk.second], g->hop_events[2 * tk.second + 1]));
+        kc_ms[tk.first] += ms;
     }
+    const double hop_ms = kc_ms[SC_KC_DENSE_HOP];
+    double all_bytes = 0.0;
+    for (int c = 0; c < SC_KC_COUNT; ++c) all_bytes += R.kc_bytes[c];
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));
         rep->ell_global = ell_global;
@@ -1429,8 +1765,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->launches = R.launches;
         rep->hops = R.hops;
         rep->source_hops = R.source_hops;
-        rep->algorithmic_bytes = R.alg_bytes;
-        rep->foster_sum = 0.5 * foster2;
+        rep->algorithmic_bytes = all_bytes;
+        rep->foster_sum = sub ? foster2 : 0.5 * foster2;  // sc_some_edges: the sum of the listed entries' values
         rep->max_tail_bound = max_bound;
         rep->lambda_star = need_lambda ? lam_star : 0.0;
         rep->propagate_ms = prop_ms;
@@ -1449,6 +1785,11 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->walk_ms = R.walk_ms;
         rep->walk_steps = R.walk_steps;
         rep->walk_device_ms = R.walk_device_ms;
+        for (int c = 0; c < SC_KC_COUNT; ++c) {
+            rep->kc_ms[c] = kc_ms[c];
+            rep->kc_launches[c] = R.kc_launches[c];
+            rep->kc_bytes[c] = R.kc_bytes[c];
+        }
     }
 }
 
@@ -1770,6 +2111,14 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
 extern "C" sc_status sc_all_edges(sc_graph *g, const sc_options *opts, double *s_hat, double *tail_bound,
                                   sc_report *report) {
     return sc::guarded([&] { sc::all_edges_impl(g, opts, s_hat, tail_bound, report); });
+}
+
+extern "C" sc_status sc_some_edges(sc_graph *g, const sc_options *opts, int64_t count, const int64_t *entries,
+                                   double *s_out, sc_report *report) {
+    return sc::guarded([&] {
+        const sc::EdgeSubset sub{count, entries, s_out};
+        sc::all_edges_impl(g, opts, nullptr, nullptr, report, nullptr, 0, &sub);
+    });
 }
 
 extern "C" sc_status sc_batch_all_edges(sc_graph *const *graphs, int32_t count, const sc_options *opts,

@@ -80,8 +80,9 @@ __device__ __forceinline__ uint4 ld_x(const uint4 *p) { return __ldg(p); }
 
 // What the gather records besides the half sums.
 struct GatherRec {
-    int mode;       // 0: t1, t2 = terms of hops tau+1, tau+2; 1: terms of hops tau-1, tau
-    double *all;    // nullable: all[k * stride + ell] = term of hop ell (every hop)
+    int mode;       // 0: t1, t2 = terms of hops tau+1, tau+2; 1: terms of hops tau-1, tau;
+                    // 2: no t1 / t2; all[k * stride + ell / 2] = term of every even hop ell < 2 stride
+    double *all;    // nullable: (modes 0, 1) all[k * stride + ell] = term of hop ell (every hop)
     int stride;
 };
 
@@ -170,7 +171,11 @@ __device__ __forceinline__ void gather_term(int32_t k, double term, const int32_
         if (ell == tk + 1) t1[k] = term;
         else if (ell == tk + 2) t2[k] = term;
     }
-    if (rec.all) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
+    if (rec.all) {
+        if (rec.mode != 2) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
+        else if ((ell & 1) == 0 && (ell >> 1) < rec.stride)
+            rec.all[static_cast<int64_t>(k) * rec.stride + (ell >> 1)] = term;
+    }
 }
 
 template <typename T, int B>

@@ -395,6 +395,20 @@ sc_status sc_estimate_lambda(sc_graph *g, const sc_lambda_opts *opts, sc_lambda 
     return sc::estimate_lambda_impl(g, opts, out);
 }
 
+sc_status sc_graph_set_lambda(sc_graph *g, const sc_lambda *lam) {
+    return sc::guarded([&] {
+        if (!g || !lam) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or lambda");
+        const double ls = lam->lambda_star;
+        if (!(ls >= 0.0 && ls <= 1.0) || !(std::fabs(lam->lambda_plus) <= ls) ||
+            (!g->bipartite && !(std::fabs(lam->lambda_minus) <= ls)))
+            SC_FAIL(SC_ERR_INVALID_ARG, "need 0 <= lambda_star <= 1 bounding |lambda_plus| (and |lambda_minus| "
+                                        "on a graph that is not bipartite), got %g, %g, %g",
+                    lam->lambda_plus, lam->lambda_minus, ls);
+        g->lam = *lam;
+        g->has_lambda = true;
+    });
+}
+
 sc_status sc_truncation_length(sc_graph *g, double eps, const sc_lambda *lam, int32_t *ell_global_out,
                                int32_t *per_source_out, int32_t *per_entry_out) {
     return sc::guarded([&] {

@@ -9,18 +9,31 @@ namespace sc {
 
 template <typename T, int B>
 static void chi_check_t(sc_graph *g, const void *x, int slices, const int32_t *src, int nsrc, int max_deg,
-                        const int32_t *tau, int ell, int gamma, double eps, double log2md, cudaStream_t s) {
-    const int nct = ceil_div(g->n, kChiRowsPerCta);
+                        const int32_t *tau, int ell, int gamma, double eps, double log2md, bool full_scan,
+                        cudaStream_t s) {
     const int ncols = slices * B;
-    double *pval = g->tp_pval.get();
-    int32_t *pid = g->tp_pid.get();
     double *pmin = g->tp_pmin.get(), *pmax = g->tp_pmax.get();
     long long *pvol = g->tp_pvol.get();
-    k_chi_scan<T, B><<<dim3(nct, slices), kChiScanThreads, 0, s>>>(g->row_ptr.get(), static_cast<const T *>(x), g->n,
-                                                                 pval, pid, pmin, pmax, pvol);
-    k_chi_merge<B><<<ncols, kChiScanThreads, 0, s>>>(nct, ncols, pval, pid, pmin, pmax, pvol, g->tp_cval.get(),
-                                                        g->tp_cid.get(), g->tp_cmin.get(), g->tp_cmax.get(),
-                                                        g->tp_cvol.get());
+    if (full_scan) {
+        // every row of a column through a sorted list per 64-row tile, lists merged per column
+        const int nct = ceil_div(g->n, kChiRowsPerCta);
+        k_chi_scan<T, B><<<dim3(nct, slices), kChiScanThreads, 0, s>>>(
+            g->row_ptr.get(), static_cast<const T *>(x), g->n, g->tp_pval.get(), g->tp_pid.get(), pmin, pmax, pvol);
+        k_chi_merge<B><<<ncols, kChiScanThreads, 0, s>>>(nct, ncols, g->tp_pval.get(), g->tp_pid.get(), pmin, pmax,
+                                                            pvol, g->tp_cval.get(), g->tp_cid.get(), g->tp_cmin.get(),
+                                                            g->tp_cmax.get(), g->tp_cvol.get());
+    } else {
+        // tile maxima, the threshold per column, then the candidates at or above it
+        const int ntiles = ceil_div(g->n, kTileRows);
+        k_chi_tiles<T, B><<<dim3(ntiles, slices), kChiScanThreads, 0, s>>>(g->row_ptr.get(),
+                                                                          static_cast<const T *>(x), g->n, pmax,
+                                                                          pmin, pvol);
+        k_chi_thresh<B><<<ncols, kChiScanThreads, 0, s>>>(ntiles, ncols, gamma, pmax, pmin, pvol, g->tp_cthr.get(),
+                                                             g->tp_cmin.get(), g->tp_cmax.get(), g->tp_cvol.get());
+        k_chi_select<T, B><<<ncols, kChiScanThreads, 0, s>>>(g->n, ntiles, ncols, gamma, static_cast<const T *>(x),
+                                                                pmax, pmin, g->tp_cthr.get(), g->tp_cval.get(),
+                                                                g->tp_cid.get());
+    }
     ChiArgs a{};
     a.row_ptr = g->row_ptr.get();
     a.col = g->col_idx.get();
@@ -91,6 +104,7 @@ void tgtplus_reserve(sc_graph *g, int slices, int B) {
     g->tp_cid.reserve(cols * kGammaMax);
     g->tp_cmin.reserve(cols);
     g->tp_cmax.reserve(cols);
+    g->tp_cthr.reserve(cols);
     g->tp_cvol.reserve(cols);
     g->tp_srcstat.reserve(3 * cols);
     g->tp_src_rhs.reserve(cols);
@@ -104,13 +118,14 @@ void tgtplus_reserve(sc_graph *g, int slices, int B) {
 // L = tau_k - ell stay in g->tp_walks for the walk kernel. vol_src / rhs_src
 // (host, nsrc each; may be null): the two sides per source.
 void tgtplus_check(sc_graph *g, int prec, int B, const void *x, int slices, const int32_t *src, const int32_t *h_src,
-                   int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, long long *lhs,
-                   long long *rhs, long long *steps, cudaStream_t s, long long *vol_src, long long *rhs_src) {
+                   int nsrc, const int32_t *tau, int ell, int gamma, double eps, double log2md, bool full_scan,
+                   long long *lhs, long long *rhs, long long *steps, cudaStream_t s, long long *vol_src,
+                   long long *rhs_src) {
     SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, 4 * sizeof(long long), s));
     int max_deg = 0;
     for (int q = 0; q < nsrc; ++q)
         if (h_src[q] >= 0) max_deg = std::max(max_deg, g->h_row_ptr[h_src[q] + 1] - g->h_row_ptr[h_src[q]]);
-    SC_DISPATCH_TB(prec, B, chi_check_t, g, x, slices, src, nsrc, max_deg, tau, ell, gamma, eps, log2md, s);
+    SC_DISPATCH_TB(prec, B, chi_check_t, g, x, slices, src, nsrc, max_deg, tau, ell, gamma, eps, log2md, full_scan, s);
     SC_LAUNCH_CHECK();
     std::vector<long long> vol(static_cast<size_t>(slices) * B);
     long long h_cnt[3] = {0, 0, 0};

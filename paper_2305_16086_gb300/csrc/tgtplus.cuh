@@ -203,6 +203,238 @@ __global__ void __launch_bounds__(kChiScanThreads)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Threshold form of the same column statistics (the default): the top-gamma
+// list of a column needs only the entries at or above thr = the gamma-th
+// largest of its tile maxima (tiles of kTileRows rows). The gamma tiles with
+// the largest maxima hold gamma entries >= thr, so the gamma-th largest entry
+// is >= thr, and every entry of the top-gamma list lies in a tile whose
+// maximum reaches thr. Three launches: tile maxima, minima and volumes
+// (k_chi_tiles); per column thr, min, max and volume (k_chi_thresh); per
+// column the entries >= thr of the tiles reaching it, and the top-gamma list
+// among them in the total order (k_chi_select). thr = 0 (fewer than gamma
+// tiles hold a positive entry) takes the positive entries of those tiles and
+// the gamma smallest-id zero rows (the ties at 0 go to smaller ids). A column
+// with more than kCandMax candidates (many ties at thr) is scanned in full.
+// The first gamma entries of each list equal the full scan's; entries past
+// gamma are not read.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 256;
+constexpr int kCandMax = 2048;
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kChiScanThreads)
+    k_chi_tiles(const int32_t *__restrict__ row_ptr, const T *__restrict__ x, int32_t n, double *__restrict__ tmax,
+                double *__restrict__ tmin, long long *__restrict__ tvol) {
+    using V = typename AccOf<T>::type;
+    constexpr int TPC = kChiScanThreads / B;  // threads per column
+    const int c = threadIdx.x % B, sub = threadIdx.x / B;
+    const int32_t r0 = blockIdx.x * kTileRows, r1 = min(n, r0 + kTileRows);
+    const T *xs = x + static_cast<int64_t>(blockIdx.y) * n * B;
+    V vmax = V(-INFINITY), vmin = V(INFINITY);
+    long long vol = 0;
+    for (int32_t r = r0 + sub; r < r1; r += TPC) {
+        const V v = to_acc(xs[static_cast<int64_t>(r) * B + c]);
+        vmax = max(vmax, v);
+        vmin = min(vmin, v);
+        if (v != V(0)) vol += row_ptr[r + 1] - row_ptr[r];
+    }
+    __shared__ double smax[kChiScanThreads], smin[kChiScanThreads];
+    __shared__ long long svol[kChiScanThreads];
+    smax[threadIdx.x] = static_cast<double>(vmax);
+    smin[threadIdx.x] = static_cast<double>(vmin);
+    svol[threadIdx.x] = vol;
+    __syncthreads();
+    if (sub == 0) {
+        double a = smax[c], b = smin[c];
+        long long w = svol[c];
+        for (int t = 1; t < TPC; ++t) {
+            a = fmax(a, smax[c + t * B]);
+            b = fmin(b, smin[c + t * B]);
+            w += svol[c + t * B];
+        }
+        const int64_t o = (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * B + c;
+        tmax[o] = a;
+        tmin[o] = b;
+        tvol[o] = w;
+    }
+}
+
+// per column q = slice * B + b: thr = the gamma-th largest tile maximum (ties
+// counted), min, max and volume. One CTA per column; the top kGammaMax tile
+// maxima by the merge tree of the full scan (value descending, tile id
+// ascending).
+template <int B>
+__global__ void __launch_bounds__(kChiScanThreads)
+    k_chi_thresh(int ntiles, int ncols, int gamma, const double *__restrict__ tmax, const double *__restrict__ tmin,
+                 const long long *__restrict__ tvol, double *__restrict__ cthr, double *__restrict__ cmin,
+                 double *__restrict__ cmax, long long *__restrict__ cvol) {
+    const int q = blockIdx.x;
+    if (q >= ncols) return;
+    const int slice = q / B, c = q % B, t = threadIdx.x;
+    constexpr int NT = kChiScanThreads;
+    __shared__ double sv[kGammaMax * NT];
+    __shared__ int32_t si[kGammaMax * NT];
+    __shared__ double smin[NT];
+    __shared__ long long svol[NT];
+    double *val = sv + t;
+    int32_t *id = si + t;
+    for (int s = 0; s < kGammaMax; ++s) {
+        val[s * NT] = -INFINITY;
+        id[s * NT] = INT32_MAX;
+    }
+    double vmin = INFINITY;
+    long long vol = 0;
+    double bv[kGammaMax];
+    int32_t bi[kGammaMax];
+    for (int p = t; p < ntiles; p += NT) {
+        const int64_t o = (static_cast<int64_t>(slice) * ntiles + p) * B + c;
+        bv[0] = tmax[o];
+        bi[0] = p;
+#pragma unroll
+        for (int s = 1; s < kGammaMax; ++s) {
+            bv[s] = -INFINITY;
+            bi[s] = INT32_MAX;
+        }
+        merge_sorted(val, id, NT, bv, bi, 1);
+        vmin = fmin(vmin, tmin[o]);
+        vol += tvol[o];
+    }
+    smin[t] = vmin;
+    svol[t] = vol;
+    __syncthreads();
+    for (int half = NT / 2; half > 0; half >>= 1) {
+        if (t < half) {
+            merge_sorted(val, id, NT, sv + t + half, si + t + half, NT);
+            smin[t] = fmin(smin[t], smin[t + half]);
+            svol[t] += svol[t + half];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double g = gamma > 0 ? sv[(gamma - 1) * NT] : INFINITY;
+        cthr[q] = g > 0.0 ? g : 0.0;  // -inf (fewer tiles than gamma) counts as 0: every entry is >= 0
+        cmax[q] = sv[0];
+        cmin[q] = smin[0];
+        cvol[q] = svol[0];
+    }
+}
+
+// per column: the candidates (entries >= thr in the tiles whose maximum
+// reaches thr; for thr = 0 the positive entries of the tiles holding one, and
+// the gamma smallest-id zero rows), then the top-kGammaMax list among them.
+template <typename T, int B>
+__global__ void __launch_bounds__(kChiScanThreads)
+    k_chi_select(int32_t n, int ntiles, int ncols, int gamma, const T *__restrict__ x, const double *__restrict__ tmax,
+                 const double *__restrict__ tmin, const double *__restrict__ cthr, double *__restrict__ cval,
+                 int32_t *__restrict__ cid) {
+    using V = typename AccOf<T>::type;
+    const int q = blockIdx.x;
+    if (q >= ncols || gamma <= 0) return;
+    const int slice = q / B, c = q % B, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NT = kChiScanThreads, NW = kChiScanThreads / 32;
+    const T *xs = x + static_cast<int64_t>(slice) * n * B + c;
+    const double thr = cthr[q];
+    const bool zero_thr = !(thr > 0.0);
+    __shared__ double cand_v[kCandMax];
+    __shared__ int32_t cand_i[kCandMax];
+    __shared__ int ncand;
+    __shared__ double sv[kGammaMax * NT];
+    __shared__ int32_t si[kGammaMax * NT];
+    if (t == 0) ncand = 0;
+    __syncthreads();
+    // candidates: each warp takes tiles in turn, 32 rows at a time
+    for (int p = warp; p < ntiles; p += NW) {
+        const double tm = tmax[(static_cast<int64_t>(slice) * ntiles + p) * B + c];
+        if (zero_thr ? !(tm > 0.0) : !(tm >= thr)) continue;
+        const int32_t r0 = p * kTileRows, r1 = min(n, r0 + kTileRows);
+        for (int32_t rb = r0; rb < r1; rb += 32) {
+            const int32_t r = rb + lane;
+            const double v = r < r1 ? static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B])) : -1.0;
+            const bool take = zero_thr ? (v > 0.0) : (v >= thr);
+            const uint32_t bal = __ballot_sync(0xffffffffu, take);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&ncand, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+                const int slot = base + __popc(bal & ((1u << lane) - 1u));
+                if (slot < kCandMax) {
+                    cand_v[slot] = v;
+                    cand_i[slot] = r;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (zero_thr && warp == 0) {
+        // the gamma smallest-id zero rows, in id order
+        int need = gamma;
+        for (int p = 0; p < ntiles && need > 0; ++p) {
+            if (tmin[(static_cast<int64_t>(slice) * ntiles + p) * B + c] > 0.0) continue;
+            const int32_t r0 = p * kTileRows, r1 = min(n, r0 + kTileRows);
+            for (int32_t rb = r0; rb < r1 && need > 0; rb += 32) {
+                const int32_t r = rb + lane;
+                const bool z = r < r1 && to_acc(xs[static_cast<int64_t>(r) * B]) == V(0);
+                uint32_t bal = __ballot_sync(0xffffffffu, z);
+                int base = 0;
+                while (bal && need > 0) {  // warp-uniform
+                    const int l = __ffs(bal) - 1;
+                    bal &= bal - 1u;
+                    if (lane == 0) {
+                        base = ncand;
+                        if (base < kCandMax) {
+                            cand_v[base] = 0.0;
+                            cand_i[base] = rb + l;
+                        }
+                        ncand = base + 1;
+                    }
+                    --need;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    double *val = sv + t;
+    int32_t *id = si + t;
+    for (int s = 0; s < kGammaMax; ++s) {
+        val[s * NT] = -INFINITY;
+        id[s * NT] = INT32_MAX;
+    }
+    double bv[kGammaMax];
+    int32_t bi[kGammaMax];
+#pragma unroll
+    for (int s = 1; s < kGammaMax; ++s) {
+        bv[s] = -INFINITY;
+        bi[s] = INT32_MAX;
+    }
+    const int count = ncand;
+    if (count <= kCandMax) {
+        for (int e = t; e < count; e += NT) {
+            bv[0] = cand_v[e];
+            bi[0] = cand_i[e];
+            merge_sorted(val, id, NT, bv, bi, 1);
+        }
+    } else {
+        // too many ties at thr for the buffer: every row of the column
+        for (int32_t r = t; r < n; r += NT) {
+            bv[0] = static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B]));
+            bi[0] = r;
+            merge_sorted(val, id, NT, bv, bi, 1);
+        }
+    }
+    __syncthreads();
+    for (int half = NT / 2; half > 0; half >>= 1) {
+        if (t < half) merge_sorted(val, id, NT, sv + t + half, si + t + half, NT);
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int s = 0; s < kGammaMax; ++s) {
+            cval[static_cast<int64_t>(q) * kGammaMax + s] = sv[s * NT];
+            cid[static_cast<int64_t>(q) * kGammaMax + s] = si[s * NT];
+        }
+}
+
 __device__ __forceinline__ bool has_edge(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                          int32_t a, int32_t b) {
     int32_t lo = row_ptr[a], hi = row_ptr[a + 1];

@@ -29,8 +29,14 @@ class _Event:
         return 25.0
 
 
+def _kc(kw):
+    t = 1.0 if kw.get("time_kernels") else 0.0
+    return {name: {"ms": t * (20.0 if name == "dense_hop" else 2.0), "launches": 4, "bytes": 4.0e8}
+            for name in ("dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop")}
+
+
 def _report(kw):
-    return {"tt_min": 4, "tt_max": 5, "walks": 10, "walk_steps": 40, "switch_tests": 2, "switch_ms": 1.0,
+    return {"kernel_classes": _kc(kw), "tt_min": 4, "tt_max": 5, "walks": 10, "walk_steps": 40, "switch_tests": 2, "switch_ms": 1.0,
             "walk_ms": 0.5, "hop_ms": 20.0 if kw.get("time_kernels") else 0.0, "hop_bytes": 4.0e8,
             "hop_launches": 4, "launches": 12, "foster_sum": 0.0, "ell_global": 7, "block_width": 64,
             "rows_split": 1, "slices": 1, "blocks": 3, "windowed": 0, "source_hops": 700, "extension_rounds": 0,
@@ -141,6 +147,8 @@ def test_default_line_has_every_contract_key(fake_cuda):
     assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
     assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
     assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
+    assert d["roofline"]["kernel_class"] == "dense_hop" and set(d["kernel_classes"]) == {
+        "dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop"}
     assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"} and d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert list(d["e2e"]["phases_ms_of_a_warmup_pass"]) == ["create_validate", "lanczos", "model_load", "all_edges_d2h"]

@@ -128,3 +128,29 @@ def test_tgt_plus_cost_rule_walks_replace_remaining_hops(cuda_lib):
         s, _, rep = G.all_edges(eps=0.02, mode="tgt_plus", policy="per_edge", precision="fp32", seed=2)
     if r is not None:
         assert np.max(np.abs(s - r)) <= 0.02
+
+
+@pytest.mark.parametrize("maker,kw", [
+    (lambda: gg.barabasi_albert(3000, 5, 41), dict(policy="global", precision="fp32", switch="paper")),
+    (lambda: gg.barabasi_albert(2600, 6, 42), dict(policy="per_edge", precision="fp64", switch="cost", block_width=32)),
+    (lambda: gg.tree_plus_gnp(2200, 7.0, 43), dict(policy="global", precision="bf16", switch="per_source",
+                                                   block_width=64)),
+    (lambda: gg.rmat(12), dict(policy="global", precision="fp32", switch="paper", gamma=3)),
+    (lambda: gg.rmat(11), dict(policy="global", precision="fp32", switch="paper", gamma=0)),
+    # every column of K_n is one value off the source: thousands of ties at the threshold, so the
+    # candidate buffer overflows and the column is scanned in full inside the kernel
+    (lambda: gg.complete(2500), dict(policy="fixed", ell_fixed=5, precision="fp64", switch="paper")),
+])
+def test_threshold_topgamma_scan_equals_full_scan(cuda_lib, maker, kw):
+    """The switch test's top-gamma candidates (Algorithm 3) from the entries at or
+    above the gamma-th largest tile maximum give what the scan of every row
+    gives: the same walk counts, switch hops and walks, bit for bit."""
+    g = maker()
+    with _graph(g) as G:
+        base = dict(eps=5e-3, mode="tgt_plus", seed=9, **kw)
+        s, _, rep = G.all_edges(**base)
+        f, _, rep_f = G.all_edges(full_topgamma_scan=True, **base)
+    assert rep["switch_tests"] > 0
+    assert np.array_equal(s, f)
+    for key in ("walks", "walk_steps", "tt_min", "tt_max", "switch_tests"):
+        assert rep[key] == rep_f[key], key

@@ -255,3 +255,75 @@ def test_tgt_plus_with_per_source_switch_within_eps():
     rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
     assert walks > 0
     assert np.max(np.abs(ghat + ghat[rev] - r)) <= eps
+
+
+# ---------------------------------------------------------------- TGT+ at learned lengths
+@pytest.mark.parametrize("maker", [lambda: gg.tree_plus_gnp(40, 5.0, 3), lambda: gg.barabasi_albert(45, 3, 2),
+                                   lambda: gg.barbell(6, 2)])
+def test_even_hop_bound_holds_against_the_exact_tail(maker):
+    """tail past odd tau (exact resistance minus the series at tau) <= the
+    one-even-hop bound lam*^(tau + 1 - l) / (1 - lam*) t_l(e) for every even
+    l <= tau + 1, with lam* the spectral radius past lambda_1 from a dense
+    eigendecomposition."""
+    from oracle import learned
+
+    g = maker()
+    r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
+    deg = g.degree.astype(float)
+    A = np.zeros((g.n, g.n))
+    A[g.entry_rows(), g.col_idx] = 1.0
+    N = A / np.sqrt(np.outer(deg, deg))
+    ev = np.sort(np.linalg.eigvalsh(N))
+    lam = max(abs(ev[0]), abs(ev[-2]))
+    T = learned.hop_terms(g.n, g.row_ptr, g.col_idx, 12)
+    rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
+    full = T + T[rev]
+    for tau in (1, 3, 5, 9, 11):
+        S, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, tau)
+        tail = r - S
+        for ell in range(0, tau + 2, 2):
+            b = np.array([tgtplus.even_hop_bound(t, ell, tau, lam) for t in full[:, ell]])
+            assert np.all(tail <= b + 1e-12), (tau, ell)
+            assert np.all(full[:, ell] >= -1e-15)  # even hop terms are sums of non-negative mode terms
+
+
+def test_learned_tgt_plus_at_the_cap_is_per_source_tgt_plus():
+    """Every source at the cap: no length can grow, so the result is the
+    per-source TGT+ of Algorithm 4 (switch_hop, then tgt_plus_half) itself."""
+    from oracle import truncation
+
+    g = gg.tree_plus_gnp(50, 6.0, 7)
+    eps = 0.05
+    _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
+    cap = int(truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam).max())
+    s, tau, tt, rounds = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, cap), cap, eps, lam,
+                                                 1.0 / g.n, 10, 5, g.m)
+    assert rounds == 0 and np.all(tau == cap)
+    ghat = np.zeros(g.nnz)
+    for i in range(g.n):
+        a, b = g.row_ptr[i], g.row_ptr[i + 1]
+        ti = tgtplus.switch_hop(g.n, g.row_ptr, g.col_idx, i, tau[a:b], eps, 1.0 / g.n, 10, g.m)
+        assert ti == tt[i]
+        gi, _, _ = tgtplus.tgt_plus_half(g.n, g.row_ptr, g.col_idx, i, tau[a:b], ti, eps, 1.0 / g.n, 10, 5, g.m)
+        ghat[a:b] = gi / g.degree[i]
+    assert np.array_equal(s, ghat + ghat[series.reverse_entries(g.n, g.row_ptr, g.col_idx)])
+
+
+@pytest.mark.parametrize("L0", [1, 3])
+def test_learned_tgt_plus_extends_short_lengths_and_meets_eps(L0):
+    """Every source predicted far too short: the certificate fails, lengths
+    grow (rounds >= 1) to ones the bound accepts or to the cap, and the result
+    is within eps of the exact values."""
+    from oracle import truncation
+
+    g = gg.tree_plus_gnp(60, 6.0, 5)
+    eps = 0.05
+    r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
+    _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
+    cap = int(truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam).max())
+    s, tau, tt, rounds = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, L0), cap, eps, lam,
+                                                 1.0 / g.n, 10, 11, g.m)
+    assert rounds >= 1 and tau.max() > L0 and np.all(tau % 2 == 1) and np.all(tau <= cap)
+    rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
+    assert np.array_equal(tau, tau[rev])
+    assert np.max(np.abs(s - r)) <= eps
