@@ -205,12 +205,24 @@ def exact_sparse_lu(n, row_ptr, col_idx, pairs, processes: int = 1):
         return _lu_solve_pairs(n, row_ptr, col_idx, pairs)
     import concurrent.futures as cf
     import multiprocessing as mp
+    import os
 
     parts = np.array_split(pairs, processes)
     rp = np.asarray(row_ptr)
     ci = np.asarray(col_idx)
-    with cf.ProcessPoolExecutor(max_workers=processes, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_lu_solve_pairs, [n] * processes, [rp] * processes, [ci] * processes, parts))
+    # one BLAS / OpenMP thread per worker: the workers share the cores
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with cf.ProcessPoolExecutor(max_workers=processes, mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_lu_solve_pairs, [n] * processes, [rp] * processes, [ci] * processes, parts))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return np.concatenate(res)
 
 
@@ -261,3 +273,25 @@ def entry_of_edges(n, row_ptr, col_idx, pairs):
     pos = np.searchsorted(keys, want)
     pos = np.minimum(pos, keys.size - 1)
     return np.where(keys[pos] == want, pos, -1)
+
+
+def reference_values(n, row_ptr, col_idx, dense_max: int = 5000, sample: int = 200, seed: int = 0,
+                     low_fill: bool = False, threads: int = 0):
+    """Exact resistances for checking a graph: every CSR entry by the dense
+    grounded-Laplacian inverse when n <= dense_max, else `sample` uniformly
+    drawn edges (seeded), by sparse LU for low-fill graphs (lattices) or by CG.
+    Returns (entry indices, values)."""
+    if n <= dense_max:
+        return np.arange(len(col_idx), dtype=np.int64), exact_dense(n, row_ptr, col_idx)
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    cols = np.asarray(col_idx, dtype=np.int64)
+    keep = np.flatnonzero(rows < cols)
+    rng = np.random.default_rng(seed)
+    pick_k = np.sort(rng.choice(keep, size=min(sample, keep.size), replace=False))
+    pairs = np.stack([rows[pick_k], cols[pick_k]], axis=1)
+    if low_fill:
+        vals = exact_sparse_lu(n, row_ptr, col_idx, pairs)
+    else:
+        vals = exact_cg(n, row_ptr, col_idx, pairs, threads=threads)
+    return pick_k, vals

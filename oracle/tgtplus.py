@@ -249,7 +249,8 @@ def tgt_plus_learned(n, row_ptr, col_idx, L_src, cap, eps, lam_star, delta, gamm
     the source's switch hop: its traversal reached it); an edge that fails
     takes the least odd tau > tau_e the same bound accepts (at most cap), and
     both endpoints run again. Returns (s_hat per entry, tau per entry, tt per
-    source, rounds with an extension)."""
+    source (its last run), rounds with an extension, (smallest, largest) tt
+    over every run)."""
     from . import series
 
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
@@ -264,10 +265,12 @@ def tgt_plus_learned(n, row_ptr, col_idx, L_src, cap, eps, lam_star, delta, gamm
     tt = np.zeros(n, dtype=np.int64)
     need = list(range(n))
     rounds = 0
+    seen = [None, None]
     for _ in range(max_rounds + 1):
         for i in need:
             a, b = row_ptr[i], row_ptr[i + 1]
             t_i = switch_hop(n, row_ptr, col_idx, i, tau[a:b], eps, delta, gamma, m)
+            seen = [t_i if seen[0] is None else min(seen[0], t_i), t_i if seen[1] is None else max(seen[1], t_i)]
             g_i, _, _ = tgt_plus_half(n, row_ptr, col_idx, i, tau[a:b], t_i, eps, delta, gamma, seed, m)
             half[a:b] = g_i / deg[i]
             tt[i] = t_i
@@ -295,4 +298,4 @@ def tgt_plus_learned(n, row_ptr, col_idx, L_src, cap, eps, lam_star, delta, gamm
             break
         rounds += 1
         need = sorted(redo)
-    return half + half[rev], tau, tt, rounds
+    return half + half[rev], tau, tt, rounds, tuple(seen)

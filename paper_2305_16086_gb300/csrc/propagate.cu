@@ -438,17 +438,11 @@ static void hop_sparse_t(const sc_graph *g, bool ball, const void *xp, void *xn,
     h.t2 = c;
     h.rec = rec;
     h.gather_ctas = gather_ell > 0 ? B : 0;
-    if (ball) {
-        h.heavy_ctas = ceil_div(g->n_heavy, kSpmmWarps);
-        h.light_ctas = ceil_div(g->n, 32 * kSpmmWarps);
-        dim3 grid(h.gather_ctas + h.heavy_ctas + h.light_ctas, slices);
-        k_hop_ball<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
-    } else {
-        h.heavy_ctas = g->n_heavy;
-        h.light_ctas = light_ctas_for(g->n, kSpmmWarps, g->num_sms);  // one light row per warp
-        dim3 grid(h.gather_ctas + g->n_heavy + h.light_ctas, slices);
-        k_hop_sparse<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
-    }
+    h.heavy_ctas = g->n_heavy;
+    h.light_ctas = light_ctas_for(g->n, kSpmmWarps, g->num_sms);  // one light row per warp
+    dim3 grid(h.gather_ctas + g->n_heavy + h.light_ctas, slices);
+    if (ball) k_hop_ball<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
+    else k_hop_sparse<T, B><<<grid, kSpmmWarps * 32, 0, s>>>(h);
 }
 
 template <typename T>

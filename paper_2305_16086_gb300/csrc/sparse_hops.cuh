@@ -180,20 +180,27 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_sparse(const SparseHopA
 // ---------------------------------------------------------------------------
 // Hop L-1 of a block whose last hop L is computed only where its gather reads
 // it (k_last_diag / k_last_rows read X_{L-1} on N(s_b) and on N(N(s_b))):
-// X_{L-1}[y, b] is computed only for y in the ball N(s_b) u N(N(s_b)), i.e.
+// X_{L-1}[y, b] is needed only for y in the ball N(s_b) u N(N(s_b)), i.e.
 // where bit b of ball(y) = mask[y] | OR_{j in N(y)} mask[j] is set (mask =
-// the sources' neighbour bits of the block's hop 2). Nothing is stored
-// elsewhere; no later read leaves the balls. Each value is summed serially by
-// one lane in k_spmm_hop's order; rows of degree above heavy_t take one warp
-// per row (hop_value, chunk sums handed round in order).
-// CTAs [0, gather_ctas): the gather of X_{L-2}; then heavy_ctas CTAs of one
-// heavy row per warp; then light CTAs of 32 consecutive rows per warp, one row
-// per lane.
+// the sources' neighbour bits of the block's hop 2). Nothing outside the
+// balls is read later, so nothing else is stored. One warp per row: the lanes
+// load the neighbours' mask words 32 at a time and OR them across the warp.
+// A row with at most kBallSparseCols marked columns sums each of them over
+// its neighbours (lane t loads neighbour t of a chunk of 32, and the chunk's
+// values are added in CSR order by a shuffle fold); a row with more, or a
+// heavy row (one CTA each), computes all B columns with the full hop's
+// vector loads. Every value is summed in k_spmm_hop's order (chunks of 32 in
+// CSR order, chunk sums in chunk order, one scale), so it is the full hop's.
+// CTAs [0, gather_ctas): the gather of X_{L-2}; then one CTA per heavy row;
+// then light CTAs whose warps stride over the rows.
 // ---------------------------------------------------------------------------
+constexpr int kBallSparseCols = 4;
+
 template <typename T, int B>
 __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_ball(const SparseHopArgs<T> a) {
     using Acc = typename AccOf<T>::type;
-    constexpr int W = B / 32;
+    constexpr int W = B / 32, CPL = B / 32, U = 8;
+    using Vec = LaneVec<T, CPL>;
     if (static_cast<int32_t>(blockIdx.x) < a.gather_ctas) {
         fused_gather<T, B>(a);
         return;
@@ -206,15 +213,9 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_ball(const SparseHopArg
     const uint32_t *__restrict__ m1 = a.mask + static_cast<int64_t>(blockIdx.y) * n * W;
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
-    const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;
-    if (cta < a.heavy_ctas) {
-        // heavy row: ball bits by the warp's lanes over the row, then one
-        // hop_value per marked column
-        const int32_t h = cta * kSpmmWarps + warp;
-        if (h >= a.n_heavy) return;
-        const int32_t y = a.row_order[h];
-        const int32_t rb = row_ptr[y], re = row_ptr[y + 1];
-        uint32_t ball[W];
+    const int lc0 = lane * CPL;
+    // ball bits of row y (every lane of the warp gets them)
+    auto ball_of = [&](int32_t y, int32_t rb, int32_t re, uint32_t *ball) {
         load_words<W>(m1 + static_cast<int64_t>(y) * W, ball);
         for (int32_t k = rb + lane; k < re; k += 32) {
             uint32_t w[W];
@@ -226,52 +227,121 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_ball(const SparseHopArg
         for (int q = 0; q < W; ++q)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ball[q] |= __shfl_xor_sync(0xffffffffu, ball[q], o);
+    };
+    // the lane's CPL columns of entries [k0, k1) added to chunk[] in CSR order
+    auto add_range = [&](int32_t k0, int32_t k1, Acc *chunk) {
+        int32_t k = k0;
+        for (; k + U <= k1; k += U) {
+            int32_t j[U];
+            Vec v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) j[u] = col[k + u];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(j[u]) * B + lc0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v[u].v[c]);
+        }
+        for (; k < k1; ++k) {
+            const Vec v = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(col[k]) * B + lc0);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v.v[c]);
+        }
+    };
+    const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;
+    if (cta < a.n_heavy) {
+        // heavy row: all B columns when the row lies in any ball (chunks over the warps, sums in
+        // chunk order through shared memory)
+        __shared__ Acc part[kSpmmWarps][B];
+        __shared__ int marked;
+        const int32_t row = a.row_order[cta];
+        const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
+        if (threadIdx.x == 0) marked = 0;
+        __syncthreads();
+        {
+            uint32_t any = 0u;
+            for (int32_t k = rb + static_cast<int32_t>(threadIdx.x); k < re; k += kSpmmWarps * 32) {
+                uint32_t w[W];
+                load_words<W>(m1 + static_cast<int64_t>(col[k]) * W, w);
+#pragma unroll
+                for (int q = 0; q < W; ++q) any |= w[q];
+            }
+            if (threadIdx.x < W) any |= m1[static_cast<int64_t>(row) * W + threadIdx.x];
+            if (__any_sync(0xffffffffu, any != 0u) && lane == 0) atomicOr(&marked, 1);
+        }
+        __syncthreads();
+        if (!marked) return;
+        const int32_t nchunks = (re - rb + kChunk - 1) / kChunk;
+        Acc total = Acc(0);  // thread t < B owns column t
+        for (int32_t base = 0; base < nchunks; base += kSpmmWarps) {
+            const int32_t c = base + warp;
+            Acc chunk[CPL];
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) chunk[e] = Acc(0);
+            if (c < nchunks) add_range(rb + c * kChunk, min(rb + (c + 1) * kChunk, re), chunk);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) part[warp][lc0 + e] = chunk[e];
+            __syncthreads();
+            if (threadIdx.x < B) {
+                const int cnt = min(kSpmmWarps, nchunks - base);
+                for (int q = 0; q < cnt; ++q) total += part[q][threadIdx.x];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < B) xn[static_cast<int64_t>(row) * B + threadIdx.x] = from_acc<T>(total * a.inv_deg[row]);
+        return;
+    }
+    if (cta - a.n_heavy >= a.light_ctas) return;
+    const int64_t stride = static_cast<int64_t>(a.light_ctas) * kSpmmWarps;
+    const int32_t heavy_t = a.n_heavy > 0 ? a.heavy_t : 0x7fffffff;
+    for (int64_t idx = static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp; idx < n; idx += stride) {
+        const int32_t y = static_cast<int32_t>(idx);
+        const int32_t rb = row_ptr[y], re = row_ptr[y + 1];
+        if (re - rb > heavy_t) continue;  // a heavy row: its own CTA computes it
+        uint32_t ball[W];
+        ball_of(y, rb, re, ball);
+        int marked = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) marked += __popc(ball[q]);
+        if (marked == 0) continue;
+        const Acc sc = a.inv_deg[y];
+        if (marked > kBallSparseCols) {
+            // every column, the full hop's way
+            Acc acc[CPL], chunk[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) acc[c] = Acc(0);
+            for (int32_t k0 = rb; k0 < re; k0 += kChunk) {
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) chunk[c] = Acc(0);
+                add_range(k0, min(k0 + kChunk, re), chunk);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] += chunk[c];
+            }
+            Vec out;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) out.v[c] = from_acc<T>(acc[c] * sc);
+            *reinterpret_cast<Vec *>(xn + static_cast<int64_t>(y) * B + lc0) = out;
+            continue;
+        }
+        // the marked columns one by one: lane t loads neighbour t of each chunk, a shuffle fold
+        // adds the chunk in CSR order
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             uint32_t bits = ball[q];
-            while (bits) {
+            while (bits) {  // warp-uniform
                 const int b = q * 32 + __ffs(bits) - 1;
                 bits &= bits - 1u;
-                const double v = hop_value<T, B>(row_ptr, col, a.inv_deg, xp + b, 0, y, lane);
-                if (lane == 0) xn[static_cast<int64_t>(y) * B + b] = from_acc<T>(static_cast<Acc>(v));
-            }
-        }
-        return;
-    }
-    // light rows: lane = row
-    const int64_t y64 = (static_cast<int64_t>(cta - a.heavy_ctas) * kSpmmWarps + warp) * 32 + lane;
-    if (y64 >= n) return;
-    const int32_t y = static_cast<int32_t>(y64);
-    const int32_t rb = row_ptr[y], re = row_ptr[y + 1];
-    const int32_t heavy_t = a.n_heavy > 0 ? a.heavy_t : 0x7fffffff;
-    if (re - rb > heavy_t) return;
-    uint32_t ball[W];
-    load_words<W>(m1 + static_cast<int64_t>(y) * W, ball);
-    for (int32_t k = rb; k < re; ++k) {
-        uint32_t w[W];
-        load_words<W>(m1 + static_cast<int64_t>(col[k]) * W, w);
-#pragma unroll
-        for (int q = 0; q < W; ++q) ball[q] |= w[q];
-    }
-    const Acc sc = a.inv_deg[y];
-#pragma unroll
-    for (int q = 0; q < W; ++q) {
-        uint32_t bits = ball[q];
-        while (bits) {
-            const int b = q * 32 + __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const T *xb = xp + b;
-            Acc acc = Acc(0), chunk = Acc(0);
-            int32_t k = rb;
-            for (; k < re; ++k) {
-                chunk += to_acc(xb[static_cast<int64_t>(col[k]) * B]);
-                if (((k - rb + 1) % kChunk) == 0) {
+                Acc acc = Acc(0);
+                for (int32_t k0 = rb; k0 < re; k0 += kChunk) {
+                    const int cnt = min(kChunk, re - k0);
+                    const Acc x = lane < cnt ? to_acc(xp[static_cast<int64_t>(col[k0 + lane]) * B + b]) : Acc(0);
+                    Acc chunk = Acc(0);
+                    for (int t = 0; t < cnt; ++t) chunk += __shfl_sync(0xffffffffu, x, t);
                     acc += chunk;
-                    chunk = Acc(0);
                 }
+                if (lane == 0) xn[static_cast<int64_t>(y) * B + b] = from_acc<T>(acc * sc);
             }
-            acc += chunk;
-            xn[static_cast<int64_t>(y) * B + b] = from_acc<T>(acc * sc);
         }
     }
 }

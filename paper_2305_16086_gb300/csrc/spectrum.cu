@@ -99,9 +99,12 @@ __global__ void k_spmv_norm(const int32_t *__restrict__ row_ptr, const int32_t *
     if (lane == 0) y[r] = isd[r] * acc;
 }
 
-// partial[q * kDotBlocks + b] = block b's share of <V_q, w>, for q < nvec
+// partial[q * kDotBlocks + b] = block b's share of <V_q, w>, for q < nvec.
+// skip (nullable): when *skip != 0 the launch does nothing (a pass the device
+// decided against).
 __global__ void k_multidot_partial(const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
-                                   int32_t n, double *__restrict__ partial) {
+                                   int32_t n, double *__restrict__ partial, const int *__restrict__ skip = nullptr) {
+    if (skip && *skip) return;
     __shared__ double sh[kDotThreads];
     const int q = blockIdx.y;
     const double *v = V + q * ldv;
@@ -117,10 +120,15 @@ __global__ void k_multidot_partial(const double *__restrict__ V, int64_t ldv, in
     if (threadIdx.x == 0) partial[q * kDotBlocks + blockIdx.x] = sh[0];
 }
 
-// out[q] = sum of the kDotBlocks partials of row q (fixed tree)
-__global__ void k_multidot_final(const double *__restrict__ partial, double *__restrict__ out) {
+// out[q] = sum of the kDotBlocks partials of row q (fixed tree); 0 when *skip
+__global__ void k_multidot_final(const double *__restrict__ partial, double *__restrict__ out,
+                                 const int *__restrict__ skip = nullptr) {
     __shared__ double sh[kDotBlocks];
     const int q = blockIdx.x;
+    if (skip && *skip) {
+        if (threadIdx.x == 0) out[q] = 0.0;
+        return;
+    }
     sh[threadIdx.x] = partial[q * kDotBlocks + threadIdx.x];
     __syncthreads();
     for (int s = kDotBlocks / 2; s > 0; s >>= 1) {
@@ -130,9 +138,10 @@ __global__ void k_multidot_final(const double *__restrict__ partial, double *__r
     if (threadIdx.x == 0) out[q] = sh[0];
 }
 
-// w -= sum_q c[q] V_q (q in order)
+// w -= sum_q c[q] V_q (q in order); nothing when *skip
 __global__ void k_sub_combination(const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ c,
-                                  double *__restrict__ w, int32_t n) {
+                                  double *__restrict__ w, int32_t n, const int *__restrict__ skip = nullptr) {
+    if (skip && *skip) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double acc = w[i];
@@ -151,6 +160,32 @@ __global__ void k_scale_into(const double *__restrict__ src, const double *__res
 // alpha of a Lanczos step: the coefficients of V_vj in the two orthogonalisation passes, summed
 __global__ void k_alpha_of(const double *__restrict__ c, int nbasis, int vj, double *__restrict__ alpha) {
     *alpha = c[vj] + c[nbasis + vj];
+}
+
+// The three-term part of a Lanczos step: w -= a V_vj + beta V_vj-1, with a =
+// <w, V_vj> (from the device) and beta = sqrt(|w_prev|^2) (nrm2_prev null:
+// no previous Lanczos vector, the first step)
+__global__ void k_three_term(const double *__restrict__ V, int64_t ldv, int vj, const double *__restrict__ a,
+                             const double *__restrict__ nrm2_prev, double *__restrict__ w, int32_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i] - *a * V[vj * ldv + i];
+    if (nrm2_prev) acc -= sqrt(*nrm2_prev) * V[(vj - 1) * ldv + i];
+    w[i] = acc;
+}
+
+// skip the second sweep unless the first removed more than half of |w|^2
+// ("twice is enough": one more sweep restores orthogonality to working
+// precision when the first lost most of the vector)
+__global__ void k_second_sweep_flag(const double *__restrict__ nrm2_before, const double *__restrict__ nrm2_after,
+                                    int *__restrict__ skip) {
+    *skip = (*nrm2_after < 0.5 * *nrm2_before) ? 0 : 1;
+}
+
+// alpha of a step with the three-term part: its coefficient plus the sweeps' coefficients of V_vj
+__global__ void k_alpha_three(const double *__restrict__ a, const double *__restrict__ c, int nbasis, int vj,
+                              double *__restrict__ alpha) {
+    *alpha = *a + c[vj] + c[nbasis + vj];
 }
 
 // locked vectors: sqrt(d_x)/sqrt(2m), and (bipartite) the same with sign (-1)^level
@@ -304,6 +339,40 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
             k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), dst);
             SC_LAUNCH_CHECK();
         };
+        // A Lanczos step's orthogonalisation: the three-term recurrence first (w -= a V_vj +
+        // beta V_vj-1), then one classical Gram-Schmidt sweep against the whole basis, and a
+        // second sweep only when the first removed more than half of |w|^2 (decided on the
+        // device: the skipped sweep's launches return at once and its coefficients are 0). In
+        // exact arithmetic the recurrence leaves w orthogonal to the basis; the sweep removes
+        // what rounding left, so the second sweep is rarely needed and a step costs about
+        // half the FP64 work of two full sweeps.
+        double *d_scal = nullptr;  // [0] a, [1] |w|^2 before the sweep, [2] after it
+        DevBuf<double> scal;
+        DevBuf<int> skip;
+        scal.reserve(4);
+        skip.reserve(1);
+        d_scal = scal.get();
+        auto step_orth = [&](int vj, const double *nrm2_prev) {
+            k_multidot_partial<<<dim3(kDotBlocks, 1), kDotThreads, 0, s>>>(V.get() + vj * ldv, ldv, 1, w.get(), n,
+                                                                          partial.get());
+            k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), d_scal);
+            k_three_term<<<nb, tb, 0, s>>>(V.get(), ldv, vj, d_scal, nrm2_prev, w.get(), n);
+            SC_LAUNCH_CHECK();
+            norm2_into(d_scal + 1);
+            const int nv = vj + 1;
+            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
+            k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), c.get());
+            k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, c.get(), w.get(), n);
+            SC_LAUNCH_CHECK();
+            norm2_into(d_scal + 2);
+            k_second_sweep_flag<<<1, 1, 0, s>>>(d_scal + 1, d_scal + 2, skip.get());
+            double *c2 = c.get() + nbasis;
+            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get(),
+                                                                           skip.get());
+            k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), c2, skip.get());
+            k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, c2, w.get(), n, skip.get());
+            SC_LAUNCH_CHECK();
+        };
 
         // start vector
         k_start_vector<<<nb, tb, 0, s>>>(w.get(), n, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
@@ -332,8 +401,8 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
             k_spmv_norm<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), isd.get(),
                                                         V.get() + vj * ldv, w.get(), n);
             SC_LAUNCH_CHECK();
-            reorth(vj + 1);
-            k_alpha_of<<<1, 1, 0, s>>>(c.get(), nbasis, vj, d_alpha + j);  // both passes' coefficient of V_vj
+            step_orth(vj, j > 0 ? d_nrm2 + (j - 1) : nullptr);
+            k_alpha_three<<<1, 1, 0, s>>>(d_scal, c.get(), nbasis, vj, d_alpha + j);
             norm2_into(d_nrm2 + j);
             const int kk = j + 1;
             if (kk == max_iter || kk == n - nlock || (kk >= 8 && kk % 4 == 0)) {

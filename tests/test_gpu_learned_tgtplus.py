@@ -50,11 +50,11 @@ def test_matches_the_oracle_walk_for_walk(cuda_lib, L0, seed):
         assert np.all(binding.mlp_predict(G, cap) == L0)
         s, _, rep = G.all_edges(eps=eps, mode="tgt_plus", policy="learned", precision="fp64", switch="per_source",
                                 seed=seed)
-    ref, tau, tt, rounds = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, L0), cap, eps, ls,
-                                                   1.0 / g.n, 10, seed, g.m)
-    assert rounds >= 1 and rep["extension_rounds"] == rounds
-    assert (rep["tt_min"], rep["tt_max"]) == (int(tt.min()), int(tt.max()))
+    ref, tau, tt, rounds, seen = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, L0), cap, eps, ls,
+                                                         1.0 / g.n, 10, seed, g.m)
     assert np.max(np.abs(s - ref)) < 1e-10
+    assert rounds >= 1 and rep["extension_rounds"] == rounds
+    assert (rep["tt_min"], rep["tt_max"]) == seen  # over every run, reruns included
     assert np.max(np.abs(s - exact.exact_dense(g.n, g.row_ptr, g.col_idx))) <= eps
 
 

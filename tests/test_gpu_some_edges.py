@@ -68,7 +68,7 @@ def test_windowed_lattice_and_device_output(cuda_lib):
     ent = _pick(g, 150, 3)
     out = torch.empty(ent.size, dtype=torch.float64, device="cuda")
     with _graph(g) as G:
-        kw = dict(policy="fixed", ell_fixed=31, precision="fp64", estimator="end_corrected")
+        kw = dict(policy="fixed", ell_fixed=31, precision="fp64", estimator="end_corrected", windows=True)
         full, _, rf = G.all_edges(**kw)
         binding.some_edges(G, ent, out=out, **kw)
         _, rp = binding.some_edges(G, ent, **kw)

@@ -244,32 +244,3 @@ def test_global_policy_rejects_bipartite(cuda_lib):
         with pytest.raises(ScError) as ei:
             G.all_edges(policy="global")
     assert ei.value.name == "SC_ERR_UNSUPPORTED"
-
-
-@pytest.mark.slow
-def test_config_ba_200k_sampled(cuda_lib):
-    """Barabasi-Albert n = 200,000, 10 edges per node, FP32 blocks, FP64
-    accumulation, eps = 1e-3, global length: sampled edges vs CG (exact) and
-    vs the series oracle at the same length, in the bench's configuration."""
-    g = gg.barabasi_albert(200_000, 10, 1)
-    rng = np.random.default_rng(0)
-    e = g.edges()
-    pick = e[rng.choice(e.shape[0], size=160, replace=False)]
-    k = exact.entry_of_edges(g.n, g.row_ptr, g.col_idx, pick)
-    with _graph(cuda_lib, g) as G:
-        lam = G.estimate_lambda()
-        s, _, rep = G.all_edges(eps=1e-3, policy="global", precision="fp32")
-    r = exact.exact_cg(g.n, g.row_ptr, g.col_idx, pick)
-    assert np.max(np.abs(s[k] - r)) <= 1e-3
-    srcs = series.sources_for_pairs(pick[:40])
-    ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, rep["ell_global"], sources=srcs)
-    k40 = k[:40]
-    assert np.max(np.abs(s[k40] - ref[k40])) < TOL32
-    # Foster: the mean error over all edges, exactly (each edge is a lower bound)
-    mean_err = ((g.n - 1) - rep["foster_sum"]) / g.m
-    assert 0 <= mean_err <= 1e-3
-    lp, lm, _ = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
-    # Ritz values approach the extremes from inside; the residual is the margin added to lambda_star
-    assert lp - lam["residual_plus"] <= lam["lambda_plus"] <= lp + 1e-10
-    assert lm - 1e-10 <= lam["lambda_minus"] <= lm + lam["residual_minus"]
-    assert lam["lambda_star"] >= max(abs(lp), abs(lm))

@@ -175,3 +175,15 @@ def test_sparse_lu_worker_processes_give_the_single_process_values():
     one = exact.exact_sparse_lu(g.n, g.row_ptr, g.col_idx, pick)
     two = exact.exact_sparse_lu(g.n, g.row_ptr, g.col_idx, pick, processes=3)
     assert np.array_equal(one, two)
+
+
+def test_reference_values_dense_and_sampled_agree():
+    g = gg.barabasi_albert(600, 3, 4)
+    k_all, dense = exact.reference_values(g.n, g.row_ptr, g.col_idx)
+    assert k_all.size == g.nnz
+    k, cg = exact.reference_values(g.n, g.row_ptr, g.col_idx, dense_max=100, sample=50, seed=3)
+    assert k.size == 50 and np.all(g.entry_rows()[k] < g.col_idx[k])
+    assert np.max(np.abs(cg - dense[k])) < 1e-10
+    grid = gg.perturbed_grid(15, 16, 0.05, 2)
+    kg, lu = exact.reference_values(grid.n, grid.row_ptr, grid.col_idx, dense_max=10, sample=30, seed=1, low_fill=True)
+    assert np.max(np.abs(lu - exact.exact_dense(grid.n, grid.row_ptr, grid.col_idx)[kg])) < 1e-10

@@ -296,8 +296,8 @@ def test_learned_tgt_plus_at_the_cap_is_per_source_tgt_plus():
     eps = 0.05
     _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
     cap = int(truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam).max())
-    s, tau, tt, rounds = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, cap), cap, eps, lam,
-                                                 1.0 / g.n, 10, 5, g.m)
+    s, tau, tt, rounds, _ = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, cap), cap, eps, lam,
+                                                    1.0 / g.n, 10, 5, g.m)
     assert rounds == 0 and np.all(tau == cap)
     ghat = np.zeros(g.nnz)
     for i in range(g.n):
@@ -321,8 +321,8 @@ def test_learned_tgt_plus_extends_short_lengths_and_meets_eps(L0):
     r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
     _, _, lam = truncation.spectrum_extremes(g.n, g.row_ptr, g.col_idx)
     cap = int(truncation.tau_entries(g.n, g.row_ptr, g.col_idx, eps / 2, lam).max())
-    s, tau, tt, rounds = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, L0), cap, eps, lam,
-                                                 1.0 / g.n, 10, 11, g.m)
+    s, tau, tt, rounds, _ = tgtplus.tgt_plus_learned(g.n, g.row_ptr, g.col_idx, np.full(g.n, L0), cap, eps, lam,
+                                                    1.0 / g.n, 10, 11, g.m)
     assert rounds >= 1 and tau.max() > L0 and np.all(tau % 2 == 1) and np.all(tau <= cap)
     rev = series.reverse_entries(g.n, g.row_ptr, g.col_idx)
     assert np.array_equal(tau, tau[rev])
