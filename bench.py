@@ -47,7 +47,15 @@ WORKLOADS = {
     "lattice_1000": dict(desc="1000x1000 lattice, 5% of edges deleted outside a random spanning tree, seed 2 "
                               "(bipartite, bandwidth 1000)",
                          make=lambda gg: gg.perturbed_grid(1000, 1000, 0.05, 2)),
+    "rmat_22": dict(desc="R-MAT scale 22, (a,b,c,d) = (.57,.19,.19,.05), edge factor 16, symmetrised, largest "
+                         "component (n = 2,394,610, m = 64,153,249), seed 5",
+                    make=lambda gg: gg.rmat(22)),
 }
+# the graph each workload's learned-length model is trained on (same family, another seed)
+TRAIN_GRAPHS = {
+    "rmat_22": ("R-MAT scale 16 seed 15", lambda gg: gg.rmat(16, seed=15)),
+}
+DEFAULT_TRAIN = ("Barabasi-Albert n=50000 m0=10 seed 101", lambda gg: gg.barabasi_albert(50_000, 10, 101))
 KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh", "paper_2305_16086_gb300/csrc/hop2_mask.cuh",
                   "paper_2305_16086_gb300/csrc/sparse_hops.cuh"]
 # kernel classes the library times separately (SC_KC_* order) and their kernels
@@ -195,13 +203,13 @@ def exact_check(g, s_hat, edges: int, seed: int = 2024):
             "oracle_cores": _native.default_threads(), "sample_seed": seed}
 
 
-def train_model(eps, stream):
+def train_model(eps, stream, workload="ba_200k"):
     """The MLP for the learned length, trained on the GPU on a separate graph of
     the same family (untimed preprocessing)."""
     import graphgen as gg
     from paper_2305_16086_gb300 import Graph, binding
 
-    tg = gg.barabasi_albert(50_000, 10, 101)
+    tg = TRAIN_GRAPHS.get(workload, DEFAULT_TRAIN)[1](gg)
     with Graph(tg.row_ptr, tg.col_idx, stream=stream) as Gt:
         Gt.estimate_lambda()
         init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
@@ -426,10 +434,13 @@ def parse_args(argv=None):
                     help="also time CalTau with device eigenpairs (Algorithm 1) on a planted partition, n=200000")
     ap.add_argument("--caltau-omega", type=int, default=64)
     ap.add_argument("--mode", default="tgt", choices=["tgt", "tgt_plus"],
-                    help="tgt: Algorithm 2; tgt_plus: Algorithm 4 (with --policy global, per_edge or fixed)")
+                    help="tgt: Algorithm 2; tgt_plus: Algorithm 4")
+    ap.add_argument("--explicit-config", action="store_true",
+                    help="keep --mode / --policy / --precision as given for the rmat_22 workload")
     args = ap.parse_args(argv)
-    if args.mode == "tgt_plus" and args.policy == "learned":
-        ap.error("--mode tgt_plus takes --policy global, per_edge or fixed (TGT+ sets its own lengths, Eq. 6 at eps/2)")
+    if args.workload == "rmat_22" and not args.explicit_config:
+        # the R-MAT workload's configuration: TGT+ walks, learned lengths, BF16 storage from hop 8
+        args.mode, args.policy, args.precision = "tgt_plus", "learned", "bf16"
     return args
 
 
@@ -469,7 +480,8 @@ def main():
     lam = G.estimate_lambda()
     model = None
     if args.policy == "learned":
-        model = train_model(args.eps, stream)
+        # TGT+ certifies its truncation with eps / 2 (Algorithm 4's split): labels at eps / 2
+        model = train_model(args.eps / 2 if args.mode == "tgt_plus" else args.eps, stream, args.workload)
         binding.mlp_load(G, model)
     out = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2: evict between steps
@@ -624,7 +636,7 @@ def main():
         "roofline": roofline, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e, "arms": arms,
         "learned": {"source_hops": rep0["source_hops"], "extension_rounds": rep0["extension_rounds"],
                     "edges_extended": rep0["edges_extended"], "max_tail_bound": rep0["max_tail_bound"],
-                    "model": "trained on Barabasi-Albert n=50000 m0=10 seed 101, 400 Adam steps"}
+                    "model": f"trained on {TRAIN_GRAPHS.get(args.workload, DEFAULT_TRAIN)[0]}, 400 Adam steps"}
         if args.policy == "learned" else None,
         "tgt_plus": {"switch_after_hops": [rep0["tt_min"], rep0["tt_max"]], "walk_pairs": rep0["walks"],
                      "walk_steps": rep0["walk_steps"], "switch_tests": rep0["switch_tests"],

@@ -233,11 +233,24 @@ __global__ void __launch_bounds__(kChiScanThreads)
     const T *xs = x + static_cast<int64_t>(blockIdx.y) * n * B;
     V vmax = V(-INFINITY), vmin = V(INFINITY);
     long long vol = 0;
-    for (int32_t r = r0 + sub; r < r1; r += TPC) {
-        const V v = to_acc(xs[static_cast<int64_t>(r) * B + c]);
-        vmax = max(vmax, v);
-        vmin = min(vmin, v);
-        if (v != V(0)) vol += row_ptr[r + 1] - row_ptr[r];
+    constexpr int UR = 8;  // rows whose loads are in flight together
+    for (int32_t rb = r0 + sub; rb < r1; rb += TPC * UR) {
+        V v[UR];
+        int32_t d[UR];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int32_t r = rb + u * TPC;
+            v[u] = r < r1 ? to_acc(xs[static_cast<int64_t>(r) * B + c]) : V(0);
+            d[u] = r < r1 ? row_ptr[r + 1] - row_ptr[r] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            if (rb + u * TPC < r1) {
+                vmax = max(vmax, v[u]);
+                vmin = min(vmin, v[u]);
+                if (v[u] != V(0)) vol += d[u];
+            }
+        }
     }
     __shared__ double smax[kChiScanThreads], smin[kChiScanThreads];
     __shared__ long long svol[kChiScanThreads];
@@ -343,24 +356,38 @@ __global__ void __launch_bounds__(kChiScanThreads)
     __shared__ int32_t si[kGammaMax * NT];
     if (t == 0) ncand = 0;
     __syncthreads();
-    // candidates: each warp takes tiles in turn, 32 rows at a time
-    for (int p = warp; p < ntiles; p += NW) {
-        const double tm = tmax[(static_cast<int64_t>(slice) * ntiles + p) * B + c];
-        if (zero_thr ? !(tm > 0.0) : !(tm >= thr)) continue;
-        const int32_t r0 = p * kTileRows, r1 = min(n, r0 + kTileRows);
-        for (int32_t rb = r0; rb < r1; rb += 32) {
-            const int32_t r = rb + lane;
-            const double v = r < r1 ? static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B])) : -1.0;
-            const bool take = zero_thr ? (v > 0.0) : (v >= thr);
-            const uint32_t bal = __ballot_sync(0xffffffffu, take);
-            int base = 0;
-            if (lane == 0 && bal) base = atomicAdd(&ncand, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-                const int slot = base + __popc(bal & ((1u << lane) - 1u));
-                if (slot < kCandMax) {
-                    cand_v[slot] = v;
-                    cand_i[slot] = r;
+    // candidates: each warp tests 32 tile maxima at once, then takes the tiles that reach thr
+    // one by one, 32 rows at a time
+    for (int pb = warp * 32; pb < ntiles; pb += NW * 32) {
+        const int pl = pb + lane;
+        const double tml = pl < ntiles ? tmax[(static_cast<int64_t>(slice) * ntiles + pl) * B + c] : -1.0;
+        uint32_t tiles = __ballot_sync(0xffffffffu, zero_thr ? (tml > 0.0) : (tml >= thr));
+        while (tiles) {  // warp-uniform
+            const int p = pb + __ffs(tiles) - 1;
+            tiles &= tiles - 1u;
+            const int32_t r0 = p * kTileRows, r1 = min(n, r0 + kTileRows);
+            constexpr int RR = kTileRows / 32;  // the tile's rows, 32 per round, loaded together
+            double vals[RR];
+#pragma unroll
+            for (int u = 0; u < RR; ++u) {
+                const int32_t r = r0 + u * 32 + lane;
+                vals[u] = r < r1 ? static_cast<double>(to_acc(xs[static_cast<int64_t>(r) * B])) : -1.0;
+            }
+#pragma unroll
+            for (int u = 0; u < RR; ++u) {
+                const int32_t r = r0 + u * 32 + lane;
+                const double v = vals[u];
+                const bool take = zero_thr ? (v > 0.0) : (v >= thr);
+                const uint32_t bal = __ballot_sync(0xffffffffu, take);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&ncand, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (take) {
+                    const int slot = base + __popc(bal & ((1u << lane) - 1u));
+                    if (slot < kCandMax) {
+                        cand_v[slot] = v;
+                        cand_i[slot] = r;
+                    }
                 }
             }
         }
