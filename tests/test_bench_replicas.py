@@ -82,8 +82,12 @@ def test_arguments_default_and_tgt_plus_mode():
     assert a.warmup >= 3
     a = bench.parse_args(["--mode", "tgt_plus", "--policy", "global"])
     assert (a.mode, a.policy) == ("tgt_plus", "global")
-    with pytest.raises(SystemExit):
-        bench.parse_args(["--mode", "tgt_plus"])  # TGT+ sets its own lengths: no learned policy
+    a = bench.parse_args(["--mode", "tgt_plus"])  # TGT+ at learned lengths (the composite path)
+    assert (a.mode, a.policy) == ("tgt_plus", "learned")
+    a = bench.parse_args(["--workload", "rmat_22"])  # the R-MAT workload's own configuration
+    assert (a.mode, a.policy, a.precision) == ("tgt_plus", "learned", "bf16")
+    a = bench.parse_args(["--workload", "rmat_22", "--explicit-config", "--mode", "tgt", "--policy", "global"])
+    assert (a.mode, a.policy, a.precision) == ("tgt", "global", "fp32")
 
 
 def test_timed_passes_split_only_the_warmups():
