@@ -313,9 +313,10 @@ sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
 /* Unwindowed TGT blocks compute hop 3 from the non-zero values of X_2 only,
    and hop L-1 only on the sources' two-hop balls, where the last hop reads it
    (Algorithm 2's frontier, which visits only nodes it reaches); the values are
-   those of full hops bit for bit. This flag runs every hop between the second
-   and the last as a full hop instead (for comparison). */
-#define SC_OPT_DENSE_HOPS 32u
+   those of full hops bit for bit. Off by default: on the power-law graphs
+   measured the hop is bound by the latency of its dependent loads per row, not
+   by the bytes it moves, and the full hop was as fast or faster. */
+#define SC_OPT_SPARSE_HOPS 32u
 /* TGT+ switch tests find each column's gamma largest entries (Algorithm 3's
    candidates) from the entries at or above the gamma-th largest maximum of its
    256-row tiles; this flag scans every row of the column instead (the same

@@ -29,7 +29,7 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 EST = {"plain": 0, "end_corrected": 1}
 MODE = {"tgt": 0, "tgt_plus": 1}
 SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
-SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE, SC_OPT_DENSE_HOPS, SC_OPT_FULL_TOPGAMMA_SCAN = 8, 16, 32, 64
+SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE, SC_OPT_SPARSE_HOPS, SC_OPT_FULL_TOPGAMMA_SCAN = 8, 16, 32, 64
 KC_NAMES = ["dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop"]  # SC_KC_* order
 
 # every symbol include/sc.h declares
@@ -338,7 +338,7 @@ class Graph:
     def options(eps=1e-3, mode="tgt", precision="fp32", policy="global", ell_fixed=0,
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
                 record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
-                switch="cost", windows=None, bf16_from_hop=0, dense_hops=False,
+                switch="cost", windows=None, bf16_from_hop=0, sparse_hops=False,
                 full_topgamma_scan=False) -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
@@ -355,8 +355,8 @@ class Graph:
         o.flags = (SC_OPT_RECORD_TAIL if record_tail else 0) | (SC_OPT_TIME_KERNELS if time_kernels else 0)
         if windows is not None:  # None: automatic; True / False: force on / off
             o.flags |= SC_OPT_WINDOWS_FORCE if windows else SC_OPT_WINDOWS_OFF
-        if dense_hops:
-            o.flags |= SC_OPT_DENSE_HOPS
+        if sparse_hops:
+            o.flags |= SC_OPT_SPARSE_HOPS
         if full_topgamma_scan:
             o.flags |= SC_OPT_FULL_TOPGAMMA_SCAN
         if seed is not None:

@@ -911,7 +911,7 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
     auto hop_bytes_per_slice = [&](int32_t ell) {
         return csr_bytes + static_cast<double>(n) * B * (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
     };
-    const bool dense_only = (R.o->flags & SC_OPT_DENSE_HOPS) != 0;
+    const bool dense_only = (R.o->flags & SC_OPT_SPARSE_HOPS) == 0;
     const bool full_scan = (R.o->flags & SC_OPT_FULL_TOPGAMMA_SCAN) != 0;
     for (int64_t sb = 0; sb < nsuper; ++sb) {
         const int64_t first = sb * S;

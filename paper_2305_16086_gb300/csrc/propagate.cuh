@@ -280,23 +280,26 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
             if (c < nchunks) {
                 const int32_t kb = rb + c * kChunk;
                 const int32_t ke = min(kb + kChunk, re);
-                // groups of U neighbours with every load in flight together; the last group is
-                // predicated (a missing neighbour adds a zero, which changes no sum)
-                for (int32_t k = kb; k < ke; k += L::U) {
+                int32_t k = kb;
+                for (; k + L::U <= ke; k += L::U) {
                     int32_t j[L::U];
 #pragma unroll
-                    for (int u = 0; u < L::U; ++u) j[u] = k + u < ke ? col[k + u] : -1;
+                    for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
                     uint4 v[L::U][VPL];
 #pragma unroll
                     for (int u = 0; u < L::U; ++u)
 #pragma unroll
-                        for (int p = 0; p < VPL; ++p)
-                            v[u][p] = j[u] >= 0 ? ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG)
-                                                : make_uint4(0u, 0u, 0u, 0u);
+                        for (int p = 0; p < VPL; ++p) v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
 #pragma unroll
                     for (int u = 0; u < L::U; ++u)
 #pragma unroll
                         for (int p = 0; p < VPL; ++p) vadd(acc + p * L::E, v[u][p], T());
+                }
+                for (; k < ke; ++k) {
+                    const int32_t j = col[k];
+#pragma unroll
+                    for (int p = 0; p < VPL; ++p)
+                        vadd(acc + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
                 }
             }
 #pragma unroll
@@ -350,19 +353,17 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
             acc[q] = Acc(0);
             chunk[q] = Acc(0);
         }
-        // groups of U neighbours with every load in flight together; the last group is
-        // predicated (a missing neighbour adds a zero, which changes no sum)
-        for (int32_t k = cb; k < ce; k += L::U) {
+        int32_t k = cb;
+        for (; k + L::U <= ce; k += L::U) {
             int32_t j[L::U];
 #pragma unroll
-            for (int u = 0; u < L::U; ++u) j[u] = k + u < ce ? col[k + u] : -1;
+            for (int u = 0; u < L::U; ++u) j[u] = col[k + u];
             uint4 v[L::U][VPL];
 #pragma unroll
             for (int u = 0; u < L::U; ++u)
 #pragma unroll
                 for (int p = 0; p < VPL; ++p)
-                    v[u][p] = j[u] >= 0 ? ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG)
-                                        : make_uint4(0u, 0u, 0u, 0u);
+                    v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
 #pragma unroll
             for (int u = 0; u < L::U; ++u)
 #pragma unroll
@@ -374,6 +375,12 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
                     chunk[q] = Acc(0);
                 }
             }
+        }
+        for (; k < ce; ++k) {
+            const int32_t j = col[k];
+#pragma unroll
+            for (int p = 0; p < VPL; ++p)
+                vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
         }
 #pragma unroll
         for (int q = 0; q < L::NACC; ++q) acc[q] += chunk[q];

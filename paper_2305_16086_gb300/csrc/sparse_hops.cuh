@@ -94,17 +94,16 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_sparse(const SparseHopA
     const int lc0 = lane * CPL, lw = lc0 / 32;
     const uint32_t lmask = (CPL == 32 ? 0xffffffffu : ((1u << CPL) - 1u)) << (lc0 % 32);
     // entries [k0, k1) of a row added to chunk[] in CSR order
-    // (groups of U with every load in flight together, the last group predicated: a missing or
-    // unmarked neighbour adds zeros)
     auto add_range = [&](int32_t k0, int32_t k1, Acc *chunk) {
-        for (int32_t k = k0; k < k1; k += U) {
+        int32_t k = k0;
+        for (; k + U <= k1; k += U) {
             int32_t j[U];
             uint32_t w[U];
             Vec v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) j[u] = k + u < k1 ? col[k + u] : -1;
+            for (int u = 0; u < U; ++u) j[u] = col[k + u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) w[u] = j[u] >= 0 ? __ldg(nz + static_cast<int64_t>(j[u]) * W + lw) : 0u;
+            for (int u = 0; u < U; ++u) w[u] = __ldg(nz + static_cast<int64_t>(j[u]) * W + lw);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (w[u] & lmask) {
@@ -118,6 +117,14 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_sparse(const SparseHopA
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v[u].v[c]);
+        }
+        for (; k < k1; ++k) {
+            const int32_t j = col[k];
+            if (__ldg(nz + static_cast<int64_t>(j) * W + lw) & lmask) {
+                const Vec v = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(j) * B + lc0);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v.v[c]);
+            }
         }
     };
     const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;
@@ -223,24 +230,23 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop_ball(const SparseHopArg
     };
     // the lane's CPL columns of entries [k0, k1) added to chunk[] in CSR order
     auto add_range = [&](int32_t k0, int32_t k1, Acc *chunk) {
-        for (int32_t k = k0; k < k1; k += U) {
+        int32_t k = k0;
+        for (; k + U <= k1; k += U) {
             int32_t j[U];
             Vec v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) j[u] = k + u < k1 ? col[k + u] : -1;
+            for (int u = 0; u < U; ++u) j[u] = col[k + u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j[u] >= 0) {
-                    v[u] = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(j[u]) * B + lc0);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c) v[u].v[c] = from_acc<T>(Acc(0));
-                }
-            }
+            for (int u = 0; u < U; ++u) v[u] = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(j[u]) * B + lc0);
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v[u].v[c]);
+        }
+        for (; k < k1; ++k) {
+            const Vec v = *reinterpret_cast<const Vec *>(xp + static_cast<int64_t>(col[k]) * B + lc0);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) chunk[c] += to_acc(v.v[c]);
         }
     };
     const int32_t cta = static_cast<int32_t>(blockIdx.x) - a.gather_ctas;

@@ -273,10 +273,13 @@ __global__ void __launch_bounds__(kChiScanThreads)
     }
 }
 
-// per column q = slice * B + b: thr = the gamma-th largest tile maximum (ties
-// counted), min, max and volume. One CTA per column; the top kGammaMax tile
-// maxima by the merge tree of the full scan (value descending, tile id
-// ascending).
+// per column q = slice * B + b: thr, min, max and volume. One CTA per
+// column; thread t takes tiles t, t + 128, ... and keeps their largest
+// maximum. thr = the gamma-th largest of those 128 maxima (0 if fewer than
+// gamma are positive): they are maxima of distinct tiles, so at least gamma
+// tiles reach thr, every top-gamma entry is >= thr, and thr is at most the
+// gamma-th largest tile maximum (a few more candidate tiles than that, no
+// merge of sorted lists).
 template <int B>
 __global__ void __launch_bounds__(kChiScanThreads)
     k_chi_thresh(int ntiles, int ncols, int gamma, const double *__restrict__ tmax, const double *__restrict__ tmin,
@@ -286,50 +289,37 @@ __global__ void __launch_bounds__(kChiScanThreads)
     if (q >= ncols) return;
     const int slice = q / B, c = q % B, t = threadIdx.x;
     constexpr int NT = kChiScanThreads;
-    __shared__ double sv[kGammaMax * NT];
-    __shared__ int32_t si[kGammaMax * NT];
-    __shared__ double smin[NT];
+    __shared__ double smax[NT], smin[NT];
     __shared__ long long svol[NT];
-    double *val = sv + t;
-    int32_t *id = si + t;
-    for (int s = 0; s < kGammaMax; ++s) {
-        val[s * NT] = -INFINITY;
-        id[s * NT] = INT32_MAX;
-    }
-    double vmin = INFINITY;
+    double vmax = -INFINITY, vmin = INFINITY;
     long long vol = 0;
-    double bv[kGammaMax];
-    int32_t bi[kGammaMax];
     for (int p = t; p < ntiles; p += NT) {
         const int64_t o = (static_cast<int64_t>(slice) * ntiles + p) * B + c;
-        bv[0] = tmax[o];
-        bi[0] = p;
-#pragma unroll
-        for (int s = 1; s < kGammaMax; ++s) {
-            bv[s] = -INFINITY;
-            bi[s] = INT32_MAX;
-        }
-        merge_sorted(val, id, NT, bv, bi, 1);
+        vmax = fmax(vmax, tmax[o]);
         vmin = fmin(vmin, tmin[o]);
         vol += tvol[o];
     }
+    smax[t] = vmax;
     smin[t] = vmin;
     svol[t] = vol;
     __syncthreads();
+    // rank of each thread's maximum among the 128 (ties by thread index); rank gamma - 1 is thr
+    int rank = 0;
+    for (int u = 0; u < NT; ++u) rank += (smax[u] > vmax || (smax[u] == vmax && u < t)) ? 1 : 0;
+    if (gamma > 0 && rank == gamma - 1) cthr[q] = vmax > 0.0 ? vmax : 0.0;
+    if (rank == 0) cmax[q] = vmax;
+    __syncthreads();
     for (int half = NT / 2; half > 0; half >>= 1) {
         if (t < half) {
-            merge_sorted(val, id, NT, sv + t + half, si + t + half, NT);
             smin[t] = fmin(smin[t], smin[t + half]);
             svol[t] += svol[t + half];
         }
         __syncthreads();
     }
     if (t == 0) {
-        const double g = gamma > 0 ? sv[(gamma - 1) * NT] : INFINITY;
-        cthr[q] = g > 0.0 ? g : 0.0;  // -inf (fewer tiles than gamma) counts as 0: every entry is >= 0
-        cmax[q] = sv[0];
         cmin[q] = smin[0];
         cvol[q] = svol[0];
+        if (gamma > NT || gamma <= 0) cthr[q] = 0.0;  // (gamma <= kGammaMax < NT on the product path)
     }
 }
 

@@ -113,7 +113,7 @@ int main(void) {
   P(SC_PREC_FP64) P(SC_PREC_FP32) P(SC_PREC_BF16) P(SC_EST_PLAIN) P(SC_EST_END_CORRECTED)
   P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER) P(SC_SWITCH_PER_SOURCE)
   P(SC_OUT_DEVICE) P(SC_OPT_RECORD_TAIL) P(SC_OPT_TIME_KERNELS) P(SC_OPT_WINDOWS_OFF) P(SC_OPT_WINDOWS_FORCE)
-  P(SC_OPT_DENSE_HOPS) P(SC_OPT_FULL_TOPGAMMA_SCAN) P(SC_KC_DENSE_HOP) P(SC_KC_MASK_HOP) P(SC_KC_SPARSE_HOP) P(SC_KC_BALL_HOP) P(SC_KC_LAST_HOP)
+  P(SC_OPT_SPARSE_HOPS) P(SC_OPT_FULL_TOPGAMMA_SCAN) P(SC_KC_DENSE_HOP) P(SC_KC_MASK_HOP) P(SC_KC_SPARSE_HOP) P(SC_KC_BALL_HOP) P(SC_KC_LAST_HOP)
   P(SC_KC_COUNT)
   P(SC_MLP_PARAMS) P(SC_MLP_FEATURES) P(SC_MLP_MODEL_FLOATS)
   return 0;
@@ -141,7 +141,7 @@ def test_header_constants_match_binding(tmp_path):
     assert (c["SC_SWITCH_COST"], c["SC_SWITCH_PAPER"], c["SC_SWITCH_PER_SOURCE"]) == (0, 1, 2)  # switch="cost" / "paper" / "per_source"
     assert binding.Graph.options(switch="per_source").switch_rule == 2
     for name in ("SC_OUT_DEVICE", "SC_OPT_RECORD_TAIL", "SC_OPT_TIME_KERNELS", "SC_OPT_WINDOWS_OFF",
-                 "SC_OPT_WINDOWS_FORCE", "SC_OPT_DENSE_HOPS", "SC_OPT_FULL_TOPGAMMA_SCAN"):
+                 "SC_OPT_WINDOWS_FORCE", "SC_OPT_SPARSE_HOPS", "SC_OPT_FULL_TOPGAMMA_SCAN"):
         assert c[name] == getattr(binding, name), name
     assert c["SC_KC_COUNT"] == len(binding.KC_NAMES)
     for i, name in enumerate(binding.KC_NAMES):

@@ -1,8 +1,8 @@
 """GPU tests of the hops a block computes only where they can be non-zero or
 are read: hop 3 from the non-zero values of X_2 (k_hop_sparse) and hop L-1 on
 the sources' two-hop balls (k_hop_ball, ahead of the sparse last hop). Both
-keep the full hop's summation order, so sc_all_edges must give bit for bit
-what it gives with every hop run in full (SC_OPT_DENSE_HOPS), for every
+keep the full hop's summation order, so sc_all_edges with SC_OPT_SPARSE_HOPS
+must give bit for bit what it gives with every hop run in full, for every
 precision, block width, lane split, heavy-row threshold and slice count; and
 the FP64 result must match the oracle's series (Algorithm 2) at 1e-12.
 """
@@ -33,8 +33,8 @@ def test_sparse_hops_equal_full_hops_fp32(cuda_lib, maker, ell):
     g = maker()
     with _graph(g) as G:
         kw = dict(policy="fixed", ell_fixed=ell, precision="fp32", windows=False, time_kernels=True)
-        s, _, rep = G.all_edges(**kw)
-        d, _, rep_d = G.all_edges(dense_hops=True, **kw)
+        s, _, rep = G.all_edges(sparse_hops=True, **kw)
+        d, _, rep_d = G.all_edges(**kw)
     assert np.array_equal(s, d)
     assert rep["foster_sum"] == rep_d["foster_sum"]
     kc = rep["kernel_classes"]
@@ -53,8 +53,8 @@ def test_every_width_split_and_heavy_threshold(cuda_lib, prec, B, vpl, heavy, sl
     with _graph(g) as G:
         kw = dict(policy="fixed", ell_fixed=7, precision=prec, block_width=B, rows_split=vpl, heavy_threshold=heavy,
                   max_slices=slices, bf16_from_hop=1)
-        s, _, _ = G.all_edges(**kw)
-        d, _, _ = G.all_edges(dense_hops=True, **kw)
+        s, _, _ = G.all_edges(sparse_hops=True, **kw)
+        d, _, _ = G.all_edges(**kw)
     assert np.array_equal(s, d)
     if prec == "fp64":
         ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, 7)
@@ -67,8 +67,8 @@ def test_bf16_switch_hop_keeps_full_hops_around_it(cuda_lib):
     g = gg.barabasi_albert(1200, 5, 8)
     with _graph(g) as G:
         kw = dict(policy="fixed", ell_fixed=9, precision="bf16", time_kernels=True)
-        s, _, rep = G.all_edges(**kw)
-        d, _, _ = G.all_edges(dense_hops=True, **kw)
+        s, _, rep = G.all_edges(sparse_hops=True, **kw)
+        d, _, _ = G.all_edges(**kw)
     assert np.array_equal(s, d)
     kc = rep["kernel_classes"]
     assert kc["sparse_hop"]["launches"] > 0 and kc["ball_hop"]["launches"] == 0
@@ -90,8 +90,8 @@ def test_learned_and_per_edge_policies(cuda_lib):
         G.estimate_lambda()
         binding.mlp_load(G, model)
         for policy in ("per_edge", "learned"):
-            s, _, rep = G.all_edges(eps=1e-3, policy=policy, precision="fp32")
-            d, _, rep_d = G.all_edges(eps=1e-3, policy=policy, precision="fp32", dense_hops=True)
+            s, _, rep = G.all_edges(eps=1e-3, policy=policy, precision="fp32", sparse_hops=True)
+            d, _, rep_d = G.all_edges(eps=1e-3, policy=policy, precision="fp32")
             assert np.array_equal(s, d), policy
             assert rep["source_hops"] == rep_d["source_hops"]
 
@@ -103,7 +103,7 @@ def test_tgt_plus_with_sparse_hop_3(cuda_lib):
     with _graph(g) as G:
         G.estimate_lambda()
         kw = dict(eps=2e-3, mode="tgt_plus", policy="global", precision="fp64", seed=5, time_kernels=True)
-        s, _, rep = G.all_edges(**kw)
-        d, _, rep_d = G.all_edges(dense_hops=True, **kw)
+        s, _, rep = G.all_edges(sparse_hops=True, **kw)
+        d, _, rep_d = G.all_edges(**kw)
     assert np.array_equal(s, d) and rep["walks"] == rep_d["walks"]
     assert rep["kernel_classes"]["ball_hop"]["launches"] == 0
