@@ -413,7 +413,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ba_200k", choices=sorted(WORKLOADS) + ["batch_512"])
-    ap.add_argument("--grid-ell", type=int, default=1001, help="length of the lattices in batch_512")
+    ap.add_argument("--grid-ell", type=int, default=2201,
+                    help="length of the lattices in batch_512 (no Eq. 6 length exists; 2201 keeps every lattice of "
+                         "the batch within eps = 1e-3)")
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--policy", default="learned", choices=["learned", "global", "per_edge", "fixed"])

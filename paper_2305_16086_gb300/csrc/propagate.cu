@@ -242,6 +242,7 @@ static void hop_t(const sc_graph *g, const HopLaunch &h, cudaStream_t s) {
     a.beta = h.beta;
     a.heavy_ids = g->heavy_ids.get();
     a.heavy_t = g->heavy_threshold_cached;
+    a.level = g->level.get();
     launch_spmm_hop<T, B, VPL>(a, h.slices, s, g->num_sms, h.win_heavy, h.win_rows);
 }
 
@@ -1155,7 +1156,8 @@ struct CaptureGuard {  // ends a stream capture left open by an exception
 };
 
 static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vector<int32_t> &len,
-                           const std::vector<int32_t> &seg_start, int32_t beta) {
+                           const std::vector<int32_t> &seg_start, int32_t beta,
+                           const std::vector<char> &seg_bipartite = {}) {
     sc_graph *g = R.g;
     cudaStream_t s = R.s;
     const int B = R.B;
@@ -1164,26 +1166,44 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
     sources.erase(std::remove_if(sources.begin(), sources.end(), [&](int32_t v) { return len[v] + R.extra <= 0; }),
                   sources.end());
     if (sources.empty()) return;
-    std::sort(sources.begin(), sources.end(), [&](int32_t a, int32_t b) {
-        return len[a] != len[b] ? len[a] > len[b] : a < b;
-    });
     auto seg_of = [&](int32_t v) {
         return static_cast<int32_t>(std::upper_bound(seg_start.begin(), seg_start.end(), v) - seg_start.begin()) - 1;
     };
-    // blocks: up to B sources of one segment and one length
+    // colour (BFS depth parity) of the sources of bipartite segments, -1 elsewhere: blocks of one
+    // colour compute half the rows per hop (SliceWin::parity)
+    const bool any_bip = std::any_of(seg_bipartite.begin(), seg_bipartite.end(), [](char c) { return c != 0; });
+    std::vector<int32_t> colour(any_bip ? g->n : 0, -1);
+    if (any_bip) {
+        std::vector<int32_t> lev(g->n);
+        SC_CUDA(cudaMemcpyAsync(lev.data(), g->level.get(), g->n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+        for (int32_t v : sources)
+            if (seg_bipartite[seg_of(v)]) colour[v] = lev[v] & 1;
+    }
+    auto colour_of = [&](int32_t v) { return any_bip ? colour[v] : -1; };
+    std::sort(sources.begin(), sources.end(), [&](int32_t a, int32_t b) {
+        if (len[a] != len[b]) return len[a] > len[b];
+        const int32_t sa = any_bip ? seg_of(a) : 0, sb = any_bip ? seg_of(b) : 0;
+        if (sa != sb) return sa < sb;
+        if (colour_of(a) != colour_of(b)) return colour_of(a) < colour_of(b);
+        return a < b;
+    });
+    // blocks: up to B sources of one segment, one length and (bipartite segments) one colour
     std::vector<WinBlock> blocks;
     std::vector<std::vector<int32_t>> block_src;
     for (size_t i = 0; i < sources.size();) {
-        const int32_t v0 = sources[i], sg = seg_of(v0), l0 = len[v0];
+        const int32_t v0 = sources[i], sg = seg_of(v0), l0 = len[v0], c0 = colour_of(v0);
         size_t j = i;
         int32_t lo = v0, hi = v0;
-        while (j < sources.size() && static_cast<int>(j - i) < B && len[sources[j]] == l0 && seg_of(sources[j]) == sg) {
+        while (j < sources.size() && static_cast<int>(j - i) < B && len[sources[j]] == l0 && seg_of(sources[j]) == sg &&
+               colour_of(sources[j]) == c0) {
             lo = std::min(lo, sources[j]);
             hi = std::max(hi, sources[j]);
             ++j;
         }
         WinBlock b{};
         SliceWin &w = b.w;
+        w.parity = c0;
         w.L = l0 + R.extra;
         w.seg_lo = seg_start[sg];
         w.seg_hi = seg_start[sg + 1];
@@ -1559,7 +1579,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     }
     const std::vector<int32_t> seg_whole{0, n};
     auto run = [&](const std::vector<int32_t> &src, const std::vector<int32_t> &l) {
-        if (use_win) run_blocks_win(R, src, l, seg_whole, beta);
+        if (use_win) run_blocks_win(R, src, l, seg_whole, beta, std::vector<char>{static_cast<char>(g->bipartite ? 1 : 0)});
         else run_blocks(R, src, l);
     };
     DevBuf<int32_t> tau_saved;
@@ -1970,6 +1990,7 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     U->rev.reserve(NNZ);
     U->inv_deg_f.reserve(N);
     U->inv_deg_d.reserve(N);
+    U->level.reserve(N);
     U->h_row_ptr.resize(N + 1);
     U->min_degree = INT32_MAX;
     for (int32_t i = 0; i < count; ++i) {
@@ -1979,6 +2000,7 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
         k_offset_copy<<<ceil_div(g->nnz, 256), 256, 0, s>>>(U->col_idx.get() + ka, g->col_idx.get(), g->nnz, a);
         k_offset_copy<<<ceil_div(g->nnz, 256), 256, 0, s>>>(U->rev.get() + ka, g->rev.get(), g->nnz, ka);
         SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(U->level.get() + a, g->level.get(), g->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         SC_CUDA(cudaMemcpyAsync(U->inv_deg_f.get() + a, g->inv_deg_f.get(), g->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         SC_CUDA(cudaMemcpyAsync(U->inv_deg_d.get() + a, g->inv_deg_d.get(), g->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         for (int32_t r = 0; r < g->n; ++r) U->h_row_ptr[a + r] = g->h_row_ptr[r] + ka;
@@ -2045,7 +2067,9 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     }
     seg_start[count] = N;
     SC_CUDA(cudaEventRecord(ev1, s));
-    run_blocks_win(R, all, len, seg_start, beta);
+    std::vector<char> seg_bip(count);
+    for (int32_t i = 0; i < count; ++i) seg_bip[i] = graphs[i]->bipartite ? 1 : 0;
+    run_blocks_win(R, all, len, seg_start, beta, seg_bip);
 
     // ---- combine, per-graph Foster sums, outputs
     DevBuf<double> d_s, seg_sum;

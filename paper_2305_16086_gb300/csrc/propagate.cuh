@@ -101,6 +101,10 @@ struct SliceWin {
     int32_t src_lo, src_hi;
     int32_t heavy_begin, heavy_cnt;  // the segment's heavy rows in the id-sorted heavy list
     int32_t L;                       // hops of the slice's block: no rows are computed past it
+    // a bipartite segment whose block holds sources of one colour c (BFS depth parity): X_l is
+    // zero on every row of colour c + l + 1 (mod 2), so hop l computes the rows of colour
+    // c + l (mod 2) only; -1: every row
+    int32_t parity;
 };
 
 __host__ __device__ __forceinline__ void window_rows(const SliceWin &w, int32_t beta, int32_t ell, int32_t *lo,
@@ -145,6 +149,7 @@ struct HopArgs {
     int32_t ell, beta;
     const int32_t *heavy_ids;
     int32_t heavy_t;
+    const int32_t *level;  // BFS depth per node (its parity is the colour of a bipartite graph)
 };
 
 // Algorithm 2's accumulation of Eq. 9 for hop `ell` and launch source q (slice q / B, column
@@ -220,8 +225,10 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
     const int32_t n = a.n;
     int64_t slice_off = static_cast<int64_t>(blockIdx.y) * n * B;
     int32_t base = 0, lo = 0, hi = n, n_heavy = a.n_heavy;
+    int32_t want = -1;  // windowed bipartite block: the colour of the rows hop ell computes
     if constexpr (WIN) {
         const SliceWin w = a.win[blockIdx.y];
+        if (w.parity >= 0) want = (w.parity + a.ell) & 1;
         slice_off = w.xoff;
         base = w.base;
         int64_t wa = w.seg_lo, wb = w.seg_hi;
@@ -265,6 +272,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
         if constexpr (WIN) {
             row = a.heavy_ids[a.win[blockIdx.y].heavy_begin + cta];
             if (row < lo || row >= hi) return;  // outside the window: X_l is zero there
+            if (want >= 0 && (a.level[row] & 1) != want) return;  // the other colour: zero too
         } else {
             row = a.row_order[cta];
         }
@@ -333,20 +341,23 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
     const int32_t heavy_t = n_heavy > 0 || WIN ? a.heavy_t : 0x7fffffff;
     int64_t idx = (static_cast<int64_t>(cta - n_heavy) * kSpmmWarps + warp) * L::G + grp;
     auto row_at = [&](int64_t i) -> int32_t { return row0 + static_cast<int32_t>(i); };
-    int32_t row = 0, rb = 0, re = 0;
+    int32_t row = 0, rb = 0, re = 0, lv = 0;
     if (idx < nlight) {
         row = row_at(idx);
         rb = row_ptr[row];
         re = row_ptr[row + 1];
+        if (WIN && want >= 0) lv = a.level[row];
     }
     for (; idx < nlight; idx += stride) {
-        const int32_t cur = row, cb = rb, ce = re;
+        const int32_t cur = row, cb = rb, ce = re, cl = lv;
         if (idx + stride < nlight) {
             row = row_at(idx + stride);
             rb = row_ptr[row];
             re = row_ptr[row + 1];
+            if (WIN && want >= 0) lv = a.level[row];
         }
         if (ce - cb > heavy_t) continue;  // a heavy row: its own CTA computes it
+        if (WIN && want >= 0 && (cl & 1) != want) continue;  // the other colour: X_l is zero there
         Acc acc[L::NACC], chunk[L::NACC];
 #pragma unroll
         for (int q = 0; q < L::NACC; ++q) {
