@@ -150,10 +150,22 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
     if (cta - a.n_heavy >= a.light_ctas) return;
     const int64_t stride = static_cast<int64_t>(a.light_ctas) * kSpmmWarps;
     const int32_t heavy_t = a.n_heavy > 0 ? a.heavy_t : 0x7fffffff;
-    for (int64_t idx = static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp; idx < n; idx += stride) {
+    // the next row's bounds are loaded while the current row's chunks are in flight
+    int64_t idx = static_cast<int64_t>(cta - a.n_heavy) * kSpmmWarps + warp;
+    int32_t rb_next = 0, re_next = 0;
+    if (idx < n) {
+        rb_next = row_ptr[idx];
+        re_next = row_ptr[idx + 1];
+    }
+    for (; idx < n; idx += stride) {
         const int32_t row = static_cast<int32_t>(idx);
-        const int32_t rb = row_ptr[row], re = row_ptr[row + 1];
+        const int32_t rb = rb_next, re = re_next;
+        if (idx + stride < n) {
+            rb_next = row_ptr[idx + stride];
+            re_next = row_ptr[idx + stride + 1];
+        }
         if (re - rb > heavy_t) continue;  // a heavy row: its own CTA computes it
+        const Acc sc = a.inv_deg[row];
         Acc acc[CPL], chunk[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = Acc(0);
@@ -162,7 +174,6 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_hop2_mask(const MaskHopArgs
 #pragma unroll
             for (int c = 0; c < CPL; ++c) acc[c] += chunk[c];
         }
-        const Acc sc = a.inv_deg[row];
         // the lane's CPL values are contiguous: one vector store
         struct alignas(CPL * sizeof(T)) Vec {
             T v[CPL];

@@ -99,25 +99,27 @@ __global__ void k_spmv_norm(const int32_t *__restrict__ row_ptr, const int32_t *
     if (lane == 0) y[r] = isd[r] * acc;
 }
 
-// partial[q * kDotBlocks + b] = block b's share of <V_q, w>, for q < nvec.
+// partial[q * kDotBlocks + b] = block b's share of <V_q, w>, for q < nvec:
+// block b takes rows [b c, (b + 1) c) (c = ceil(n / kDotBlocks)), its warps
+// take the vectors q = warp, warp + 8, ..., each lane a strided share of the
+// rows in order, then a fixed shuffle tree. One launch of kDotBlocks blocks
+// for every vector of the basis (the rows of w it reads stay in L1).
 // skip (nullable): when *skip != 0 the launch does nothing (a pass the device
 // decided against).
 __global__ void k_multidot_partial(const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
                                    int32_t n, double *__restrict__ partial, const int *__restrict__ skip = nullptr) {
     if (skip && *skip) return;
-    __shared__ double sh[kDotThreads];
-    const int q = blockIdx.y;
-    const double *v = V + q * ldv;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads)
-        acc += v[i] * w[i];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kDotThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
+    const int64_t c = (static_cast<int64_t>(n) + kDotBlocks - 1) / kDotBlocks;
+    const int64_t i0 = blockIdx.x * c, i1 = min(static_cast<int64_t>(n), i0 + c);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kDotThreads / 32;
+    for (int q = warp; q < nvec; q += nw) {
+        const double *v = V + q * ldv;
+        double acc = 0.0;
+        for (int64_t i = i0 + lane; i < i1; i += 32) acc += v[i] * w[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) partial[q * kDotBlocks + blockIdx.x] = acc;
     }
-    if (threadIdx.x == 0) partial[q * kDotBlocks + blockIdx.x] = sh[0];
 }
 
 // out[q] = sum of the kDotBlocks partials of row q (fixed tree); 0 when *skip
@@ -328,14 +330,14 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
         auto reorth = [&](int nv) {
             for (int pass = 0; pass < 2; ++pass) {
                 double *cc = c.get() + (pass ? nbasis : 0);
-                k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
+                k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
                 k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), cc);
                 k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, cc, w.get(), n);
                 SC_LAUNCH_CHECK();
             }
         };
         auto norm2_into = [&](double *dst) {  // dst = <w, w> on the device
-            k_multidot_partial<<<dim3(kDotBlocks, 1), kDotThreads, 0, s>>>(w.get(), ldv, 1, w.get(), n, partial.get());
+            k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(w.get(), ldv, 1, w.get(), n, partial.get());
             k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), dst);
             SC_LAUNCH_CHECK();
         };
@@ -353,21 +355,21 @@ sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambd
         skip.reserve(1);
         d_scal = scal.get();
         auto step_orth = [&](int vj, const double *nrm2_prev) {
-            k_multidot_partial<<<dim3(kDotBlocks, 1), kDotThreads, 0, s>>>(V.get() + vj * ldv, ldv, 1, w.get(), n,
+            k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(V.get() + vj * ldv, ldv, 1, w.get(), n,
                                                                           partial.get());
             k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), d_scal);
             k_three_term<<<nb, tb, 0, s>>>(V.get(), ldv, vj, d_scal, nrm2_prev, w.get(), n);
             SC_LAUNCH_CHECK();
             norm2_into(d_scal + 1);
             const int nv = vj + 1;
-            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
+            k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get());
             k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), c.get());
             k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, c.get(), w.get(), n);
             SC_LAUNCH_CHECK();
             norm2_into(d_scal + 2);
             k_second_sweep_flag<<<1, 1, 0, s>>>(d_scal + 1, d_scal + 2, skip.get());
             double *c2 = c.get() + nbasis;
-            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get(),
+            k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(V.get(), ldv, nv, w.get(), n, partial.get(),
                                                                            skip.get());
             k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), c2, skip.get());
             k_sub_combination<<<nb, tb, 0, s>>>(V.get(), ldv, nv, c2, w.get(), n, skip.get());
@@ -641,14 +643,14 @@ static LanczosOut lanczos_run(sc_graph *g, double *V, int64_t ldv, int nlock, in
     auto reorth = [&](int nv) {
         for (int pass = 0; pass < 2; ++pass) {
             double *cc = c.get() + (pass ? nbasis : 0);
-            k_multidot_partial<<<dim3(kDotBlocks, nv), kDotThreads, 0, s>>>(V, ldv, nv, w.get(), n, partial.get());
+            k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(V, ldv, nv, w.get(), n, partial.get());
             k_multidot_final<<<nv, kDotBlocks, 0, s>>>(partial.get(), cc);
             k_sub_combination<<<nb, tb, 0, s>>>(V, ldv, nv, cc, w.get(), n);
             SC_LAUNCH_CHECK();
         }
     };
     auto norm2_into = [&](double *dst) {
-        k_multidot_partial<<<dim3(kDotBlocks, 1), kDotThreads, 0, s>>>(w.get(), ldv, 1, w.get(), n, partial.get());
+        k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(w.get(), ldv, 1, w.get(), n, partial.get());
         k_multidot_final<<<1, kDotBlocks, 0, s>>>(partial.get(), dst);
         SC_LAUNCH_CHECK();
     };
