@@ -54,7 +54,10 @@ WORKLOADS = {
 # the graph each workload's learned-length model is trained on (same family, another seed)
 TRAIN_GRAPHS = {
     "rmat_22": ("R-MAT scale 16 seed 15", lambda gg: gg.rmat(16, seed=15)),
+    "lattice_1000": ("200x200 lattice, 5% of edges deleted, seed 102 (labels from the tail estimate, cap 511)",
+                     lambda gg: gg.perturbed_grid(200, 200, 0.05, 102)),
 }
+TRAIN_CAP = 511  # label cap of a bipartite training graph (sc_estimated_lengths)
 DEFAULT_TRAIN = ("Barabasi-Albert n=50000 m0=10 seed 101", lambda gg: gg.barabasi_albert(50_000, 10, 101))
 KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh", "paper_2305_16086_gb300/csrc/hop2_mask.cuh",
                   "paper_2305_16086_gb300/csrc/sparse_hops.cuh"]
@@ -210,11 +213,57 @@ def train_model(eps, stream, workload="ba_200k"):
     from paper_2305_16086_gb300 import Graph, binding
 
     tg = TRAIN_GRAPHS.get(workload, DEFAULT_TRAIN)[1](gg)
+    bip = bool(tg.meta.get("bipartite"))
     with Graph(tg.row_ptr, tg.col_idx, stream=stream) as Gt:
-        Gt.estimate_lambda()
+        Gt.estimate_lambda(allow_unconverged=bip)  # a bipartite graph's labels do not use lambda
         init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
-        model, _ = binding.mlp_train([Gt], init, epochs=400, lr=1e-2, eps=eps, precision="fp32")
+        model, _ = binding.mlp_train([Gt], init, epochs=400, lr=1e-2, eps=eps, precision="fp32",
+                                     ell_cap=TRAIN_CAP if bip else 0)
     return model
+
+
+def lattice_reference(g, edges: int, seed: int = 2024):
+    """Exact resistances (oracle O1, sparse LU of the grounded Laplacian, one
+    process per host core) on `edges` uniformly sampled edges of a lattice,
+    where CG converges slowly. Part of the CPU baseline leg."""
+    from oracle import _native, exact
+
+    e = g.edges()
+    rng = np.random.default_rng(seed)
+    pick = e[rng.choice(e.shape[0], size=min(edges, e.shape[0]), replace=False)]
+    k = exact.entry_of_edges(g.n, g.row_ptr, g.col_idx, pick)
+    t0 = time.perf_counter()
+    r = exact.exact_sparse_lu(g.n, g.row_ptr, g.col_idx, pick, processes=_native.default_threads())
+    return {"pick": pick, "k": k, "r": r, "seconds": time.perf_counter() - t0, "seed": seed,
+            "cores": _native.default_threads()}
+
+
+def errors_at(ref, s_hat):
+    err = np.abs(np.asarray(s_hat)[ref["k"]] - ref["r"])
+    return {"sampled_edges": int(ref["k"].size), "max_abs_err": float(err.max()), "mean_abs_err": float(err.mean())}
+
+
+def empirical_length(G, ref, eps, cap, kw):
+    """The global judge on a slow-mixing graph: the least odd length whose
+    end-corrected series is within eps of the exact values on the sampled
+    edges (bisection: the end-corrected series grows with the length), from the
+    GPU series at the sampled entries (sc_some_edges)."""
+    from paper_2305_16086_gb300 import binding
+
+    def ok(ell):
+        s, _ = binding.some_edges(G, ref["k"], **dict(kw, policy="fixed", ell_fixed=ell))
+        return np.max(np.abs(s - ref["r"])) <= eps
+
+    lo, hi = 0, (cap - 1) // 2  # odd lengths 2 i + 1, i in [lo, hi]
+    if not ok(2 * hi + 1):
+        return None
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if ok(2 * mid + 1):
+            hi = mid
+        else:
+            lo = mid + 1
+    return 2 * lo + 1
 
 
 def dist_setup():
@@ -437,12 +486,20 @@ def parse_args(argv=None):
     ap.add_argument("--caltau-omega", type=int, default=64)
     ap.add_argument("--mode", default="tgt", choices=["tgt", "tgt_plus"],
                     help="tgt: Algorithm 2; tgt_plus: Algorithm 4")
+    ap.add_argument("--ell-cap", type=int, default=1023,
+                    help="learned length on a bipartite graph: the longest length an edge may be extended to")
     ap.add_argument("--explicit-config", action="store_true",
-                    help="keep --mode / --policy / --precision as given for the rmat_22 workload")
+                    help="keep --mode / --policy / --precision (/ --eps / --estimator) as given for the rmat_22 "
+                         "and lattice_1000 workloads")
     args = ap.parse_args(argv)
     if args.workload == "rmat_22" and not args.explicit_config:
         # the R-MAT workload's configuration: TGT+ walks, learned lengths, BF16 storage from hop 8
         args.mode, args.policy, args.precision = "tgt_plus", "learned", "bf16"
+    if args.workload == "lattice_1000" and not args.explicit_config:
+        # the lattice's configuration: eps = 1e-2, learned lengths accepted by the tail estimate
+        # (no bound exists on a bipartite graph), the end-corrected estimator, FP32 blocks
+        args.eps, args.mode, args.policy = 1e-2, "tgt", "learned"
+        args.estimator, args.precision = "end_corrected", "fp32"
     return args
 
 
@@ -474,12 +531,15 @@ def main():
     stream = torch.cuda.current_stream()
     run_kw = dict(eps=args.eps, precision=args.precision, policy=args.policy, block_width=args.block_width,
                   rows_split=args.rows_split, heavy_threshold=args.heavy_threshold, ell_fixed=args.ell,
-                  estimator=args.estimator, mode=args.mode)
+                  estimator=args.estimator, mode=args.mode, ell_cap=args.ell_cap)
 
     G = Graph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda(), stream=stream)
+    bip = bool(G.info()["bipartite"])
     # the bound of Eq. 6 needs a converged lambda (its residual is the safety margin): an
-    # unconverged estimate raises here and no value is reported
-    lam = G.estimate_lambda()
+    # unconverged estimate raises here and no value is reported. A fixed length, or any
+    # length on a bipartite graph (lambda* = 1: no bound), does not use it.
+    lambda_free = bip or args.policy == "fixed"
+    lam = G.estimate_lambda(allow_unconverged=lambda_free)
     model = None
     if args.policy == "learned":
         # TGT+ certifies its truncation with eps / 2 (Algorithm 4's split): labels at eps / 2
@@ -553,7 +613,7 @@ def main():
         def e2e_pass(mark):
             with Graph(rp_h, ci_h, stream=stream) as Gh:
                 mark("create_validate")
-                Gh.estimate_lambda()
+                Gh.estimate_lambda(allow_unconverged=lambda_free)
                 mark("lanczos")
                 if model is not None:
                     binding.mlp_load(Gh, model)
@@ -570,9 +630,38 @@ def main():
                "phases_ms_of_a_warmup_pass": phases}
 
     # comparison arms: TGT (traversal only) at the plain global length in FP32 and FP64
-    # (one warm-up, one timed step each)
+    # (one warm-up, one timed step each); on a bipartite graph the global length is the
+    # empirical one (least odd length within eps on the sampled edges) in FP32
     arms = {}
-    if not args.no_arms:
+    lat_ref = None
+    if bip and rank == 0 and world == 1 and not args.no_cpu_baseline and args.check_edges > 0:
+        lat_ref = lattice_reference(g, min(args.check_edges, 500))
+    ours_host = out.cpu().numpy()
+    if bip and not args.no_arms:
+        ell_emp = None
+        if lat_ref is not None:
+            ell_emp = empirical_length(G, lat_ref, args.eps, args.ell_cap,
+                                       dict(eps=args.eps, precision=args.precision, estimator="end_corrected"))
+        if ell_emp is None:
+            ell_emp = 105  # the least odd length within eps = 1e-2 on the 1000 x 1000 lattice's LU sample
+        kw = dict(run_kw, policy="fixed", ell_fixed=ell_emp, estimator="end_corrected", mode="tgt")
+        G.all_edges(out=out, **kw)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, r = G.all_edges(out=out, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        arms["global_emp_fp32"] = {"value": world * g.m / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                                   "ms_per_step": e0.elapsed_time(e1), "source_hops": r["source_hops"],
+                                   "ell": ell_emp,
+                                   "ell_from": "least odd length within eps on the sampled edges (LU)"
+                                   if lat_ref is not None else "fixed (no exact sample in this run)",
+                                   "foster_mean_abs_error": ((g.n - 1) - r["foster_sum"]) / g.m}
+        if lat_ref is not None:
+            arms["global_emp_fp32"].update(errors_at(lat_ref, out.cpu().numpy()))
+    elif not args.no_arms:
         arm_policy = "global" if args.policy == "learned" else args.policy
         for name, prec in ((f"{arm_policy}_fp32", "fp32"), (f"{arm_policy}_fp64", "fp64")):
             kw = dict(run_kw, policy=arm_policy, precision=prec, mode="tgt")
@@ -614,9 +703,15 @@ def main():
     cpu = None
     accuracy = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(g, rep0["ell_global"], target_s=args.cpu_seconds)
-        if args.check_edges > 0:
-            accuracy = exact_check(g, out.cpu().numpy(), args.check_edges)
+        cpu_ell = arms["global_emp_fp32"]["ell"] if "global_emp_fp32" in arms else rep0["ell_global"]
+        cpu = cpu_baseline(g, cpu_ell, target_s=args.cpu_seconds)
+        if lat_ref is not None:
+            accuracy = dict(errors_at(lat_ref, ours_host),
+                            oracle="FP64 sparse LU of the grounded Laplacian per sampled edge",
+                            oracle_seconds=round(lat_ref["seconds"], 2), oracle_cores=lat_ref["cores"],
+                            sample_seed=lat_ref["seed"])
+        elif args.check_edges > 0:
+            accuracy = exact_check(g, ours_host, args.check_edges)
     caltau_arm = run_caltau_arm(args, stream) if args.caltau_arm else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -638,6 +733,9 @@ def main():
         "roofline": roofline, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e, "arms": arms,
         "learned": {"source_hops": rep0["source_hops"], "extension_rounds": rep0["extension_rounds"],
                     "edges_extended": rep0["edges_extended"], "max_tail_bound": rep0["max_tail_bound"],
+                    "acceptance": "power-law tail estimate (uncertified: no bound exists at lambda* = 1)"
+                    if rep0["uncertified"] else "a-posteriori bound (certified)",
+                    "ell_cap": args.ell_cap if rep0["uncertified"] else None,
                     "model": f"trained on {TRAIN_GRAPHS.get(args.workload, DEFAULT_TRAIN)[0]}, 400 Adam steps"}
         if args.policy == "learned" else None,
         "tgt_plus": {"switch_after_hops": [rep0["tt_min"], rep0["tt_max"]], "walk_pairs": rep0["walks"],

@@ -279,7 +279,11 @@ sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
 #define SC_ELL_FIXED 2      /* opts.ell_fixed for every edge (no eigenvalue needed) */
 #define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP (sc_mlp_load); every edge
                                is then certified by the bound of sc_certified_lengths and, if it
-                               fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed */
+                               fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed.
+                               On a bipartite graph (lambda* = 1: no bound and no Eq. 6 length)
+                               with SC_EST_END_CORRECTED, an edge is accepted by the tail estimate
+                               of sc_estimated_lengths instead (uncertified: report.uncertified)
+                               and extended up to opts.ell_cap */
 #define SC_ELL_CALTAU 4     /* the per-edge lengths of the graph's last sc_caltau (same eps; TGT only);
                                sources run the longest of their edges */
 
@@ -350,7 +354,9 @@ typedef struct sc_options {
     int32_t switch_rule;      /* TGT+: SC_SWITCH_COST (default) or SC_SWITCH_PAPER (Eq. 14 as printed) */
     int32_t bf16_from_hop;    /* SC_PREC_BF16: X_l is stored in bf16 for l >= this hop and in fp32
                                  before it, where the probabilities are large (0 = 8; 1 = every hop) */
-    int32_t reserved[5];
+    int32_t ell_cap;          /* SC_ELL_LEARNED on a bipartite graph: the longest length an edge may
+                                 be extended to (>= 3; required there, unused elsewhere) */
+    int32_t reserved[4];
 } sc_options;
 
 /* TGT+ switch rules (when to stop the traversal and draw walks) */
@@ -402,6 +408,9 @@ typedef struct sc_report {
     double kc_ms[SC_KC_COUNT];
     int64_t kc_launches[SC_KC_COUNT];
     double kc_bytes[SC_KC_COUNT];
+    int32_t uncertified;       /* 1 if the learned lengths were accepted by the tail estimate of
+                                  sc_estimated_lengths (bipartite graph), not by a bound */
+    int32_t reserved_r;
 } sc_report;
 
 /*
@@ -519,18 +528,49 @@ sc_status sc_source_features(sc_graph *g, float *features);
 sc_status sc_certified_lengths(sc_graph *g, double eps, int32_t precision, int32_t *per_entry, int32_t *per_source,
                                int32_t *cap);
 
+/*
+ * sc_estimated_lengths -- the training labels and acceptance rule of the
+ * learned length on a bipartite graph, where lambda* = 1 leaves neither the
+ * bound above nor an a-priori length. With the end-corrected estimator the
+ * remainder past odd tau is sum_k c_k lambda_k^(tau+1) (1 + lambda_k) /
+ * (2 (1 - lambda_k)) >= 0 (mode expansion in the proof of Theorem 3.2, the
+ * lambda = -1 mode removed exactly), and the pair sums q_e(tau) = t_{tau+1}(e)
+ * + t_{tau+2}(e) >= 0 decay slowly (diffusively on a lattice). The estimate
+ * fits q_e(x) = C x^-p through q_e(tau - 2) and q_e(tau) at x = tau - 1, tau + 1
+ * and integrates the fitted pair sums past tau (half a unit of x per hop):
+ *     p   = ln(q_e(tau - 2) / q_e(tau)) / ln((tau + 1) / (tau - 1)),
+ *     est = q_e(tau) (tau + 1) ((tau + 1) / tau)^(p - 1) / (2 (p - 1)),
+ * 0 when q_e(tau) <= 0, +inf when tau < 3, q_e(tau - 2) <= 0 or p <= 1. It is
+ * an estimate, not a bound (no certificate exists at lambda* = 1). per_entry:
+ * host int32[nnz], the least odd tau in [3, cap] whose estimate is at most
+ * eps, else cap; per_source (nullable): host int32[n], the row maxima.
+ * Traverses every source to cap + 2 with all hop terms recorded
+ * (8 (cap + 3) nnz bytes of device scratch).
+ * Errors: SC_ERR_INVALID_ARG (null, eps outside (0, 1), cap < 3),
+ * SC_ERR_UNSUPPORTED (the graph is not bipartite: use sc_certified_lengths).
+ */
+sc_status sc_estimated_lengths(sc_graph *g, double eps, int32_t precision, int32_t cap, int32_t *per_entry,
+                               int32_t *per_source);
+
 typedef struct sc_mlp_train_opts {
     int32_t epochs;       /* full-batch Adam steps */
     float lr;             /* learning rate */
     float beta1, beta2, adam_eps;  /* 0 = 0.9, 0.999, 1e-8 */
     int32_t precision;    /* block precision used for the labels */
     double eps;           /* accuracy the labels certify */
+    int32_t ell_cap;      /* bipartite training graphs: the cap of sc_estimated_lengths (>= 3) */
+    int32_t reserved;
 } sc_mlp_train_opts;
 
 /*
  * sc_mlp_train -- builds the training set from `graphs` (features and log of
- * the certified per-source lengths), standardises the features, and trains
- * the MLP on the device (loss: mean (y - log L*)^2 / 2; full-batch Adam).
+ * the certified per-source lengths; sc_estimated_lengths on a bipartite
+ * graph), standardises the features, and trains the MLP on the device (loss:
+ * mean (y - log L*)^2 / 2; full-batch Adam). A feature constant over the
+ * training set (such as the spectral feature of one graph) carries no
+ * information: its first-layer weights are set to zero, which leaves the
+ * training unchanged (its standardised input is 0) and makes the model
+ * ignore it on other graphs.
  *   init_params : host float[SC_MLP_PARAMS], the starting weights (caller's choice)
  *   model_out   : host float[SC_MLP_MODEL_FLOATS]
  *   loss_curve  : host float[epochs], nullable: the loss before each step

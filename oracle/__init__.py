@@ -16,7 +16,8 @@ Modules:
   philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
   tgtplus     the TGT+ pieces: CalChi (Alg. 3), walk counts (Eq. 13), walk
               estimator (Eq. 11), switch rule (Eq. 14)
-  mlp         FP64 reference MLP (features, forward, backward, Adam) for the
-              learned truncation length
+  learned     FP64 reference MLP (features, forward, backward, Adam) for the
+              learned truncation length, its certified labels, and on bipartite
+              graphs the power-law tail estimate and its extension loop
 """
 from . import exact, learned, philox, series, tgtplus, truncation  # noqa: F401

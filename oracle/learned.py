@@ -34,6 +34,30 @@ label costs its source a rerun, one above it wasted hops).
 
 Flat parameter layout (float32, 1313 entries): W1[32][6], b1[32], W2[32][32],
 b2[32], W3[32], b3[1].
+
+Bipartite graphs (lambda* = 1) have neither the bound above nor an a-priori
+length, and need the end-corrected estimator S_hat = S_tau + t_{tau+1}/2.
+Its remainder past odd tau is sum_k c_k lambda_k^(tau+1) (1 + lambda_k) /
+(2 (1 - lambda_k)) >= 0 (the same mode expansion; the lambda = -1 mode drops
+out), which for the slow modes is about the sum of the pair sums
+q(tau) = t_{tau+1} + t_{tau+2}, q(tau + 2), ... On a lattice these decay like
+a power of the hop (diffusion), so the pair sums are fitted by C x^-p through
+q(tau - 2) at x = tau - 1 and q(tau) at x = tau + 1, and the fit is summed
+past tau as an integral at half a unit of x per hop:
+
+    p   = ln(q(tau - 2) / q(tau)) / ln((tau + 1) / (tau - 1)),
+    est = C tau^(1-p) / (2 (p - 1)) = q(tau) (tau + 1) ((tau + 1)/tau)^(p-1) / (2 (p - 1)).
+
+This is an estimate, not a bound (``tail_estimate``). A bipartite graph's
+labels are the least odd tau in [3, cap] whose estimate is at most eps
+(``estimated_lengths``); ``learned_bipartite`` is the extension loop of the
+learned policy with this acceptance. Where it differs from a geometric
+extrapolation of the same ratio: a geometric fit assumes the ratio
+q(tau)/q(tau-2) stays fixed, and on a power-law tail C x^-p it falls short by
+the factor (p - 1)/p (one half on a 2-D lattice); the power-law fit is
+exact there and overshoots a geometric tail (parity unpinned against the
+paper: the paper has no bipartite rule; pinned by closed forms and brute
+force below).
 """
 from __future__ import annotations
 
@@ -194,3 +218,65 @@ def predict_lengths(theta, F, mu, sd, cap):
         e = np.ceil(np.exp(y) - 0.25)
     L = np.clip(np.nan_to_num(e, nan=1.0, posinf=float(cap)), 1, cap).astype(np.int64)
     return np.where(L % 2 == 0, np.minimum(L + 1, cap if cap % 2 == 1 else cap + 1), L)
+
+
+# ---------------------------------------------------------------------------
+# bipartite graphs: the tail estimate and the learned policy's loop with it
+# ---------------------------------------------------------------------------
+
+def tail_estimate(q_prev, q, tau):
+    """Power-law tail estimate from the pair sums q(tau - 2) and q(tau) (see the
+    module notes): 0 where q <= 0; +inf where tau < 3, q(tau - 2) <= 0 or the
+    fitted exponent p <= 1 (no decay fast enough to sum)."""
+    q_prev = np.asarray(q_prev, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    tau = np.broadcast_to(np.asarray(tau, dtype=np.float64), q.shape)
+    out = np.full(q.shape, np.inf)
+    ok = (tau >= 3) & (q_prev > 0) & (q > 0)
+    x = tau[ok]
+    p = np.log(q_prev[ok] / q[ok]) / np.log((x + 1.0) / (x - 1.0))
+    est = np.full(x.shape, np.inf)
+    dec = p > 1.0
+    pd, xd = p[dec], x[dec]
+    est[dec] = q[ok][dec] * (xd + 1.0) * np.exp((pd - 1.0) * np.log((xd + 1.0) / xd)) / (2.0 * (pd - 1.0))
+    out[ok] = est
+    out[q <= 0] = 0.0
+    return out
+
+
+def estimated_lengths(n, row_ptr, col_idx, eps, cap):
+    """Least odd tau in [3, cap] per entry whose tail estimate is <= eps (else cap)."""
+    T = hop_terms(n, row_ptr, col_idx, cap + 2)
+    rev = series.reverse_entries(n, row_ptr, col_idx)
+    full = T + T[rev]  # t_l(e), l = 0..cap+2
+    tau = np.full(full.shape[0], cap, dtype=np.int64)
+    done = np.zeros(full.shape[0], dtype=bool)
+    for t in range(3, cap + 1, 2):
+        est = tail_estimate(full[:, t - 1] + full[:, t], full[:, t + 1] + full[:, t + 2], t)
+        ok = (~done) & (est <= eps)
+        tau[ok] = t
+        done |= ok
+    return tau
+
+
+def learned_bipartite(n, row_ptr, col_idx, L_src, cap, eps):
+    """The learned policy on a bipartite graph: tau_e = min(L_i, L_j); each
+    round evaluates the tail estimate of every edge at its tau from the
+    end-corrected series at tau and tau - 2, and an edge whose estimate exceeds
+    eps below the cap takes tau <- min(2 tau + 1, cap); until none does.
+    Returns (s_hat per entry, tau per entry, rounds)."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    L_src = np.asarray(L_src, dtype=np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    cols = np.asarray(col_idx, dtype=np.int64)
+    tau = np.minimum(L_src[rows], L_src[cols])
+    rounds = 0
+    while True:
+        s, q = series.series_entries(n, row_ptr, col_idx, tau, end_corrected=True)
+        _, q_prev = series.series_entries(n, row_ptr, col_idx, np.maximum(tau - 2, 0), end_corrected=True)
+        est = tail_estimate(q_prev, q, tau)
+        fail = (est > eps) & (tau < cap)
+        if not fail.any():
+            return s, tau, rounds
+        tau = np.where(fail, np.minimum(2 * tau + 1, cap), tau)
+        rounds += 1

@@ -39,7 +39,7 @@ EXPORTS = [
     "sc_last_error_detail", "sc_abi_version", "sc_all_edges_noalloc", "sc_source_features",
     "sc_certified_lengths", "sc_mlp_train", "sc_mlp_load", "sc_mlp_predict", "sc_mlp_loss_grad",
     "sc_batch_all_edges", "sc_selftest_bounded_waits", "sc_eigenpairs", "sc_caltau", "sc_tridiag_eig",
-    "sc_series_meet", "sc_some_edges", "sc_graph_set_lambda",
+    "sc_series_meet", "sc_some_edges", "sc_graph_set_lambda", "sc_estimated_lengths",
 ]
 OMEGA_MAX = 257
 MLP_PARAMS, MLP_FEATURES = 1313, 6
@@ -71,7 +71,7 @@ class Options(ctypes.Structure):
                 ("max_slices", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("delta", ctypes.c_double), ("gamma", ctypes.c_int32),
                 ("switch_rule", ctypes.c_int32), ("bf16_from_hop", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("ell_cap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Report(ctypes.Structure):
@@ -89,7 +89,8 @@ class Report(ctypes.Structure):
                 ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32),
                 ("walk_steps", ctypes.c_int64), ("walk_device_ms", ctypes.c_double),
                 ("kc_ms", ctypes.c_double * 5), ("kc_launches", ctypes.c_int64 * 5),
-                ("kc_bytes", ctypes.c_double * 5)]
+                ("kc_bytes", ctypes.c_double * 5), ("uncertified", ctypes.c_int32),
+                ("reserved_r", ctypes.c_int32)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -115,7 +116,7 @@ class EigReport(ctypes.Structure):
 class MlpTrainOpts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("precision", ctypes.c_int32),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("ell_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ScError(RuntimeError):
@@ -170,6 +171,8 @@ def load(path: str = LIB_PATH):
     L.sc_source_features.restype = ctypes.c_int
     L.sc_certified_lengths.argtypes = [vp, f64, i32, i32p, i32p, i32p]
     L.sc_certified_lengths.restype = ctypes.c_int
+    L.sc_estimated_lengths.argtypes = [vp, f64, i32, i32, i32p, i32p]
+    L.sc_estimated_lengths.restype = ctypes.c_int
     L.sc_mlp_train.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(MlpTrainOpts), f32p, f32p, f32p]
     L.sc_mlp_train.restype = ctypes.c_int
     L.sc_mlp_load.argtypes = [vp, f32p]
@@ -339,7 +342,7 @@ class Graph:
                 estimator="plain", block_width=0, rows_split=0, heavy_threshold=0, max_slices=0,
                 record_tail=False, time_kernels=False, seed=None, delta=0.0, gamma=None,
                 switch="cost", windows=None, bf16_from_hop=0, sparse_hops=False,
-                full_topgamma_scan=False) -> Options:
+                full_topgamma_scan=False, ell_cap=0) -> Options:
         o = Options()
         load().sc_options_default(ctypes.byref(o))
         o.eps = eps
@@ -366,6 +369,7 @@ class Graph:
             o.gamma = gamma
         o.switch_rule = {"cost": 0, "paper": 1, "per_source": 2}[switch]
         o.bf16_from_hop = bf16_from_hop
+        o.ell_cap = ell_cap
         return o
 
     def all_edges(self, out=None, tail_bound=None, **kw):
@@ -530,10 +534,20 @@ def certified_lengths(graph, eps: float, precision: str = "fp64"):
     return pe, ps, int(cap.value)
 
 
-def mlp_train(graphs, init_params, epochs=300, lr=1e-2, eps=1e-3, precision="fp32"):
-    """Train on the GPU. Returns (model float32[MLP_MODEL_FLOATS], loss curve float32[epochs])."""
+def estimated_lengths(graph, eps: float, cap: int, precision: str = "fp64"):
+    """Bipartite graph: (per_entry int32[nnz], per_source int32[n]) from the tail estimate."""
+    pe = np.empty(graph.nnz, dtype=np.int32)
+    ps = np.empty(graph.n, dtype=np.int32)
+    _check(load().sc_estimated_lengths(graph._h, eps, PREC[precision], cap, _i32p(pe), _i32p(ps)),
+           "sc_estimated_lengths")
+    return pe, ps
+
+
+def mlp_train(graphs, init_params, epochs=300, lr=1e-2, eps=1e-3, precision="fp32", ell_cap=0):
+    """Train on the GPU. Returns (model float32[MLP_MODEL_FLOATS], loss curve float32[epochs]).
+    ell_cap: the label cap of bipartite training graphs (sc_estimated_lengths)."""
     hs = (ctypes.c_void_p * len(graphs))(*[g._h.value for g in graphs])
-    opts = MlpTrainOpts(epochs, lr, 0.0, 0.0, 0.0, PREC[precision], eps)
+    opts = MlpTrainOpts(epochs, lr, 0.0, 0.0, 0.0, PREC[precision], eps, ell_cap, 0)
     p, pp = _f32(init_params)
     model = np.empty(MLP_MODEL_FLOATS, dtype=np.float32)
     curve = np.empty(epochs, dtype=np.float32)

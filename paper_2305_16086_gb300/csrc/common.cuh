@@ -117,6 +117,13 @@ __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) { retu
 
 inline int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
+// a launch shape of the propagation: block width, 16-byte vectors per lane
+// (0 = the TMA-gather kernel) and the measured time of one hop per source
+struct TuneResult {
+    int B, vpl;
+    double ms_per_source_hop;
+};
+
 }  // namespace sc
 
 // ---------------------------------------------------------------------------
@@ -162,6 +169,10 @@ struct sc_graph {
     // autotuned (block width, lane split) per request key, and its measured ms per source-hop
     std::map<long long, std::pair<int, int>> tuned;
     std::map<long long, double> tuned_cost;
+    // per request key: the best lane split of each block width, and the launch shape chosen
+    // by timing one real block of each (the block loop's own kernels, see pick_block_width)
+    std::map<long long, std::vector<sc::TuneResult>> tuned_per_b;
+    std::map<long long, sc::TuneResult> tuned_block;
 
     // learned length: features (n x 6) and the loaded model
     sc::DevBuf<float> features, mlp;

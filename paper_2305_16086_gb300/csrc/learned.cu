@@ -7,7 +7,9 @@
 // the a-posteriori bound lambda*^2/(1-lambda*^2) (t_{tau-1} + t_tau) (from the
 // mode expansion in the proof of Theorem 3.2) and extends the edges that fail,
 // up to the a-priori length of Eq. (6), so the eps guarantee does not depend
-// on the model.
+// on the model. A bipartite graph (lambda* = 1) has neither: there the labels
+// and the acceptance come from the power-law tail estimate of the
+// end-corrected series (sc_estimated_lengths), an estimate, not a bound.
 //
 // Features of source i: log d_i; log min_{j in N(i)} d_j; local clustering;
 // log(sum_{j in N(i)} d_j / 2m); p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j;
@@ -24,6 +26,7 @@ namespace sc {
 
 sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
 void certified_lengths_impl(sc_graph *g, double eps, int precision, int32_t *per_entry_dev, int32_t *cap_out);
+void estimated_lengths_impl(sc_graph *g, double eps, int precision, int32_t cap, int32_t *per_entry_dev);
 
 constexpr int kH = SC_MLP_HIDDEN;
 constexpr int kF = SC_MLP_FEATURES;
@@ -336,6 +339,27 @@ sc_status sc_certified_lengths(sc_graph *g, double eps, int32_t precision, int32
     });
 }
 
+sc_status sc_estimated_lengths(sc_graph *g, double eps, int32_t precision, int32_t cap, int32_t *per_entry,
+                               int32_t *per_source) {
+    return guarded([&] {
+        if (!g || !per_entry) SC_FAIL(SC_ERR_INVALID_ARG, "null argument");
+        if (!(eps > 0.0 && eps < 1.0)) SC_FAIL(SC_ERR_INVALID_ARG, "eps must lie in (0, 1)");
+        if (cap < 3) SC_FAIL(SC_ERR_INVALID_ARG, "cap must be >= 3, got %d", cap);
+        DevBuf<int32_t> te;
+        te.reserve(g->nnz);
+        estimated_lengths_impl(g, eps, precision, cap, te.get());
+        SC_CUDA(cudaMemcpyAsync(per_entry, te.get(), g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+        SC_CUDA(cudaStreamSynchronize(g->stream));
+        if (per_source) {
+            for (int32_t i = 0; i < g->n; ++i) {
+                int32_t m = 0;
+                for (int32_t k = g->h_row_ptr[i]; k < g->h_row_ptr[i + 1]; ++k) m = std::max(m, per_entry[k]);
+                per_source[i] = m;
+            }
+        }
+    });
+}
+
 sc_status sc_mlp_loss_grad(const float *model, const float *features, const float *targets, int32_t count,
                            float *loss, float *grad, void *stream) {
     return guarded([&] {
@@ -374,7 +398,7 @@ sc_status sc_mlp_train(sc_graph *const *graphs, int32_t count, const sc_mlp_trai
         if (opts->epochs <= 0 || !(opts->lr > 0.0f) || !(opts->eps > 0.0 && opts->eps < 1.0))
             SC_FAIL(SC_ERR_INVALID_ARG, "epochs, lr and eps must be positive (eps < 1)");
         cudaStream_t s = graphs[0]->stream;
-        // training set: features and log certified per-source lengths of every graph
+        // training set: features and log certified (bipartite: estimated) per-source lengths of every graph
         std::vector<float> F, y;
         for (int32_t gi = 0; gi < count; ++gi) {
             sc_graph *g = graphs[gi];
@@ -386,7 +410,13 @@ sc_status sc_mlp_train(sc_graph *const *graphs, int32_t count, const sc_mlp_trai
             DevBuf<int32_t> te;
             te.reserve(g->nnz);
             int32_t cap = 0;
-            certified_lengths_impl(g, opts->eps, opts->precision, te.get(), &cap);
+            if (g->bipartite) {
+                if (opts->ell_cap < 3 || (opts->ell_cap & 1) == 0)
+                    SC_FAIL(SC_ERR_INVALID_ARG, "graph %d is bipartite: its labels need an odd ell_cap >= 3", gi);
+                estimated_lengths_impl(g, opts->eps, opts->precision, opts->ell_cap, te.get());
+            } else {
+                certified_lengths_impl(g, opts->eps, opts->precision, te.get(), &cap);
+            }
             std::vector<int32_t> tau(g->nnz);
             SC_CUDA(cudaMemcpyAsync(tau.data(), te.get(), g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
             SC_CUDA(cudaStreamSynchronize(g->stream));
@@ -410,8 +440,13 @@ sc_status sc_mlp_train(sc_graph *const *graphs, int32_t count, const sc_mlp_trai
             }
             const double sd = std::sqrt(sq / N);
             model[kP + f] = static_cast<float>(mu);
-            // a spread at rounding level marks a constant feature (scale 1)
-            model[kP + kF + f] = sd > 1e-9 * std::max(std::fabs(mu), 1.0) ? static_cast<float>(sd) : 1.0f;
+            // a spread at rounding level marks a constant feature (scale 1); its
+            // standardised input is 0 on every sample, so zero first-layer weights
+            // change no step of the training and make the model ignore it elsewhere
+            const bool constant = !(sd > 1e-9 * std::max(std::fabs(mu), 1.0));
+            model[kP + kF + f] = constant ? 1.0f : static_cast<float>(sd);
+            if (constant)
+                for (int a = 0; a < kH; ++a) model[oW1 + a * kF + f] = 0.0f;
         }
         std::vector<float> X(F.size());
         for (int32_t i = 0; i < N; ++i)

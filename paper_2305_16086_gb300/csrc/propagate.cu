@@ -31,6 +31,7 @@ long long tgtplus_walks(sc_graph *g, int prec, int B, const void *x, const int32
                         long long *steps_out);
 constexpr int kCostRuleHops = 4;  // the cost rule tests the last hops only
 constexpr int kEvenDepthCap = 16;  // TGT+ at learned lengths: even hops recorded for the check (hop <= 16)
+constexpr int kTuneHops = 8;       // hops of the sample block that picks the block width
 // TGT+ cost rule rates measured on GB300: a hop costs about this much per
 // source and CSR entry (BA-200k, FP32 blocks: 1.1 us per source over 4.0M
 // entries), a walk step (three dependent random reads) about kWalkStepNs
@@ -525,20 +526,19 @@ static int slices_for(const sc_graph *g, int B, size_t elem, int max_slices) {
 // sample of sources (values do not change the cost). Keeps the least time per
 // source; cached per graph, precision, request and length. The gathers write
 // the accumulators, which the caller resets afterwards.
-struct TuneResult {
-    int B, vpl;
-    double ms_per_source_hop;  // one hop with gather, per source
-};
-
+// per_b (nullable): the best lane split of every block width, by the same model
 static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_slices, int32_t L, const GatherRec &rec,
-                           bool allow_tma, cudaStream_t s) {
+                           bool allow_tma, cudaStream_t s, std::vector<TuneResult> *per_b = nullptr) {
     L = std::max(L, 1);
     const long long key = (static_cast<long long>(prec) << 40) ^ (static_cast<long long>(fixB) << 24) ^
                           (static_cast<long long>(fixV) << 16) ^ static_cast<long long>(max_slices & 0xffff) ^
                           (static_cast<long long>(g->n_heavy) << 44) ^ (static_cast<long long>(L) << 52) ^
                           (static_cast<long long>(allow_tma) << 62);
     auto it = g->tuned.find(key);
-    if (it != g->tuned.end()) return TuneResult{it->second.first, it->second.second, g->tuned_cost[key]};
+    if (it != g->tuned.end() && (!per_b || g->tuned_per_b.count(key))) {
+        if (per_b) *per_b = g->tuned_per_b[key];
+        return TuneResult{it->second.first, it->second.second, g->tuned_cost[key]};
+    }
     std::vector<std::pair<int, int>> cands;
     for (int B : {32, 64, 128})
         for (int v : {0, 1, 2, 4})
@@ -619,13 +619,23 @@ static TuneResult autotune(sc_graph *g, int prec, int fixB, int fixV, int max_sl
     }
     g->tuned[key] = cands[pick];
     g->tuned_cost[key] = best_hop[pick];
+    std::vector<TuneResult> pb;
+    for (int B : {32, 64, 128}) {
+        int bi = -1;
+        for (size_t ci = 0; ci < cands.size(); ++ci)
+            if (cands[ci].first == B && (bi < 0 || best_block[ci] < best_block[bi])) bi = static_cast<int>(ci);
+        if (bi >= 0) pb.push_back(TuneResult{B, cands[bi].second, best_hop[bi]});
+    }
+    g->tuned_per_b[key] = pb;
+    if (per_b) *per_b = pb;
     return TuneResult{cands[pick].first, cands[pick].second, best_hop[pick]};
 }
 
 // ---------------------------------------------------------------------------
 // accumulator reset for a set of source rows (all rows when rows == nullptr):
 // the hop-0 term of Eq. (9) is 1 (unscaled); with record mode 1 the hop-0 term
-// is also the "tau - 1" record of a length-1 entry
+// is also the "tau - 1" record of a length-1 entry, with mode 3 the first
+// record slot of a length-1 entry (the second of a length-0 one)
 // ---------------------------------------------------------------------------
 __global__ void k_reset_rows(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rows, int32_t nrows,
                              const int32_t *__restrict__ tau, int mode, double *__restrict__ g, double *__restrict__ t1,
@@ -639,7 +649,12 @@ __global__ void k_reset_rows(const int32_t *__restrict__ row_ptr, const int32_t 
         const int32_t tk = tau[k];
         t1[k] = (mode == 1 && tk == 1) ? 1.0 : 0.0;
         t2[k] = (mode == 1 && tk == 0) ? 1.0 : 0.0;
-        if (rec_all) rec_all[static_cast<int64_t>(k) * rec_stride] = 1.0;
+        if (rec_all && mode == 3) {
+            rec_all[static_cast<int64_t>(k) * 2] = tk == 1 ? 1.0 : 0.0;
+            rec_all[static_cast<int64_t>(k) * 2 + 1] = tk == 0 ? 1.0 : 0.0;
+        } else if (rec_all) {
+            rec_all[static_cast<int64_t>(k) * rec_stride] = 1.0;
+        }
     }
 }
 
@@ -682,6 +697,78 @@ __global__ void k_extend_failing(const int32_t *__restrict__ row_ptr, const int3
     if (lane == 0) {
         row_flag[r] = any;
         if (c) atomicAdd(count, c);
+    }
+}
+
+// The learned length's acceptance test on a bipartite graph (lambda* = 1, no
+// bound): with the end-corrected estimator the remainder past odd tau is
+// sum_k c_k lambda_k^(tau+1) (1 + lambda_k) / (2 (1 - lambda_k)) >= 0 (mode
+// expansion in the proof of Theorem 3.2), i.e. about the sum of the pair sums
+// q(tau) = t_{tau+1} + t_{tau+2}, q(tau + 2), ... when the slow modes dominate.
+// The pair sums are fitted by q(x) = C x^-p through q(tau - 2) = qp at x = tau - 1
+// and q(tau) = q at x = tau + 1 (a diffusive, power-law decay), and the fitted
+// pair sums are integrated past tau at half a unit of x per hop:
+// C tau^(1-p) / (2 (p - 1)). An estimate, not a bound. 0 when q <= 0;
+// +inf when tau < 3, qp <= 0 or p <= 1 (no decay to extrapolate).
+__device__ __forceinline__ double tail_estimate(double qp, double q, int32_t tau) {
+    if (q <= 0.0) return 0.0;
+    if (tau < 3 || !(qp > 0.0)) return INFINITY;
+    const double x = static_cast<double>(tau);
+    const double p = log(qp / q) / log((x + 1.0) / (x - 1.0));
+    if (!(p > 1.0)) return INFINITY;
+    return q * (x + 1.0) * exp((p - 1.0) * log((x + 1.0) / x)) / (2.0 * (p - 1.0));
+}
+
+// per entry: est[k] = tail_estimate of its edge from the records of hops
+// tau-1, tau (pre[2k], pre[2k+1]) and tau+1, tau+2 (t1, t2) of both halves,
+// each combined as t_l(e) = h_l[k] / d_i + h_l[rev k] / d_j (the same
+// commutative expression in both directions)
+__global__ void k_tail_estimate(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                                const double *__restrict__ pre, const double *__restrict__ t1,
+                                const double *__restrict__ t2, const int32_t *__restrict__ tau, int32_t n,
+                                double *__restrict__ est) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const double ir = inv_d[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t kr = rev[k];
+        const double ij = inv_d[col[k]];
+        auto full = [&](double a, double b) { return __dadd_rn(__dmul_rn(a, ir), __dmul_rn(b, ij)); };
+        const double qp = __dadd_rn(full(pre[2 * static_cast<int64_t>(k)], pre[2 * static_cast<int64_t>(kr)]),
+                                    full(pre[2 * static_cast<int64_t>(k) + 1], pre[2 * static_cast<int64_t>(kr) + 1]));
+        const double q = __dadd_rn(full(t1[k], t1[kr]), full(t2[k], t2[kr]));
+        est[k] = tail_estimate(qp, q, tau[k]);
+    }
+}
+
+// training labels on a bipartite graph: every source ran cap + 2 hops with all
+// hop terms recorded (rec[k * stride + l]); each entry takes the least odd
+// tau in [3, cap] whose tail estimate is at most eps, else cap
+__global__ void k_estimate_lengths(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                   const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                                   const double *__restrict__ rec, int stride, int32_t n, int32_t cap, double eps,
+                                   int32_t *__restrict__ tau_out) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const double ir = inv_d[r];
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t kr = rev[k];
+        const double ij = inv_d[col[k]];
+        auto full = [&](int l) {
+            return __dadd_rn(__dmul_rn(rec[static_cast<int64_t>(k) * stride + l], ir),
+                             __dmul_rn(rec[static_cast<int64_t>(kr) * stride + l], ij));
+        };
+        int32_t t = cap;
+        for (int32_t c = 3; c <= cap; c += 2) {
+            if (tail_estimate(__dadd_rn(full(c - 1), full(c)), __dadd_rn(full(c + 1), full(c + 2)), c) <= eps) {
+                t = c;
+                break;
+            }
+        }
+        tau_out[k] = t;
     }
 }
 
@@ -1376,6 +1463,93 @@ static void run_blocks_win(Run &R, std::vector<int32_t> sources, const std::vect
 // ---------------------------------------------------------------------------
 // sc_all_edges
 // ---------------------------------------------------------------------------
+// Block width from one real block per width. autotune() models a block by its
+// dense hops and leaves out the kernels that run once per block (hops 1-2 from
+// the sources' masks, the last hop on the gather's rows), whose cost per source
+// grows as the block narrows. Here, for the best lane split of each width, one
+// launch worth of sample sources (spread over the ids; a contiguous id run for
+// windowed blocks, whose cost depends on the sources' id range) runs through
+// the block loop itself at min(L, kTuneHops) hops with their own lengths; a
+// source's cost is that time per source plus the remaining hops at the width's
+// measured hop cost. Two rounds after a warm-up, interleaved over the widths,
+// the least kept; cached per request key. The traversal only (no TGT+ test or
+// walk, no records). The sample's gathers write the accumulators, which the
+// caller resets afterwards.
+static TuneResult pick_block_width(const Run &base, const std::vector<TuneResult> &per_b,
+                                   const std::vector<int32_t> &len, int32_t Lmax, bool use_win, int32_t beta,
+                                   const std::vector<char> &bip, long long key) {
+    sc_graph *g = base.g;
+    cudaStream_t s = base.s;
+    auto hit = g->tuned_block.find(key);
+    if (hit != g->tuned_block.end()) return hit->second;
+    const int32_t n = g->n;
+    const size_t elem = alloc_elem(base.prec, base.h0);
+    const int32_t Ls = std::min(Lmax, kTuneHops);
+    size_t need = 0;
+    for (const auto &c : per_b)
+        need = std::max(need, slices_for(g, c.B, elem, base.o->max_slices) * static_cast<size_t>(n) * c.B * elem);
+    g->xa.reserve(need);
+    g->xb.reserve(need);
+    cudaEvent_t e0, e1;
+    SC_CUDA(cudaEventCreate(&e0));
+    SC_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{e0, e1};
+    std::vector<double> best(per_b.size(), INFINITY);
+    std::vector<int32_t> ls(len);
+    const std::vector<int32_t> seg_whole{0, n};
+    for (int round = 0; round < 3; ++round) {
+        for (size_t ci = 0; ci < per_b.size(); ++ci) {
+            const TuneResult &c = per_b[ci];
+            Run R = base;
+            R.B = c.B;
+            R.vpl = c.vpl;
+            R.slices = slices_for(g, c.B, elem, base.o->max_slices);
+            R.slice_bytes = static_cast<size_t>(n) * c.B * elem;
+            R.plus = false;
+            R.time_kernels = false;
+            R.depth = nullptr;
+            R.capture = false;
+            R.extra = 0;
+            R.rec = GatherRec{base.rec.mode, nullptr, 0};
+            const int32_t cnt = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(R.slices) * c.B, n));
+            std::vector<int32_t> src(cnt);
+            const int32_t lo = use_win ? (n - cnt) / 2 : 0;
+            for (int32_t q = 0; q < cnt; ++q) {
+                const int32_t v = use_win ? lo + q : static_cast<int32_t>((static_cast<int64_t>(q) * n) / cnt);
+                src[q] = v;
+                ls[v] = std::min(len[v] + base.extra, Ls);
+            }
+            SC_CUDA(cudaEventRecord(e0, s));
+            if (use_win) run_blocks_win(R, src, ls, seg_whole, beta, bip);
+            else run_blocks(R, src, ls);
+            SC_CUDA(cudaEventRecord(e1, s));
+            SC_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            for (int32_t q = 0; q < cnt; ++q) ls[src[q]] = len[src[q]];
+            if (round == 0) continue;  // warm-up
+            const double per_source = ms / cnt + std::max(Lmax - Ls, 0) * c.ms_per_source_hop;
+            best[ci] = std::min(best[ci], per_source);
+        }
+    }
+    size_t pick = 0;
+    const bool log = std::getenv("SC_AUTOTUNE_LOG") != nullptr;
+    for (size_t ci = 0; ci < per_b.size(); ++ci) {
+        if (log)
+            std::fprintf(stderr, "sc block width: B %d split %d: %.4f us per source (sample block of %d hops, L %d)\n",
+                         per_b[ci].B, per_b[ci].vpl == 0 ? -1 : per_b[ci].vpl, 1e3 * best[ci], Ls, Lmax);
+        if (best[ci] < best[pick]) pick = ci;
+    }
+    g->tuned_block[key] = per_b[pick];
+    return per_b[pick];
+}
+
 static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, double *tail_bound, sc_report *rep,
                            double *rec_all = nullptr, int rec_stride = 0, const EdgeSubset *sub = nullptr) {
     if (!g || (!s_hat && !sub)) SC_FAIL(SC_ERR_INVALID_ARG, "null graph or output");
@@ -1409,8 +1583,17 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
     const bool learned = o.ell_policy == SC_ELL_LEARNED;
     if (learned && !g->mlp_loaded) SC_FAIL(SC_ERR_INVALID_ARG, "no model loaded: call sc_mlp_load first");
-    if (learned && o.estimator != SC_EST_PLAIN)
+    // a bipartite graph has no bound and no a-priori length: the learned lengths are
+    // accepted by the tail estimate (end-corrected estimator) and capped by opts.ell_cap
+    const bool est_learned = learned && g->bipartite;
+    if (learned && !est_learned && o.estimator != SC_EST_PLAIN)
         SC_FAIL(SC_ERR_UNSUPPORTED, "the learned length certifies the plain estimator");
+    if (est_learned && plus) SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ needs lambda_star < 1: the graph is bipartite");
+    if (est_learned && o.estimator != SC_EST_END_CORRECTED)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "the learned length on a bipartite graph needs the end-corrected estimator");
+    if (est_learned && (o.ell_cap < 3 || (o.ell_cap & 1) == 0))
+        SC_FAIL(SC_ERR_INVALID_ARG, "the learned length on a bipartite graph needs an odd ell_cap >= 3, got %d",
+                o.ell_cap);
     const bool out_dev = (o.flags & SC_OUT_DEVICE) != 0;
     const bool time_kernels = (o.flags & SC_OPT_TIME_KERNELS) != 0;
     const bool record_after = (o.flags & SC_OPT_RECORD_TAIL) || o.estimator == SC_EST_END_CORRECTED;
@@ -1438,9 +1621,9 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         sc_status st = estimate_lambda_impl(g, nullptr, &lam);
         if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
     }
-    if (o.ell_policy != SC_ELL_FIXED && !caltau && (g->bipartite || g->lam.lambda_star >= 1.0))
+    if (o.ell_policy != SC_ELL_FIXED && !caltau && !est_learned && (g->bipartite || g->lam.lambda_star >= 1.0))
         SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_star >= 1 (bipartite graph): no finite length meets eps; use a fixed "
-                                    "length with the end-corrected estimator");
+                                    "length or the learned one with the end-corrected estimator");
     const double lam_star = g->lam.lambda_star;
 
     // ---- truncation lengths --------------------------------------------------
@@ -1462,6 +1645,16 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SC_CUDA(cudaStreamSynchronize(s));
         ell_global = *std::max_element(len.begin(), len.end());
+    } else if (est_learned) {
+        // per-source lengths from the model, capped by the caller's longest length
+        ell_global = o.ell_cap;
+        learned_lengths(g, ell_global, tau_src.get(), s);
+        k_tau_min_of_sources<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), tau_src.get(), n,
+                                                              g->tau_entry.get());
+        k_row_max<<<ceil_div(n, 256), 256, 0, s>>>(g->row_ptr.get(), g->tau_entry.get(), n, tau_src.get());
+        SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(len.data(), tau_src.get(), n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
     } else {
         // TGT+ (Algorithm 4) asks for a tail of at most eps/2 and leaves eps/2 to the walks
         tau_entries_device(g, plus ? 0.5 * o.eps : o.eps, lam_star, g->tau_entry.get(), tau_src.get(), &ell_global);
@@ -1505,7 +1698,14 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rec_all = even_rec.get();
         rec_stride = even_stride;
     }
-    const GatherRec rec{learned_plus ? 2 : (learned ? 1 : 0), rec_all, rec_stride};
+    // the tail estimate of a bipartite graph reads the terms of hops tau-1, tau (and tau+1, tau+2)
+    DevBuf<double> pre_rec;
+    if (est_learned) {
+        pre_rec.reserve(static_cast<size_t>(nnz) * 2);
+        rec_all = pre_rec.get();
+        rec_stride = 2;
+    }
+    const GatherRec rec{learned_plus ? 2 : (est_learned ? 3 : (learned ? 1 : 0)), rec_all, rec_stride};
     g->acc_g.reserve(nnz);
     g->acc_t1.reserve(nnz);
     g->acc_t2.reserve(nnz);
@@ -1519,8 +1719,9 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     // a bf16 run whose early hops are fp32 is tuned (and its buffers sized) in fp32
     const int32_t h0 = bf16_first_hop(o);
     const int tune_prec = (o.precision == SC_PREC_BF16 && h0 > 1) ? SC_PREC_FP32 : o.precision;
+    std::vector<TuneResult> per_b;
     const TuneResult tr = autotune(g, tune_prec, o.block_width, fixV, o.max_slices, Lmax,
-                                   GatherRec{rec.mode, nullptr, 0}, !use_win, s);
+                                   GatherRec{rec.mode, nullptr, 0}, !use_win, s, &per_b);
     Run R;
     R.g = g;
     R.o = &o;
@@ -1539,6 +1740,22 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     R.log2md = std::log(2.0 * static_cast<double>(nnz / 2) / delta);
     R.extra = record_after ? 2 : 0;
     R.rec = rec;
+    if (per_b.size() > 1 && Lmax >= 2) {
+        // the block width from one real block of each (the request's lengths, kernels and records)
+        const long long key = (static_cast<long long>(tune_prec) << 56) ^ (static_cast<long long>(fixV + 1) << 52) ^
+                              (static_cast<long long>(o.max_slices & 0xfff) << 40) ^
+                              (static_cast<long long>(Lmax) << 16) ^ (static_cast<long long>(use_win) << 15) ^
+                              (static_cast<long long>(rec.mode) << 12) ^
+                              (static_cast<long long>((o.flags & SC_OPT_SPARSE_HOPS) != 0) << 11) ^
+                              (static_cast<long long>(o.ell_policy) << 8) ^ (static_cast<long long>(o.estimator) << 6) ^
+                              (static_cast<long long>(plus) << 5) ^ static_cast<long long>(std::min(h0, 31));
+        const TuneResult t2 = pick_block_width(R, per_b, len, Lmax, use_win, beta,
+                                               std::vector<char>{static_cast<char>(g->bipartite ? 1 : 0)}, key);
+        R.B = t2.B;
+        R.vpl = t2.vpl;
+        R.slice_bytes = static_cast<size_t>(n) * R.B * elem;
+        R.slices = slices_for(g, R.B, elem, o.max_slices);
+    }
     std::vector<int32_t> depth;
     if (learned_plus) {
         depth.assign(n, 0);
@@ -1618,7 +1835,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     // q / (1 - lambda*^2); learned (records of hops tau-1, tau): lambda*^2 / (1 - lambda*^2) (t_{tau-1} + t_tau).
     // lambda_plus carries its Ritz residual as a safety margin.
     double bound_scale = 0.0;
-    if (learned && !plus) {
+    if (learned && !plus && !est_learned) {
         bound_scale = lam_star * lam_star / (1.0 - lam_star * lam_star);
     } else if (record_after) {
         const double lp = g->lam.lambda_plus + std::max(g->lam.residual_plus, 0.0);
@@ -1688,6 +1905,13 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         g->tp_counters.reserve(4);
         std::vector<int32_t> h_flag(n);
         while (true) {
+            if (est_learned) {  // the bound column takes the tail estimate
+                k_tail_estimate<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(),
+                                                               g->inv_deg_d.get(), pre_rec.get(), g->acc_t1.get(),
+                                                               g->acc_t2.get(), g->tau_entry.get(), n, d_b);
+                SC_LAUNCH_CHECK();
+                R.launches += 1;
+            }
             SC_CUDA(cudaMemsetAsync(g->tp_counters.get(), 0, sizeof(long long), s));
             k_extend_failing<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), d_b, n, o.eps,
                                                             ell_global, sub ? active.get() : nullptr,
@@ -1712,8 +1936,8 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
             rows.reserve(redo.size());
             SC_CUDA(cudaMemcpyAsync(rows.get(), redo.data(), redo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
             k_reset_rows<<<ceil_div(static_cast<int64_t>(redo.size()), 8), 256, 0, s>>>(
-                g->row_ptr.get(), rows.get(), static_cast<int32_t>(redo.size()), g->tau_entry.get(), 1, g->acc_g.get(),
-                g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
+                g->row_ptr.get(), rows.get(), static_cast<int32_t>(redo.size()), g->tau_entry.get(), rec.mode,
+                g->acc_g.get(), g->acc_t1.get(), g->acc_t2.get(), rec_all, rec_stride);
             SC_LAUNCH_CHECK();
             R.launches += 2;
             run(redo, len);
@@ -1792,6 +2016,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rep->edges_extended = static_cast<int32_t>(extended);
         rep->extension_rounds = rounds;
         rep->windowed = use_win ? 1 : 0;
+        rep->uncertified = est_learned ? 1 : 0;
         rep->tt_min = plus ? (R.tt_min == INT32_MAX ? 0 : R.tt_min) : 0;
         rep->tt_max = plus ? R.tt_max : 0;
         rep->switch_tests = R.switch_tests;
@@ -1871,6 +2096,33 @@ void certified_lengths_impl(sc_graph *g, double eps, int precision, int32_t *per
     SC_LAUNCH_CHECK();
     SC_CUDA(cudaStreamSynchronize(s));
     *cap_out = cap;
+}
+
+// training labels on a bipartite graph: every source runs cap + 2 hops with
+// every hop's half term recorded (end-corrected estimator), then each edge
+// takes the least odd tau in [3, cap] whose tail estimate is within eps
+void estimated_lengths_impl(sc_graph *g, double eps, int precision, int32_t cap, int32_t *per_entry_dev) {
+    cudaStream_t s = g->stream;
+    if (!g->bipartite) SC_FAIL(SC_ERR_UNSUPPORTED, "the graph is not bipartite: its lengths are certified by a bound");
+    if (cap < 3 || (cap & 1) == 0) SC_FAIL(SC_ERR_INVALID_ARG, "cap must be odd and >= 3, got %d", cap);
+    DevBuf<double> rec, sh;
+    const int stride = cap + 3;
+    rec.reserve(static_cast<size_t>(g->nnz) * stride);
+    sh.reserve(g->nnz);
+    sc_options o;
+    sc_options_default(&o);
+    o.eps = eps;
+    o.precision = precision;
+    o.ell_policy = SC_ELL_FIXED;
+    o.ell_fixed = cap;
+    o.estimator = SC_EST_END_CORRECTED;
+    o.flags = SC_OUT_DEVICE;
+    all_edges_impl(g, &o, sh.get(), nullptr, nullptr, rec.get(), stride);
+    k_estimate_lengths<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(),
+                                                         g->inv_deg_d.get(), rec.get(), stride, g->n, cap, eps,
+                                                         per_entry_dev);
+    SC_LAUNCH_CHECK();
+    SC_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------------------

@@ -82,6 +82,7 @@ __device__ __forceinline__ uint4 ld_x(const uint4 *p) { return __ldg(p); }
 struct GatherRec {
     int mode;       // 0: t1, t2 = terms of hops tau+1, tau+2; 1: terms of hops tau-1, tau;
                     // 2: no t1 / t2; all[k * stride + ell / 2] = term of every even hop ell < 2 stride
+                    // 3: as 0, and all[k * 2 + 0 / 1] = terms of hops tau-1, tau
     double *all;    // nullable: (modes 0, 1) all[k * stride + ell] = term of hop ell (every hop)
     int stride;
 };
@@ -172,14 +173,19 @@ __device__ __forceinline__ void gather_term(int32_t k, double term, const int32_
             if (ell == tk - 1) t1[k] = term;
             else if (ell == tk) t2[k] = term;
         }
-    } else if (rec.mode == 0) {
+    } else if (rec.mode == 0 || rec.mode == 3) {
         if (ell == tk + 1) t1[k] = term;
         else if (ell == tk + 2) t2[k] = term;
     }
     if (rec.all) {
-        if (rec.mode != 2) rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
-        else if ((ell & 1) == 0 && (ell >> 1) < rec.stride)
-            rec.all[static_cast<int64_t>(k) * rec.stride + (ell >> 1)] = term;
+        if (rec.mode == 2) {
+            if ((ell & 1) == 0 && (ell >> 1) < rec.stride)
+                rec.all[static_cast<int64_t>(k) * rec.stride + (ell >> 1)] = term;
+        } else if (rec.mode == 3) {
+            if (ell == tk - 1 || ell == tk) rec.all[static_cast<int64_t>(k) * 2 + (ell - tk + 1)] = term;
+        } else {
+            rec.all[static_cast<int64_t>(k) * rec.stride + ell] = term;
+        }
     }
 }
 

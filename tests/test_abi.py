@@ -69,6 +69,8 @@ int main(void) {
   printf("sc_graph_info %zu\nsc_lambda %zu\nsc_lambda_opts %zu\nsc_options %zu\nsc_report %zu\n",
          sizeof(sc_graph_info), sizeof(sc_lambda), sizeof(sc_lambda_opts), sizeof(sc_options), sizeof(sc_report));
   printf("sc_eig_opts %zu\nsc_eig_report %zu\n", sizeof(sc_eig_opts), sizeof(sc_eig_report));
+  printf("sc_mlp_train_opts %zu\n", sizeof(sc_mlp_train_opts));
+  F(sc_mlp_train_opts, eps) F(sc_mlp_train_opts, ell_cap) F(sc_options, ell_cap) F(sc_report, uncertified)
   F(sc_eig_opts, tol) F(sc_eig_opts, rest_tol) F(sc_eig_opts, rest_max_iter) F(sc_eig_opts, seed)
   F(sc_eig_report, rest_converged) F(sc_eig_report, max_residual) F(sc_eig_report, lambda_rest)
   F(sc_options, seed) F(sc_options, delta) F(sc_options, gamma) F(sc_options, flags) F(sc_options, bf16_from_hop)
@@ -90,7 +92,7 @@ def test_struct_layouts_match_c(tmp_path):
     c = dict(line.split() for line in lines if line.strip())
     py = {"sc_graph_info": binding.GraphInfo, "sc_lambda": binding.Lambda, "sc_lambda_opts": binding.LambdaOpts,
           "sc_options": binding.Options, "sc_report": binding.Report, "sc_eig_opts": binding.EigOpts,
-          "sc_eig_report": binding.EigReport}
+          "sc_eig_report": binding.EigReport, "sc_mlp_train_opts": binding.MlpTrainOpts}
     for name, cls in py.items():
         assert int(c[name]) == ctypes.sizeof(cls), name
     for key, val in c.items():

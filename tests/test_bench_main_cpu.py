@@ -40,7 +40,7 @@ def _report(kw):
             "walk_ms": 0.5, "hop_ms": 20.0 if kw.get("time_kernels") else 0.0, "hop_bytes": 4.0e8,
             "hop_launches": 4, "launches": 12, "foster_sum": 0.0, "ell_global": 7, "block_width": 64,
             "rows_split": 1, "slices": 1, "blocks": 3, "windowed": 0, "source_hops": 700, "extension_rounds": 0,
-            "edges_extended": 0, "max_tail_bound": 1e-4}
+            "edges_extended": 0, "max_tail_bound": 1e-4, "uncertified": 0}
 
 
 class _FakeGraph:
@@ -58,6 +58,9 @@ class _FakeGraph:
 
     def close(self):
         pass
+
+    def info(self):
+        return {"n": self.n, "nnz": self.nnz, "bipartite": 0}
 
     def estimate_lambda(self, **kw):
         return {"lambda_star": 0.43, "lambda_plus": 0.43, "lambda_minus": -0.3, "converged": 1, "iterations": 40,

@@ -88,6 +88,11 @@ def test_arguments_default_and_tgt_plus_mode():
     assert (a.mode, a.policy, a.precision) == ("tgt_plus", "learned", "bf16")
     a = bench.parse_args(["--workload", "rmat_22", "--explicit-config", "--mode", "tgt", "--policy", "global"])
     assert (a.mode, a.policy, a.precision) == ("tgt", "global", "fp32")
+    a = bench.parse_args(["--workload", "lattice_1000"])  # learned lengths by the tail estimate, eps = 1e-2
+    assert (a.eps, a.mode, a.policy, a.estimator, a.precision, a.ell_cap) == (
+        1e-2, "tgt", "learned", "end_corrected", "fp32", 1023)
+    a = bench.parse_args(["--workload", "lattice_1000", "--explicit-config", "--policy", "fixed", "--ell", "105"])
+    assert (a.eps, a.policy, a.ell, a.estimator) == (1e-3, "fixed", 105, "plain")
 
 
 def test_timed_passes_split_only_the_warmups():

@@ -155,3 +155,110 @@ def test_training_reduces_loss_and_predictions_are_odd():
 
 def _csr(g):
     return g.n, g.row_ptr, g.col_idx
+
+
+# ---------------------------------------------------------------------------
+# bipartite graphs: the power-law tail estimate and the extension loop
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1.5, 2.0, 3.0])
+@pytest.mark.parametrize("tau", [11, 51, 301])
+def test_tail_estimate_sums_a_power_law(p, tau):
+    """Pair sums a(x) = x^-p at x = tau+1, tau+3, ...: the estimate from
+    q(tau-2), q(tau) recovers their sum (brute force to 2e6 terms plus the
+    integral of the rest) within the midpoint rule's error p(p+1)/(8 tau^2)."""
+    q_prev, q = (tau - 1.0) ** -p, (tau + 1.0) ** -p
+    est = learned.tail_estimate(np.array([q_prev]), np.array([q]), tau)[0]
+    i = np.arange(2_000_000, dtype=np.float64)
+    far = tau + 1.0 + 2.0 * i.size
+    brute = np.sum((tau + 1.0 + 2.0 * i) ** -p) + far ** (1.0 - p) / (2.0 * (p - 1.0))
+    assert abs(est / brute - 1.0) <= p * (p + 1.0) / (8.0 * tau * tau)
+
+
+@pytest.mark.parametrize("mu", [0.1, 0.5, 0.9])
+@pytest.mark.parametrize("tau", [11, 101])
+def test_tail_estimate_overshoots_a_geometric_tail(mu, tau):
+    """Pair sums falling by a fixed ratio mu per two hops sum to q / (1 - mu);
+    the power-law fit never falls below that (it reads a faster-falling ratio
+    as a steeper power), or is infinite when the fitted power is <= 1."""
+    est = learned.tail_estimate(np.array([1.0 / mu]), np.array([1.0]), tau)[0]
+    assert est >= 1.0 / (1.0 - mu)
+
+
+def test_tail_estimate_special_cases():
+    est = learned.tail_estimate(np.array([1.0, 1.0, 0.0, 1.0, 1.0, 1.0, np.nan, 1.1]),
+                                np.array([0.0, -1e-20, 1.0, 1.0, 2.0, 0.5, 1.0, 1.0]),
+                                np.array([5, 5, 5, 5, 5, 1, 5, 5]))
+    assert est[0] == 0.0 and est[1] == 0.0  # nothing left (or rounding below zero)
+    assert np.isinf(est[2])  # no earlier pair to fit
+    assert np.isinf(est[3]) and np.isinf(est[4])  # no decay, or growth: p <= 1
+    assert np.isinf(est[5])  # tau = 1 has no pair before it
+    assert np.isinf(est[6])
+    assert np.isinf(est[7])  # decay too slow to sum (p = ln 1.1 / ln 1.5 < 1)
+
+
+def _lattice():
+    return gg.perturbed_grid(24, 30, 0.05, 2)
+
+
+def test_tail_estimate_on_a_perturbed_lattice():
+    """Against the exact remainder of the end-corrected series (grounded
+    Laplacian): from hop 21 on the estimate is never below 0.8 of it (the
+    diffusive decay it is made for), and the geometric fit of the same pair
+    sums falls to about half of it."""
+    g = _lattice()
+    r = exact.exact_dense(*_csr(g))
+    L = 160
+    T = learned.hop_terms(*_csr(g), L)
+    rev = series.reverse_entries(*_csr(g))
+    full = T + T[rev]
+    cs = np.cumsum(full, axis=1)
+    geo_min = np.inf
+    for t in range(21, L - 2, 10):
+        true = r - (cs[:, t] + 0.5 * full[:, t + 1])
+        qp, q = full[:, t - 1] + full[:, t], full[:, t + 1] + full[:, t + 2]
+        est = learned.tail_estimate(qp, q, t)
+        m = true > 1e-9
+        assert np.all(true > -1e-12)  # the remainder is non-negative (lower bound)
+        assert np.min(est[m] / true[m]) >= 0.8
+        geo = q / (2.0 * (1.0 - np.sqrt(q / qp)))
+        geo_min = min(geo_min, np.min(geo[m] / true[m]))
+    assert geo_min < 0.6
+
+
+def test_estimated_lengths_two_routes():
+    """The labels from the recorded hop terms equal a search over odd tau with
+    the series oracle's own pair sums q(tau) (Algorithm 2 at each length)."""
+    g = _lattice()
+    eps, cap = 1e-2, 61
+    tau = learned.estimated_lengths(*_csr(g), eps, cap)
+    assert np.all(tau % 2 == 1) and np.all((tau >= 3) & (tau <= cap))
+    rev = series.reverse_entries(*_csr(g))
+    assert np.array_equal(tau, tau[rev])
+    q = {t: series.series_entries(*_csr(g), t, end_corrected=True)[1] for t in range(1, cap + 1, 2)}
+    want = np.full(g.nnz, cap)
+    done = np.zeros(g.nnz, dtype=bool)
+    for t in range(3, cap + 1, 2):
+        ok = ~done & (learned.tail_estimate(q[t - 2], q[t], t) <= eps)
+        want[ok] = t
+        done |= ok
+    assert np.array_equal(tau, want)
+
+
+def test_learned_bipartite_within_eps():
+    """The extension loop from a short constant length: every edge ends at an
+    odd length whose estimate passed (or the cap), the values are the
+    end-corrected series there, and all are within eps of the exact values."""
+    g = _lattice()
+    eps, cap = 1e-2, 255
+    s, tau, rounds = learned.learned_bipartite(g.n, g.row_ptr, g.col_idx, np.full(g.n, 5), cap, eps)
+    assert rounds >= 2
+    assert np.all(tau % 2 == 1) and np.all(tau <= cap)
+    assert np.mean(tau) < 0.5 * cap  # accepted well below the cap, not run out to it
+    ref, q = series.series_entries(*_csr(g), tau, end_corrected=True)
+    assert np.array_equal(s, ref)
+    _, qp = series.series_entries(*_csr(g), tau - 2, end_corrected=True)
+    est = learned.tail_estimate(qp, q, tau)
+    assert np.all((est <= eps) | (tau == cap))
+    r = exact.exact_dense(*_csr(g))
+    assert np.all(s <= r + 1e-12) and np.max(r - s) <= eps

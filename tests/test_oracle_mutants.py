@@ -99,6 +99,12 @@ LEARNED = [
     ("gradient vs finite differences", tl.test_mlp_gradient_matches_finite_differences),
     ("Adam first step", tl.test_adam_first_step_closed_form),
     ("odd prediction with slack", tl.test_prediction_rounds_to_an_odd_length_with_a_quarter_slack),
+    ("tail estimate sums a power law", lambda: tl.test_tail_estimate_sums_a_power_law(2.0, 11)),
+    ("tail estimate overshoots a geometric tail", lambda: tl.test_tail_estimate_overshoots_a_geometric_tail(0.5, 11)),
+    ("tail estimate special cases", tl.test_tail_estimate_special_cases),
+    ("tail estimate on a lattice", tl.test_tail_estimate_on_a_perturbed_lattice),
+    ("estimated lengths, two routes", tl.test_estimated_lengths_two_routes),
+    ("bipartite extension loop", tl.test_learned_bipartite_within_eps),
 ]
 
 CALTAU = [
@@ -313,6 +319,20 @@ PY_MUTANTS = [
      "e = np.ceil(np.exp(y) - 0.25)", "e = np.ceil(np.exp(y))"),
     ("learned", "certificate from one term", "learned",
      "(factor * (full[:, t - 1] + full[:, t]) <= eps)", "(factor * full[:, t] <= eps)"),
+    ("learned", "tail estimate without the half unit per hop", "learned",
+     "/ (2.0 * (pd - 1.0))", "/ (pd - 1.0)"),
+    ("learned", "power fitted over abscissae tau - 2, tau", "learned",
+     "np.log((x + 1.0) / (x - 1.0))", "np.log(x / (x - 2.0))"),
+    ("learned", "tail estimate zero where nothing decays", "learned",
+     "    dec = p > 1.0\n", "    dec = p > 0.0\n"),
+    ("learned", "labels from the pair after tau", "learned",
+     "est = tail_estimate(full[:, t - 1] + full[:, t], full[:, t + 1] + full[:, t + 2], t)",
+     "est = tail_estimate(full[:, t + 1] + full[:, t + 2], full[:, t + 1] + full[:, t + 2], t)"),
+    ("learned", "extension loop fits one pair twice", "learned",
+     "np.maximum(tau - 2, 0), end_corrected=True)", "tau, end_corrected=True)"),
+    ("learned", "extension loop plain estimator", "learned",
+     "s, q = series.series_entries(n, row_ptr, col_idx, tau, end_corrected=True)",
+     "s, q = series.series_entries(n, row_ptr, col_idx, tau, end_corrected=False)"),
 ]
 
 
