@@ -58,6 +58,13 @@ TRAIN_GRAPHS = {
                      lambda gg: gg.perturbed_grid(200, 200, 0.05, 102)),
 }
 TRAIN_CAP = 511  # label cap of a bipartite training graph (sc_estimated_lengths)
+# the batch's model: one graph of each family of the batch (other seeds); the lattice's labels
+# at eps = 1e-3 reach a few thousand hops, hence the larger cap
+BATCH_TRAIN = ("G(n, 8/(n-1)) LCC n=5000 seed 901, Barabasi-Albert n=5000 m=5 seed 902, 70x70 lattice seed 903 "
+               "(labels from the tail estimate, cap 4095)",
+               lambda gg: [gg.gnp_lcc(5000, 8.0, 901), gg.barabasi_albert(5000, 5, 902),
+                           gg.perturbed_grid(70, 70, 0.05, 903)])
+BATCH_TRAIN_CAP = 4095
 DEFAULT_TRAIN = ("Barabasi-Albert n=50000 m0=10 seed 101", lambda gg: gg.barabasi_albert(50_000, 10, 101))
 KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh", "paper_2305_16086_gb300/csrc/hop2_mask.cuh",
                   "paper_2305_16086_gb300/csrc/sparse_hops.cuh"]
@@ -358,11 +365,52 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def train_batch_model(eps, stream):
+    """The batch's MLP: trained on the GPU on one graph of each family of the
+    batch (other seeds; untimed preprocessing)."""
+    import graphgen as gg
+    from paper_2305_16086_gb300 import Graph, binding
+
+    ts = BATCH_TRAIN[1](gg)
+    Gt = [Graph(t.row_ptr, t.col_idx, stream=stream) for t in ts]
+    try:
+        for G, t in zip(Gt, ts):
+            G.estimate_lambda(allow_unconverged=bool(t.meta.get("bipartite")))
+        init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
+        model, _ = binding.mlp_train(Gt, init, epochs=400, lr=1e-2, eps=eps, precision="fp32",
+                                     ell_cap=BATCH_TRAIN_CAP)
+    finally:
+        for G in Gt:
+            G.close()
+    return model
+
+
+def batch_references(gs, workers: int):
+    """Start the exact values of every graph of the batch (oracle O1: dense for
+    n <= 5000, else 200 sampled edges by sparse LU for lattices or CG) in a
+    spawn pool, to run on the host cores while the GPU works. Part of the CPU
+    baseline leg. Returns (executor, futures)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from oracle import exact
+
+    ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    futs = [ex.submit(exact.reference_values, x.n, x.row_ptr, x.col_idx, 5000, 200, 100 + i,
+                      bool(x.meta.get("bipartite")), 2) for i, x in enumerate(gs)]
+    return ex, futs
+
+
 def run_batch(args, world, rank):
     """The many-graph workload through sc_batch_all_edges: 512 graphs, n
     log-uniform in [1e3, 5e4] (G(n, 8/(n-1)) LCC, Barabasi-Albert m = 5 and
-    perturbed lattices in turn), FP32 blocks. Non-bipartite graphs take their
-    own Eq. 6 length; the lattices (no Eq. 6 length) take --grid-ell."""
+    perturbed lattices in turn), FP32 blocks. With the learned policy (the
+    default) every graph takes its lengths from one model (checked per edge:
+    the bound with the graph's lambda*, on the lattices the tail estimate, cap
+    --batch-cap); otherwise non-bipartite graphs take their own Eq. 6 length
+    and the lattices (no Eq. 6 length) take --grid-ell. The per-graph maximum
+    error against the exact values is reported (the CPU leg, computed while
+    the GPU runs)."""
     import torch
 
     import graphgen as gg
@@ -372,39 +420,83 @@ def run_batch(args, world, rank):
     t0 = time.perf_counter()
     gs = gg.batch_graphs(512, 1000, 50000, base_seed=4)
     gen_s = time.perf_counter() - t0
+    refs_ex = refs = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {key: os.environ.get(key) for key in keys}
+        os.environ.update({key: "2" for key in keys})  # workers of two threads share the host cores
+        try:
+            refs_ex, refs = batch_references(gs, max(1, (os.cpu_count() or 8) // 2 - 1))
+        finally:
+            for key, v in saved.items():
+                if v is None:
+                    os.environ.pop(key, None)
+                else:
+                    os.environ[key] = v
     stream = torch.cuda.current_stream()
+    learned = args.policy == "learned"
+    model = train_batch_model(args.eps, stream) if learned else None
     Gs = [Graph(g.row_ptr, g.col_idx, stream=stream) for g in gs]
-    ells = [args.grid_ell if g.meta.get("bipartite") else 0 for g in gs]
-    for G, e in zip(Gs, ells):
-        if e == 0:
+    if learned:
+        ells = None
+        for G, g in zip(Gs, gs):
             G.estimate_lambda(allow_unconverged=True)
-    kw = dict(eps=args.eps, precision=args.precision, estimator="end_corrected")
+            binding.mlp_load(G, model)
+    else:
+        ells = [args.grid_ell if g.meta.get("bipartite") else 0 for g in gs]
+        for G, e in zip(Gs, ells):
+            if e == 0:
+                G.estimate_lambda(allow_unconverged=True)
+    kw = dict(eps=args.eps, precision=args.precision, estimator="end_corrected",
+              policy="learned" if learned else "global", ell_cap=args.batch_cap)
     for _ in range(args.warmup):
         binding.batch_all_edges(Gs, ells, **kw)
     torch.cuda.synchronize()
-    times, reps = [], None
+    times, reps, outs = [], None, None
     with ClockSampler(torch.cuda.current_device()) as clk:
         for _ in range(args.steps):
             t = time.perf_counter()
-            _, reps = binding.batch_all_edges(Gs, ells, **kw)
+            outs, reps = binding.batch_all_edges(Gs, ells, **kw)
             times.append((time.perf_counter() - t) * 1e3)
     m = sum(g.m for g in gs)
     ms = statistics.mean(times)
     lens = [r["ell_global"] for r in reps]
-    line = {"metric": "AESC edges/sec over a batch of 512 graphs (batched FP32, one CUDA-graph launch)",
+    accuracy = None
+    if refs is not None:
+        errs = []
+        for x, out, fut in zip(gs, outs, refs):
+            kk, vals = fut.result()
+            errs.append(float(np.max(np.abs(out[kk] - vals))))
+        refs_ex.shutdown()
+        bip = np.array([bool(x.meta.get("bipartite")) for x in gs])
+        errs = np.array(errs)
+        accuracy = {"graphs_checked": len(errs), "max_abs_err_worst_graph": float(errs.max()),
+                    "max_abs_err_median_graph": float(np.median(errs)),
+                    "graphs_above_eps": int(np.sum(errs > args.eps)),
+                    "worst_lattice": float(errs[bip].max()) if bip.any() else None,
+                    "worst_other": float(errs[~bip].max()) if (~bip).any() else None,
+                    "oracle": "per graph: dense grounded-Laplacian inverse (n <= 5000, every edge) or 200 sampled "
+                              "edges (sparse LU for lattices, CG otherwise), FP64, in a spawn pool on the host"}
+    line = {"metric": "AESC edges/sec over a batch of 512 graphs (batched FP32, CUDA-graph launches)",
             "value": m / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "512 graphs, n log-uniform in [1000, 50000]: G(n, 8/(n-1)) LCC, "
                                    "Barabasi-Albert m=5, perturbed lattices, seeds 4..515",
                        "graphs": len(gs), "n_total": sum(g.n for g in gs), "m_total": m, "eps": args.eps,
-                       "lattice_length": args.grid_ell, "estimator": "end_corrected",
+                       "policy": "learned" if learned else "global (lattices: fixed)",
+                       "lattice_length": None if learned else args.grid_ell,
+                       "lattice_cap": args.batch_cap if learned else None,
+                       "model": f"trained on {BATCH_TRAIN[0]}, 400 Adam steps" if learned else None,
+                       "estimator": "end_corrected",
                        "lengths_min_max": [min(lens), max(lens)], "block_width": reps[0]["block_width"],
+                       "source_hops": int(sum(r["source_hops"] for r in reps)),
+                       "extension_rounds": reps[0]["extension_rounds"],
                        "hop_launches": reps[0]["hop_launches"], "generation_s": gen_s},
             "roofline": {"bound": "hbm", "achieved": reps[0]["hop_bytes"] / (reps[0]["propagate_ms"] / 1e3) / 1e9,
                          "peak": measured_peaks()[0], "unit": "GB/s", "note": "algorithmic bytes over the "
                          "propagation time (whole CUDA graph, not one kernel)"},
-            "clocks": clk.summary(), "gpu_launches": int(reps[0]["launches"])}
+            "clocks": clk.summary(), "gpu_launches": int(reps[0]["launches"]), "accuracy": accuracy}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     for G in Gs:
         G.close()
@@ -486,6 +578,8 @@ def parse_args(argv=None):
     ap.add_argument("--caltau-omega", type=int, default=64)
     ap.add_argument("--mode", default="tgt", choices=["tgt", "tgt_plus"],
                     help="tgt: Algorithm 2; tgt_plus: Algorithm 4")
+    ap.add_argument("--batch-cap", type=int, default=4095,
+                    help="batch_512 with the learned policy: the lattices' longest length")
     ap.add_argument("--ell-cap", type=int, default=1023,
                     help="learned length on a bipartite graph: the longest length an edge may be extended to")
     ap.add_argument("--explicit-config", action="store_true",

@@ -279,11 +279,12 @@ sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
 #define SC_ELL_FIXED 2      /* opts.ell_fixed for every edge (no eigenvalue needed) */
 #define SC_ELL_LEARNED 3    /* per-source length predicted by the MLP (sc_mlp_load); every edge
                                is then certified by the bound of sc_certified_lengths and, if it
-                               fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed.
-                               On a bipartite graph (lambda* = 1: no bound and no Eq. 6 length)
-                               with SC_EST_END_CORRECTED, an edge is accepted by the tail estimate
-                               of sc_estimated_lengths instead (uncertified: report.uncertified)
-                               and extended up to opts.ell_cap */
+                               fails, extended (tau <- 2 tau + 1, at most Eq. 6) and recomputed;
+                               the bound also covers the end-corrected estimator (whose remainder
+                               is the smaller). On a bipartite graph (lambda* = 1: no bound and no
+                               Eq. 6 length) with SC_EST_END_CORRECTED, an edge is accepted by the
+                               tail estimate of sc_estimated_lengths instead (uncertified:
+                               report.uncertified) and extended up to opts.ell_cap */
 #define SC_ELL_CALTAU 4     /* the per-edge lengths of the graph's last sc_caltau (same eps; TGT only);
                                sources run the longest of their edges */
 
@@ -373,7 +374,8 @@ typedef struct sc_options {
 void sc_options_default(sc_options *opts);
 
 typedef struct sc_report {
-    int32_t ell_global;        /* longest per-edge length used */
+    int32_t ell_global;        /* longest per-edge length used (the learned policy: its cap, Eq. 6
+                                  or opts.ell_cap) */
     int32_t ell_min_source;    /* shortest / longest source run (hops) */
     int32_t ell_max_source;
     int32_t block_width;       /* B actually used */
@@ -478,22 +480,31 @@ sc_status sc_some_edges(sc_graph *g, const sc_options *opts, int64_t count, cons
  *                   stream; each graph's lambda estimate is computed if the
  *                   Eq. 6 length needs it and none is cached.
  *   opts          : as sc_all_edges, for every graph; mode SC_MODE_TGT,
- *                   policy SC_ELL_GLOBAL (each graph its own Eq. 6 length)
- *                   or SC_ELL_FIXED; no TMA-gather split.
+ *                   policy SC_ELL_GLOBAL (each graph its own Eq. 6 length),
+ *                   SC_ELL_FIXED, or SC_ELL_LEARNED (each graph its own
+ *                   loaded model; every edge checked as in sc_all_edges, by
+ *                   the bound with the graph's lambda* or, on a bipartite
+ *                   graph, by the tail estimate with the end-corrected
+ *                   estimator; failing edges of all graphs are extended and
+ *                   rerun together); no TMA-gather split.
  *   ell_per_graph : nullable; count entries; > 0 overrides graph i's length
  *                   (e.g. an empirical length for a bipartite lattice, whose
- *                   Eq. 6 length does not exist), 0 keeps the policy.
+ *                   Eq. 6 length does not exist), 0 keeps the policy. With
+ *                   SC_ELL_LEARNED it is graph i's cap (its longest length;
+ *                   default Eq. 6, or opts.ell_cap on a bipartite graph).
  *   s_hat         : count pointers; s_hat[i] holds graphs[i]'s nnz values,
  *                   host or device per SC_OUT_DEVICE (caller-owned).
  *   reports       : nullable; count reports. Per graph: ell_global,
  *                   ell_min/max_source, blocks, source_hops, foster_sum,
- *                   lambda_star; launches, hops, hop_launches, bytes and
- *                   times hold the batch totals in every report.
- * Errors: SC_ERR_UNSUPPORTED for TGT+, the learned policy, or a bipartite
- * graph under SC_ELL_GLOBAL without an override; SC_ERR_INVALID_ARG for
- * NULL inputs, mixed devices, negative lengths or a union of 2^31 nodes or
- * entries; SC_ERR_OOM / SC_ERR_CUDA as elsewhere. Outputs are unspecified
- * on error.
+ *                   lambda_star, uncertified; launches, hops, hop_launches,
+ *                   bytes, times, extension_rounds and edges_extended hold
+ *                   the batch totals in every report.
+ * Errors: SC_ERR_UNSUPPORTED for TGT+, a bipartite graph under SC_ELL_GLOBAL
+ * without an override, or under SC_ELL_LEARNED without the end-corrected
+ * estimator; SC_ERR_INVALID_ARG for NULL inputs, mixed devices, negative
+ * lengths, a learned batch with a graph that has no model or a bipartite
+ * graph without an odd cap >= 3, or a union of 2^31 nodes or entries;
+ * SC_ERR_OOM / SC_ERR_CUDA as elsewhere. Outputs are unspecified on error.
  */
 sc_status sc_batch_all_edges(sc_graph *const *graphs, int32_t count, const sc_options *opts,
                              const int32_t *ell_per_graph, double *const *s_hat, sc_report *reports);
@@ -508,10 +519,11 @@ sc_status sc_batch_all_edges(sc_graph *const *graphs, int32_t count, const sc_op
 #define SC_MLP_MODEL_FLOATS (SC_MLP_PARAMS + 2 * SC_MLP_FEATURES)
 
 /*
- * sc_source_features -- the model's inputs for every node, host float[n * 6]:
- * log d_i, log min_{j in N(i)} d_j, local clustering, log(sum_{j in N(i)} d_j / 2m),
- * p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j, log(1 / (1 - lambda_plus)).
- * Runs sc_estimate_lambda first if needed.
+ * sc_source_features -- the model's inputs for every node, host float[n * 6],
+ * each local and independent of the graph's size: log d_i, log min_{j in N(i)} d_j,
+ * local clustering, log((sum_{j in N(i)} d_j / d_i) / (2m / n)) (mean neighbour
+ * degree over the mean degree), p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j, and
+ * p_3(i,i) = (1/d_i) sum over the triangles (i, j, k) of 1/(d_j d_k).
  */
 sc_status sc_source_features(sc_graph *g, float *features);
 

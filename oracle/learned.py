@@ -16,13 +16,14 @@ traversed. An edge is certified at the least odd tau where the bound is at
 most eps. The label of source i is the largest certified length over its
 edges; a small MLP predicts it from six per-source features.
 
-Features (in this order):
+Features (in this order; all local and independent of the graph's size, so
+that a model trained on a smaller graph of a family serves a larger one):
   0  log d_i
   1  log min_{j in N(i)} d_j
   2  local clustering c_i = triangles(i) / (d_i (d_i - 1) / 2) (0 for d_i < 2)
-  3  log(sum_{j in N(i)} d_j / (2m))      (share of the volume one hop reaches)
+  3  log((sum_{j in N(i)} d_j / d_i) / (2m / n))  (mean neighbour degree over the mean degree)
   4  p_2(i, i) = (1/d_i) sum_{j in N(i)} 1/d_j
-  5  log(1 / (1 - lambda_plus))          (the graph's spectral gap)
+  5  p_3(i, i) = (1/d_i) sum over triangles (i, j, k) of 1/(d_j d_k)
 
 Network: inputs standardised with the training set's mean and standard
 deviation, then 6 -> 32 -> 32 -> 1 with ReLU after the two hidden layers; the
@@ -73,28 +74,30 @@ NF = 6
 NPARAM = H * NF + H + H * H + H + H + 1
 
 
-def features(n, row_ptr, col_idx, lam_plus):
+def features(n, row_ptr, col_idx):
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     col_idx = np.asarray(col_idx, dtype=np.int64)
     deg = np.diff(row_ptr).astype(np.float64)
-    two_m = deg.sum()
+    mean_deg = deg.sum() / n
     F = np.zeros((n, NF))
     for i in range(n):
         nb = col_idx[row_ptr[i]:row_ptr[i + 1]]
         d = deg[i]
         tri = 0
+        cyc = 0.0
         s = set(nb.tolist())
         for j in nb:
             for y in col_idx[row_ptr[j]:row_ptr[j + 1]]:
-                if y in s:
+                if y in s:  # the walk i -> j -> y -> i
                     tri += 1
+                    cyc += 1.0 / (deg[j] * deg[y])
         tri //= 2  # each triangle at i is seen from both of its other corners
         F[i, 0] = math.log(d)
         F[i, 1] = math.log(deg[nb].min())
         F[i, 2] = tri / (d * (d - 1) / 2.0) if d >= 2 else 0.0
-        F[i, 3] = math.log(deg[nb].sum() / two_m)
+        F[i, 3] = math.log(deg[nb].sum() / d / mean_deg)
         F[i, 4] = np.sum(1.0 / deg[nb]) / d
-        F[i, 5] = math.log(1.0 / (1.0 - lam_plus))
+        F[i, 5] = cyc / d
     return F
 
 

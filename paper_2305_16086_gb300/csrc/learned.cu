@@ -11,11 +11,14 @@
 // and the acceptance come from the power-law tail estimate of the
 // end-corrected series (sc_estimated_lengths), an estimate, not a bound.
 //
-// Features of source i: log d_i; log min_{j in N(i)} d_j; local clustering;
-// log(sum_{j in N(i)} d_j / 2m); p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j;
-// log(1 / (1 - lambda_plus)). Flat parameters (float): W1[32][6], b1[32],
-// W2[32][32], b2[32], W3[32], b3; the model adds the features' mean and
-// standard deviation used to standardise the inputs.
+// Features of source i, all local and independent of the graph's size (a
+// model trained on a smaller graph of a family serves a larger one): log d_i;
+// log min_{j in N(i)} d_j; local clustering; log of the mean neighbour degree
+// over the mean degree, log((sum_{j in N(i)} d_j / d_i) / (2m / n));
+// p_2(i,i) = (1/d_i) sum_{j in N(i)} 1/d_j; p_3(i,i) = (1/d_i) sum over the
+// triangles (i, j, k) of 1/(d_j d_k). Flat parameters (float): W1[32][6],
+// b1[32], W2[32][32], b2[32], W3[32], b3; the model adds the features' mean
+// and standard deviation used to standardise the inputs.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -24,7 +27,6 @@
 
 namespace sc {
 
-sc_status estimate_lambda_impl(sc_graph *g, const sc_lambda_opts *opts, sc_lambda *out);
 void certified_lengths_impl(sc_graph *g, double eps, int precision, int32_t *per_entry_dev, int32_t *cap_out);
 void estimated_lengths_impl(sc_graph *g, double eps, int precision, int32_t cap, int32_t *per_entry_dev);
 
@@ -50,7 +52,7 @@ __device__ __forceinline__ bool contains(const int32_t *__restrict__ col, int32_
 }
 
 __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
-                           double two_m, double f5, float *__restrict__ out) {
+                           double mean_deg, float *__restrict__ out) {
     const int32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -58,7 +60,7 @@ __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *_
     const double d = static_cast<double>(ie - ib);
     int32_t dmin = INT32_MAX;
     long long vol = 0, tri2 = 0;
-    double inv_sum = 0.0;
+    double inv_sum = 0.0, cyc3 = 0.0;
     for (int32_t k = ib + lane; k < ie; k += 32) {
         const int32_t j = col[k];
         const int32_t jb = row_ptr[j], je = row_ptr[j + 1];
@@ -66,11 +68,17 @@ __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *_
         dmin = min(dmin, dj);
         vol += dj;
         inv_sum += 1.0 / static_cast<double>(dj);
-        // |N(i) & N(j)|: walk the shorter list, search the longer one
-        if (dj <= ie - ib) {
-            for (int32_t e = jb; e < je; ++e) tri2 += contains(col, ib, ie, col[e]) ? 1 : 0;
-        } else {
-            for (int32_t e = ib; e < ie; ++e) tri2 += contains(col, jb, je, col[e]) ? 1 : 0;
+        // the common neighbours x of i and j: walk the shorter list, search the longer one;
+        // each closes the triangle (i, j, x), which adds 1 / (d_j d_x) to p_3(i,i) d_i
+        const bool walk_j = dj <= ie - ib;
+        const int32_t wb = walk_j ? jb : ib, we = walk_j ? je : ie;
+        const int32_t sb = walk_j ? ib : jb, se = walk_j ? ie : je;
+        for (int32_t e = wb; e < we; ++e) {
+            const int32_t x = col[e];
+            if (contains(col, sb, se, x)) {
+                ++tri2;
+                cyc3 += 1.0 / (static_cast<double>(dj) * static_cast<double>(row_ptr[x + 1] - row_ptr[x]));
+            }
         }
     }
 #pragma unroll
@@ -79,15 +87,16 @@ __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *_
         vol += __shfl_xor_sync(0xffffffffu, vol, o);
         tri2 += __shfl_xor_sync(0xffffffffu, tri2, o);
         inv_sum += __shfl_xor_sync(0xffffffffu, inv_sum, o);
+        cyc3 += __shfl_xor_sync(0xffffffffu, cyc3, o);
     }
     if (lane == 0) {
         float *f = out + static_cast<int64_t>(i) * kF;
         f[0] = static_cast<float>(log(d));
         f[1] = static_cast<float>(log(static_cast<double>(dmin)));
         f[2] = d >= 2.0 ? static_cast<float>((static_cast<double>(tri2) / 2.0) / (d * (d - 1.0) / 2.0)) : 0.0f;
-        f[3] = static_cast<float>(log(static_cast<double>(vol) / two_m));
+        f[3] = static_cast<float>(log(static_cast<double>(vol) / d / mean_deg));
         f[4] = static_cast<float>(inv_sum / d);
-        f[5] = static_cast<float>(f5);
+        f[5] = static_cast<float>(cyc3 / d);
     }
 }
 
@@ -261,16 +270,9 @@ __global__ void k_mlp_predict(const float *__restrict__ model, const float *__re
 // ---------------------------------------------------------------------------
 static void ensure_features(sc_graph *g, cudaStream_t s) {
     if (g->features_ready) return;
-    if (!g->has_lambda) {
-        sc_lambda lam;
-        sc_status st = estimate_lambda_impl(g, nullptr, &lam);
-        if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
-    }
-    const double lp = g->lam.lambda_plus;
-    if (!(lp < 1.0)) SC_FAIL(SC_ERR_UNSUPPORTED, "lambda_plus >= 1");
     g->features.reserve(static_cast<size_t>(g->n) * kF);
     k_features<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->n,
-                                                 static_cast<double>(g->nnz), log(1.0 / (1.0 - lp)),
+                                                 static_cast<double>(g->nnz) / static_cast<double>(g->n),
                                                  g->features.get());
     SC_LAUNCH_CHECK();
     SC_CUDA(cudaStreamSynchronize(s));

@@ -673,14 +673,17 @@ __global__ void k_tau_min_of_sources(const int32_t *__restrict__ row_ptr, const 
 // its row is marked for a rerun. Both directions of an edge carry the same
 // bound, so both endpoints are marked.
 // With `active` (a subset of the sources was run), only entries whose two
-// endpoints were both run are checked.
+// endpoints were both run are checked. cap_row (nullable): a cap per row (the
+// graphs of a batch; both endpoints of an edge lie in one graph), else cap.
 __global__ void k_extend_failing(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                 const double *__restrict__ bound, int32_t n, double eps, int32_t cap,
+                                 const double *__restrict__ bound, int32_t n, double eps, int32_t cap_all,
                                  const int32_t *__restrict__ active, int32_t *__restrict__ tau,
-                                 int32_t *__restrict__ row_flag, unsigned long long *count) {
+                                 int32_t *__restrict__ row_flag, unsigned long long *count,
+                                 const int32_t *__restrict__ cap_row = nullptr) {
     const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
+    const int32_t cap = cap_row ? cap_row[r] : cap_all;
     int any = 0;
     unsigned long long c = 0;
     const bool row_on = !active || active[r];
@@ -719,30 +722,6 @@ __device__ __forceinline__ double tail_estimate(double qp, double q, int32_t tau
     return q * (x + 1.0) * exp((p - 1.0) * log((x + 1.0) / x)) / (2.0 * (p - 1.0));
 }
 
-// per entry: est[k] = tail_estimate of its edge from the records of hops
-// tau-1, tau (pre[2k], pre[2k+1]) and tau+1, tau+2 (t1, t2) of both halves,
-// each combined as t_l(e) = h_l[k] / d_i + h_l[rev k] / d_j (the same
-// commutative expression in both directions)
-__global__ void k_tail_estimate(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
-                                const double *__restrict__ pre, const double *__restrict__ t1,
-                                const double *__restrict__ t2, const int32_t *__restrict__ tau, int32_t n,
-                                double *__restrict__ est) {
-    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= n) return;
-    const double ir = inv_d[r];
-    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
-        const int32_t kr = rev[k];
-        const double ij = inv_d[col[k]];
-        auto full = [&](double a, double b) { return __dadd_rn(__dmul_rn(a, ir), __dmul_rn(b, ij)); };
-        const double qp = __dadd_rn(full(pre[2 * static_cast<int64_t>(k)], pre[2 * static_cast<int64_t>(kr)]),
-                                    full(pre[2 * static_cast<int64_t>(k) + 1], pre[2 * static_cast<int64_t>(kr) + 1]));
-        const double q = __dadd_rn(full(t1[k], t1[kr]), full(t2[k], t2[kr]));
-        est[k] = tail_estimate(qp, q, tau[k]);
-    }
-}
-
 // training labels on a bipartite graph: every source ran cap + 2 hops with all
 // hop terms recorded (rec[k * stride + l]); each entry takes the least odd
 // tau in [3, cap] whose tail estimate is at most eps, else cap
@@ -769,6 +748,44 @@ __global__ void k_estimate_lengths(const int32_t *__restrict__ row_ptr, const in
             }
         }
         tau_out[k] = t;
+    }
+}
+
+// The learned policy's test value per entry: rows whose graph has factor
+// f >= 0 take the bound f (t_{tau-1} + t_tau) (R6', f = lambda*^2 / (1 -
+// lambda*^2), which also bounds the end-corrected remainder, smaller than the
+// plain one); rows with f < 0 (a bipartite graph) take the tail estimate of
+// the end-corrected series. f = fac[r] (a batch's union of graphs) or fac_all.
+// The terms of hops tau-1, tau are in t1 / t2 (record mode 1) or in pre (mode
+// 3, whose t1 / t2 hold hops tau+1, tau+2). Both directions of an edge
+// evaluate the same expression.
+__global__ void k_learned_check(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                const int32_t *__restrict__ rev, const double *__restrict__ inv_d,
+                                const double *__restrict__ pre, const double *__restrict__ t1,
+                                const double *__restrict__ t2, int mode, const double *__restrict__ fac,
+                                double fac_all, const int32_t *__restrict__ tau, int32_t n,
+                                double *__restrict__ out) {
+    const int32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const double ir = inv_d[r];
+    const double f = fac ? fac[r] : fac_all;
+    for (int32_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
+        const int32_t kr = rev[k];
+        const double ij = inv_d[col[k]];
+        auto full = [&](double a, double b) { return __dadd_rn(__dmul_rn(a, ir), __dmul_rn(b, ij)); };
+        double qp;
+        if (mode == 3)
+            qp = __dadd_rn(full(pre[2 * static_cast<int64_t>(k)], pre[2 * static_cast<int64_t>(kr)]),
+                           full(pre[2 * static_cast<int64_t>(k) + 1], pre[2 * static_cast<int64_t>(kr) + 1]));
+        else
+            qp = __dadd_rn(full(t1[k], t1[kr]), full(t2[k], t2[kr]));
+        if (f >= 0.0) {
+            out[k] = __dmul_rn(f, qp);
+        } else {
+            const double q = __dadd_rn(full(t1[k], t1[kr]), full(t2[k], t2[kr]));
+            out[k] = tail_estimate(qp, q, tau[k]);
+        }
     }
 }
 
@@ -1584,10 +1601,13 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     const bool learned = o.ell_policy == SC_ELL_LEARNED;
     if (learned && !g->mlp_loaded) SC_FAIL(SC_ERR_INVALID_ARG, "no model loaded: call sc_mlp_load first");
     // a bipartite graph has no bound and no a-priori length: the learned lengths are
-    // accepted by the tail estimate (end-corrected estimator) and capped by opts.ell_cap
+    // accepted by the tail estimate (end-corrected estimator) and capped by opts.ell_cap.
+    // With the end-corrected estimator the learned policy records hops tau-1 .. tau+2
+    // (mode 3): the bound of R6' or the tail estimate, and the end correction
     const bool est_learned = learned && g->bipartite;
-    if (learned && !est_learned && o.estimator != SC_EST_PLAIN)
-        SC_FAIL(SC_ERR_UNSUPPORTED, "the learned length certifies the plain estimator");
+    const bool learned3 = learned && !plus && o.estimator == SC_EST_END_CORRECTED;
+    if (learned && plus && o.estimator != SC_EST_PLAIN)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ at learned lengths certifies the plain estimator");
     if (est_learned && plus) SC_FAIL(SC_ERR_UNSUPPORTED, "TGT+ needs lambda_star < 1: the graph is bipartite");
     if (est_learned && o.estimator != SC_EST_END_CORRECTED)
         SC_FAIL(SC_ERR_UNSUPPORTED, "the learned length on a bipartite graph needs the end-corrected estimator");
@@ -1698,14 +1718,14 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         rec_all = even_rec.get();
         rec_stride = even_stride;
     }
-    // the tail estimate of a bipartite graph reads the terms of hops tau-1, tau (and tau+1, tau+2)
+    // mode 3 records the terms of hops tau-1, tau here (and tau+1, tau+2 in t1 / t2)
     DevBuf<double> pre_rec;
-    if (est_learned) {
+    if (learned3) {
         pre_rec.reserve(static_cast<size_t>(nnz) * 2);
         rec_all = pre_rec.get();
         rec_stride = 2;
     }
-    const GatherRec rec{learned_plus ? 2 : (est_learned ? 3 : (learned ? 1 : 0)), rec_all, rec_stride};
+    const GatherRec rec{learned_plus ? 2 : (learned3 ? 3 : (learned ? 1 : 0)), rec_all, rec_stride};
     g->acc_g.reserve(nnz);
     g->acc_t1.reserve(nnz);
     g->acc_t2.reserve(nnz);
@@ -1835,7 +1855,7 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     // q / (1 - lambda*^2); learned (records of hops tau-1, tau): lambda*^2 / (1 - lambda*^2) (t_{tau-1} + t_tau).
     // lambda_plus carries its Ritz residual as a safety margin.
     double bound_scale = 0.0;
-    if (learned && !plus && !est_learned) {
+    if (learned && !plus && !learned3) {
         bound_scale = lam_star * lam_star / (1.0 - lam_star * lam_star);
     } else if (record_after) {
         const double lp = g->lam.lambda_plus + std::max(g->lam.residual_plus, 0.0);
@@ -1905,10 +1925,12 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
         g->tp_counters.reserve(4);
         std::vector<int32_t> h_flag(n);
         while (true) {
-            if (est_learned) {  // the bound column takes the tail estimate
-                k_tail_estimate<<<ceil_div(n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), g->rev.get(),
-                                                               g->inv_deg_d.get(), pre_rec.get(), g->acc_t1.get(),
-                                                               g->acc_t2.get(), g->tau_entry.get(), n, d_b);
+            if (learned3) {  // the bound column: R6' from the recorded hops, or the tail estimate
+                k_learned_check<<<ceil_div(n, 8), 256, 0, s>>>(
+                    g->row_ptr.get(), g->col_idx.get(), g->rev.get(), g->inv_deg_d.get(), pre_rec.get(),
+                    g->acc_t1.get(), g->acc_t2.get(), 3, nullptr,
+                    est_learned ? -1.0 : lam_star * lam_star / (1.0 - lam_star * lam_star), g->tau_entry.get(), n,
+                    d_b);
                 SC_LAUNCH_CHECK();
                 R.launches += 1;
             }
@@ -2160,8 +2182,9 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     if (o.precision < SC_PREC_FP64 || o.precision > SC_PREC_BF16) SC_FAIL(SC_ERR_INVALID_ARG, "precision %d", o.precision);
     if (o.bf16_from_hop < 0) SC_FAIL(SC_ERR_INVALID_ARG, "bf16_from_hop %d < 0", o.bf16_from_hop);
     if (o.mode != SC_MODE_TGT) SC_FAIL(SC_ERR_UNSUPPORTED, "batches run TGT (Algorithm 2) only");
-    if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_FIXED)
-        SC_FAIL(SC_ERR_UNSUPPORTED, "batches take the Eq. 6 or a fixed length");
+    const bool learned = o.ell_policy == SC_ELL_LEARNED;
+    if (o.ell_policy != SC_ELL_GLOBAL && o.ell_policy != SC_ELL_FIXED && !learned)
+        SC_FAIL(SC_ERR_UNSUPPORTED, "batches take the Eq. 6, a fixed or the learned length");
     if (o.ell_policy == SC_ELL_FIXED && o.ell_fixed < 0) SC_FAIL(SC_ERR_INVALID_ARG, "ell_fixed < 0");
     if (o.estimator != SC_EST_PLAIN && o.estimator != SC_EST_END_CORRECTED) SC_FAIL(SC_ERR_INVALID_ARG, "estimator");
     if (o.rows_split == -1) SC_FAIL(SC_ERR_UNSUPPORTED, "the TMA-gather hop has no windowed form");
@@ -2193,7 +2216,9 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     } evg{ev0, ev1, ev2};
     SC_CUDA(cudaEventRecord(ev0, s));
 
-    // ---- per-graph lengths: an override, the fixed length, or Eq. 6 with the graph's own lambda*
+    // ---- per-graph lengths: an override, the fixed length, or Eq. 6 with the graph's own lambda*;
+    // with the learned policy these are the caps (Eq. 6; on a bipartite graph opts.ell_cap or the
+    // override) and each source takes its model's prediction
     std::vector<int32_t> ell(count);
     std::vector<double> lam(count, 0.0);
     std::vector<int64_t> n_off(count + 1, 0), k_off(count + 1, 0);
@@ -2202,7 +2227,31 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
         sc_graph *g = graphs[i];
         SC_CUDA(cudaStreamSynchronize(g->stream));
         const int32_t over = ell_per_graph ? ell_per_graph[i] : 0;
-        if (over > 0) {
+        if (learned) {
+            if (!g->mlp_loaded) SC_FAIL(SC_ERR_INVALID_ARG, "graph %d: no model loaded: call sc_mlp_load first", i);
+            if (!g->has_lambda) {
+                sc_lambda l;
+                sc_status st = estimate_lambda_impl(g, nullptr, &l);
+                if (st != SC_OK && st != SC_ERR_LAMBDA_NOT_CONVERGED) throw Failure{st};
+            }
+            if (g->bipartite) {
+                if (o.estimator != SC_EST_END_CORRECTED)
+                    SC_FAIL(SC_ERR_UNSUPPORTED, "graph %d is bipartite: the learned length needs the end-corrected "
+                                                "estimator", i);
+                ell[i] = over > 0 ? over : o.ell_cap;
+                if (ell[i] < 3 || (ell[i] & 1) == 0)
+                    SC_FAIL(SC_ERR_INVALID_ARG, "graph %d is bipartite: its cap (ell_cap or the override) must be odd "
+                                                "and >= 3, got %d", i, ell[i]);
+            } else {
+                if (g->lam.lambda_star >= 1.0) SC_FAIL(SC_ERR_UNSUPPORTED, "graph %d: lambda_star >= 1", i);
+                lam[i] = g->lam.lambda_star;
+                g->tau_entry.reserve(g->nnz);
+                DevBuf<int32_t> ts;
+                ts.reserve(g->n);
+                tau_entries_device(g, o.eps, lam[i], g->tau_entry.get(), ts.get(), &ell[i]);
+                if (over > 0) ell[i] = over;
+            }
+        } else if (over > 0) {
             ell[i] = over;
         } else if (o.ell_policy == SC_ELL_FIXED) {
             ell[i] = o.ell_fixed;
@@ -2262,7 +2311,30 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     U->h_row_ptr[N] = static_cast<int32_t>(NNZ);
     SC_CUDA(cudaMemcpyAsync(U->row_ptr.get() + N, &U->h_row_ptr[N], sizeof(int32_t), cudaMemcpyHostToDevice, s));
     U->tau_entry.reserve(NNZ);
-    for (int32_t i = 0; i < count; ++i) fill_i32(U->tau_entry.get() + k_off[i], graphs[i]->nnz, ell[i], s);
+    std::vector<int32_t> len(N);
+    if (learned) {
+        // per source the model's length (at most the graph's cap), per edge the shorter of its two
+        for (int32_t i = 0; i < count; ++i) {
+            sc_graph *g = graphs[i];
+            DevBuf<int32_t> Ls;
+            Ls.reserve(g->n);
+            learned_lengths(g, ell[i], Ls.get(), s);
+            k_tau_min_of_sources<<<ceil_div(g->n, 8), 256, 0, s>>>(g->row_ptr.get(), g->col_idx.get(), Ls.get(), g->n,
+                                                                     U->tau_entry.get() + k_off[i]);
+            SC_LAUNCH_CHECK();
+        }
+        DevBuf<int32_t> ts;
+        ts.reserve(N);
+        k_row_max<<<ceil_div(N, 256), 256, 0, s>>>(U->row_ptr.get(), U->tau_entry.get(), N, ts.get());
+        SC_LAUNCH_CHECK();
+        SC_CUDA(cudaMemcpyAsync(len.data(), ts.get(), N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+    } else {
+        for (int32_t i = 0; i < count; ++i) {
+            fill_i32(U->tau_entry.get() + k_off[i], graphs[i]->nnz, ell[i], s);
+            std::fill(len.begin() + n_off[i], len.begin() + n_off[i + 1], ell[i]);
+        }
+    }
     const int heavy_t = o.heavy_threshold > 0 ? o.heavy_threshold : 256;
     ensure_row_order(U.get(), heavy_t);
     int32_t beta = 0;
@@ -2300,39 +2372,122 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
     R.plus = false;
     R.time_kernels = false;
     R.extra = extra;
-    R.rec = GatherRec{0, nullptr, 0};
+    // the learned policy's records: hops tau-1, tau (mode 1; mode 3 adds tau+1, tau+2 in t1 / t2
+    // for the end-corrected estimator and the tail estimate)
+    const int rec_mode = learned ? (record_after ? 3 : 1) : 0;
+    DevBuf<double> pre;
+    if (rec_mode == 3) pre.reserve(static_cast<size_t>(NNZ) * 2);
+    R.rec = GatherRec{rec_mode, rec_mode == 3 ? pre.get() : nullptr, rec_mode == 3 ? 2 : 0};
     R.capture = true;
     U->acc_g.reserve(NNZ);
     U->acc_t1.reserve(NNZ);
     U->acc_t2.reserve(NNZ);
     U->status.reserve(4);
     SC_CUDA(cudaMemsetAsync(U->status.get(), 0, 4 * sizeof(int32_t), s));
-    k_reset_rows<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), nullptr, N, U->tau_entry.get(), 0, U->acc_g.get(),
-                                                U->acc_t1.get(), U->acc_t2.get(), nullptr, 0);
+    k_reset_rows<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), nullptr, N, U->tau_entry.get(), rec_mode,
+                                                U->acc_g.get(), U->acc_t1.get(), U->acc_t2.get(), R.rec.all,
+                                                R.rec.stride);
     SC_LAUNCH_CHECK();
-    std::vector<int32_t> len(N), all(N);
+    std::vector<int32_t> all(N);
     std::iota(all.begin(), all.end(), 0);
     std::vector<int32_t> seg_start(count + 1);
-    for (int32_t i = 0; i < count; ++i) {
-        std::fill(len.begin() + n_off[i], len.begin() + n_off[i + 1], ell[i]);
-        seg_start[i] = static_cast<int32_t>(n_off[i]);
-    }
+    for (int32_t i = 0; i < count; ++i) seg_start[i] = static_cast<int32_t>(n_off[i]);
     seg_start[count] = N;
+    // per graph: source-hops, shortest and longest source run
+    std::vector<int64_t> g_hops(count, 0);
+    std::vector<int32_t> g_lmin(count, INT32_MAX), g_lmax(count, 0);
+    auto book = [&](const std::vector<int32_t> &src) {
+        int32_t i = 0;
+        for (int32_t v : src) {  // src is in id order: graphs in turn
+            while (v >= n_off[i + 1]) ++i;
+            const int32_t l = len[v] + extra;
+            g_hops[i] += l;
+            g_lmin[i] = std::min(g_lmin[i], l);
+            g_lmax[i] = std::max(g_lmax[i], l);
+        }
+    };
     SC_CUDA(cudaEventRecord(ev1, s));
     std::vector<char> seg_bip(count);
     for (int32_t i = 0; i < count; ++i) seg_bip[i] = graphs[i]->bipartite ? 1 : 0;
     run_blocks_win(R, all, len, seg_start, beta, seg_bip);
+    book(all);
 
-    // ---- combine, per-graph Foster sums, outputs
+    // ---- combine (and for the learned lengths the check / extension loop), Foster sums, outputs
     DevBuf<double> d_s, seg_sum;
     DevBuf<int64_t> d_off;
     d_s.reserve(NNZ);
     seg_sum.reserve(count);
     d_off.reserve(count + 1);
-    k_combine<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), U->col_idx.get(), U->rev.get(), U->inv_deg_d.get(),
-                                             U->acc_g.get(), U->acc_t1.get(), U->acc_t2.get(), N,
-                                             o.estimator == SC_EST_END_CORRECTED, record_after ? 1 : 0, 0.0, d_s.get(),
-                                             nullptr);
+    auto combine = [&] {
+        k_combine<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), U->col_idx.get(), U->rev.get(),
+                                                 U->inv_deg_d.get(), U->acc_g.get(), U->acc_t1.get(),
+                                                 U->acc_t2.get(), N, o.estimator == SC_EST_END_CORRECTED,
+                                                 record_after ? 1 : 0, 0.0, d_s.get(), nullptr);
+        SC_LAUNCH_CHECK();
+        R.launches += 1;
+    };
+    combine();
+    int32_t rounds = 0;
+    int64_t extended = 0;
+    if (learned) {
+        // per row: the bound factor of its graph (-1: bipartite, the tail estimate) and its cap
+        std::vector<double> h_fac(N);
+        std::vector<int32_t> h_cap(N);
+        for (int32_t i = 0; i < count; ++i) {
+            const double f = graphs[i]->bipartite ? -1.0 : lam[i] * lam[i] / (1.0 - lam[i] * lam[i]);
+            std::fill(h_fac.begin() + n_off[i], h_fac.begin() + n_off[i + 1], f);
+            std::fill(h_cap.begin() + n_off[i], h_cap.begin() + n_off[i + 1], ell[i]);
+        }
+        DevBuf<double> fac, d_b;
+        DevBuf<int32_t> cap_row, row_flag, rows, ts;
+        fac.reserve(N);
+        cap_row.reserve(N);
+        row_flag.reserve(N);
+        ts.reserve(N);
+        d_b.reserve(NNZ);
+        U->tp_counters.reserve(4);
+        SC_CUDA(cudaMemcpyAsync(fac.get(), h_fac.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+        SC_CUDA(cudaMemcpyAsync(cap_row.get(), h_cap.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        std::vector<int32_t> h_flag(N);
+        while (true) {
+            k_learned_check<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), U->col_idx.get(), U->rev.get(),
+                                                           U->inv_deg_d.get(), pre.get(), U->acc_t1.get(),
+                                                           U->acc_t2.get(), rec_mode, fac.get(), 0.0,
+                                                           U->tau_entry.get(), N, d_b.get());
+            SC_CUDA(cudaMemsetAsync(U->tp_counters.get(), 0, sizeof(long long), s));
+            k_extend_failing<<<ceil_div(N, 8), 256, 0, s>>>(U->row_ptr.get(), U->col_idx.get(), d_b.get(), N, o.eps, 0,
+                                                            nullptr, U->tau_entry.get(), row_flag.get(),
+                                                            reinterpret_cast<unsigned long long *>(
+                                                                U->tp_counters.get()),
+                                                            cap_row.get());
+            SC_LAUNCH_CHECK();
+            R.launches += 2;
+            long long failing = 0;
+            SC_CUDA(cudaMemcpyAsync(&failing, U->tp_counters.get(), sizeof(long long), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            if (failing == 0) break;
+            extended += failing / 2;
+            ++rounds;
+            SC_CUDA(cudaMemcpyAsync(h_flag.data(), row_flag.get(), N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            k_row_max<<<ceil_div(N, 256), 256, 0, s>>>(U->row_ptr.get(), U->tau_entry.get(), N, ts.get());
+            SC_LAUNCH_CHECK();
+            SC_CUDA(cudaMemcpyAsync(len.data(), ts.get(), N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SC_CUDA(cudaStreamSynchronize(s));
+            std::vector<int32_t> redo;
+            for (int32_t v = 0; v < N; ++v)
+                if (h_flag[v]) redo.push_back(v);
+            rows.reserve(redo.size());
+            SC_CUDA(cudaMemcpyAsync(rows.get(), redo.data(), redo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            k_reset_rows<<<ceil_div(static_cast<int64_t>(redo.size()), 8), 256, 0, s>>>(
+                U->row_ptr.get(), rows.get(), static_cast<int32_t>(redo.size()), U->tau_entry.get(), rec_mode,
+                U->acc_g.get(), U->acc_t1.get(), U->acc_t2.get(), R.rec.all, R.rec.stride);
+            SC_LAUNCH_CHECK();
+            R.launches += 2;
+            run_blocks_win(R, redo, len, seg_start, beta, seg_bip);
+            book(redo);
+            combine();
+        }
+    }
     SC_CUDA(cudaMemcpyAsync(d_off.get(), k_off.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     k_segment_sum<<<count, 256, 0, s>>>(d_s.get(), d_off.get(), seg_sum.get());
     SC_LAUNCH_CHECK();
@@ -2353,17 +2508,21 @@ static void batch_impl(sc_graph *const *graphs, int32_t count, const sc_options 
         for (int32_t i = 0; i < count; ++i) {
             sc_report *rep = reports + i;
             std::memset(rep, 0, sizeof(*rep));
-            rep->ell_global = ell[i];
-            rep->ell_min_source = ell[i] + extra;
-            rep->ell_max_source = ell[i] + extra;
+            rep->ell_global = ell[i];  // the length (the learned policy: the cap)
+            rep->ell_min_source = g_lmin[i] == INT32_MAX ? 0 : g_lmin[i];
+            rep->ell_max_source = g_lmax[i];
             rep->block_width = R.B;
             rep->rows_split = R.vpl;
             rep->slices = 0;
             rep->blocks = (graphs[i]->n + R.B - 1) / R.B;
-            rep->source_hops = static_cast<int64_t>(graphs[i]->n) * (ell[i] + extra);
+            rep->source_hops = g_hops[i];
             rep->foster_sum = 0.5 * foster[i];
             rep->lambda_star = lam[i];
             rep->windowed = 1;
+            rep->uncertified = learned && graphs[i]->bipartite ? 1 : 0;
+            // batch totals
+            rep->extension_rounds = rounds;
+            rep->edges_extended = static_cast<int32_t>(std::min<int64_t>(extended, INT32_MAX));
             // batch totals
             rep->launches = R.launches + 4 + 3 * count;
             rep->hops = R.hops;

@@ -224,6 +224,35 @@ __device__ __forceinline__ const T *slice_column(const T *x, int32_t n, const Sl
 // heavy rows from the id-sorted list and its light rows in natural order over
 // the window, skipping the heavy ones; rows are stored from the slice's base.
 // ---------------------------------------------------------------------------
+// The last entries [k, ce) of a row or chunk, fewer than U of them: loaded in
+// groups of U/2, U/4, ..., 1 entries (the binary digits of their count), each
+// group's loads in flight together, and added in entry order (the order of
+// the one-at-a-time loop, so every sum is unchanged bit for bit).
+template <typename T, int B, int VPL>
+__device__ __forceinline__ void add_tail(const int32_t *__restrict__ col, const uint4 *xp, int32_t k, int32_t ce,
+                                         int gl, typename Layout<T, B, VPL>::Acc *chunk) {
+    using L = Layout<T, B, VPL>;
+    constexpr int W = L::U / 2 > 0 ? L::U / 2 : 1;
+#pragma unroll
+    for (int w = W; w >= 1; w >>= 1) {
+        if (k + w <= ce) {
+            int32_t j[W];
+#pragma unroll
+            for (int u = 0; u < w; ++u) j[u] = col[k + u];
+            uint4 v[W][VPL];
+#pragma unroll
+            for (int u = 0; u < w; ++u)
+#pragma unroll
+                for (int p = 0; p < VPL; ++p) v[u][p] = ld_x(xp + static_cast<int64_t>(j[u]) * L::V + gl + p * L::LG);
+#pragma unroll
+            for (int u = 0; u < w; ++u)
+#pragma unroll
+                for (int p = 0; p < VPL; ++p) vadd(chunk + p * L::E, v[u][p], T());
+            k += w;
+        }
+    }
+}
+
 template <typename T, int B, int VPL, bool WIN>
 __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a) {
     using L = Layout<T, B, VPL>;
@@ -309,12 +338,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
 #pragma unroll
                         for (int p = 0; p < VPL; ++p) vadd(acc + p * L::E, v[u][p], T());
                 }
-                for (; k < ke; ++k) {
-                    const int32_t j = col[k];
-#pragma unroll
-                    for (int p = 0; p < VPL; ++p)
-                        vadd(acc + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
-                }
+                add_tail<T, B, VPL>(col, xp, k, ke, gl, acc);
             }
 #pragma unroll
             for (int p = 0; p < VPL; ++p)
@@ -393,12 +417,7 @@ __global__ void __launch_bounds__(kSpmmWarps * 32) k_spmm_hop(const HopArgs<T> a
                 }
             }
         }
-        for (; k < ce; ++k) {
-            const int32_t j = col[k];
-#pragma unroll
-            for (int p = 0; p < VPL; ++p)
-                vadd(chunk + p * L::E, ld_x(xp + static_cast<int64_t>(j) * L::V + gl + p * L::LG), T());
-        }
+        add_tail<T, B, VPL>(col, xp, k, ce, gl, chunk);
 #pragma unroll
         for (int q = 0; q < L::NACC; ++q) acc[q] += chunk[q];
         const Acc sc = a.inv_deg[cur];

@@ -134,9 +134,9 @@ def test_batch_rejections(cuda_lib):
         with pytest.raises(ScError) as ei:
             binding.batch_all_edges(Gs, [0, 21], eps=1e-3, mode="tgt_plus")
         assert ei.value.name == "SC_ERR_UNSUPPORTED"
-        with pytest.raises(ScError) as ei:
-            binding.batch_all_edges(Gs, [0, 21], eps=1e-3, policy="learned")
-        assert ei.value.name == "SC_ERR_UNSUPPORTED"
+        with pytest.raises(ScError) as ei:  # no model loaded
+            binding.batch_all_edges(Gs, None, eps=1e-3, policy="learned", estimator="end_corrected", ell_cap=63)
+        assert ei.value.name == "SC_ERR_INVALID_ARG"
         with pytest.raises(ScError) as ei:
             binding.batch_all_edges(Gs, [0, -3], eps=1e-3)
         assert ei.value.name == "SC_ERR_INVALID_ARG"
@@ -144,3 +144,52 @@ def test_batch_rejections(cuda_lib):
         assert reps[1]["ell_global"] == 21 and reps[0]["ell_global"] >= 1
     finally:
         _close(Gs)
+
+
+def _mixed_model(eps):
+    """One model for the three families, trained on one graph of each."""
+    from paper_2305_16086_gb300 import Graph, binding
+
+    ts = [gg.gnp_lcc(1500, 8.0, 31), gg.barabasi_albert(1500, 5, 32), gg.perturbed_grid(36, 40, 0.05, 33)]
+    Gt = [Graph(t.row_ptr, t.col_idx) for t in ts]
+    try:
+        for G, t in zip(Gt, ts):
+            G.estimate_lambda(allow_unconverged=bool(t.meta.get("bipartite")))
+        init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
+        model, _ = binding.mlp_train(Gt, init, epochs=300, lr=1e-2, eps=eps, precision="fp32", ell_cap=2047)
+    finally:
+        _close(Gt)
+    return model
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_learned_batch_equals_single_runs(cuda_lib, precision):
+    """The learned policy inside a batch: each graph's values, length report
+    and certification flag equal those of sc_all_edges on that graph alone with
+    the same model, bit for bit (an edge's length sequence depends only on its
+    own graph's values); every graph within eps of the dense oracle."""
+    from paper_2305_16086_gb300 import binding
+
+    eps = 1e-3
+    model = _mixed_model(eps)
+    gs = _mixed(9, 1000, 2500, 70)
+    Gs = _graphs(gs)
+    kw = dict(eps=eps, precision=precision, estimator="end_corrected", policy="learned", ell_cap=2047,
+              block_width=64, rows_split=1)
+    try:
+        for G in Gs:
+            G.estimate_lambda(allow_unconverged=True)
+            binding.mlp_load(G, model)
+        outs, reps = binding.batch_all_edges(Gs, None, **kw)
+        singles = [G.all_edges(**kw) for G in Gs]
+    finally:
+        _close(Gs)
+    assert max(r["extension_rounds"] for _, _, r in singles) >= 1  # the check extended something
+    assert reps[0]["extension_rounds"] == max(r["extension_rounds"] for _, _, r in singles)
+    for i, (g, out, rep, (s1, _, r1)) in enumerate(zip(gs, outs, reps, singles)):
+        assert np.array_equal(out, s1), i
+        assert rep["ell_global"] == r1["ell_global"], i  # the cap
+        assert (rep["ell_min_source"], rep["ell_max_source"]) == (r1["ell_min_source"], r1["ell_max_source"]), i
+        assert rep["uncertified"] == r1["uncertified"] == (1 if g.meta.get("bipartite") else 0), i
+        r = exact.exact_dense(g.n, g.row_ptr, g.col_idx)
+        assert np.max(np.abs(out - r)) <= eps, (i, g.name)

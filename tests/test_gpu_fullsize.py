@@ -6,17 +6,15 @@ the exact values; Theorem 3.2 for TGT, Theorem 4.4 for TGT+).
     FP32 blocks (the benchmark's configuration); Foster's mean error; the
     series at 40 edges; lambda against ARPACK.
   * 1000 x 1000 lattice, 5% of edges deleted (bipartite, slow mixing),
-    eps = 1e-2 at the empirical length 105 with the end-corrected estimator
-    (no length of Eq. 6 exists there): 500 sampled edges against sparse LU
-    (the solve cost caps the sample), the series at 16 edges.
-  * 512 graphs of uneven size in one batched call, eps = 1e-3: every graph's
-    maximum error, over all of its edges (dense oracle) when n <= 5,000 and
-    over 200 sampled edges above (LU for lattices, CG otherwise). The
-    lattices have no length of Eq. 6 (lambda* = 1); at 1001 hops 43 of the 170
-    exceed eps (up to 2.4e-3: on lattices of 1.7k - 15k nodes the slowest
-    mode has not decayed yet), and the errors measured at 1001 and 1501 hops
-    extrapolate to below 0.9e-3 by 2165 hops, so they run 2201 (R7's
-    empirical length).
+    eps = 1e-2 with the end-corrected estimator (no length of Eq. 6 exists
+    there), at the empirical length 105 and at learned lengths accepted by
+    the tail estimate: 500 sampled edges against sparse LU (the solve cost
+    caps the sample), the series at 16 edges.
+  * 512 graphs of uneven size in one batched call at learned lengths, eps =
+    1e-3: every graph's maximum error, over all of its edges (dense oracle)
+    when n <= 5,000 and over 200 sampled edges above (LU for lattices, CG
+    otherwise). The lattices (lambda* = 1) are accepted by the tail estimate
+    up to 4095 hops, the other graphs certified by the bound.
   * R-MAT scale 22 (n = 2.39 M, m = 64.2 M) with TGT+ walks, learned lengths
     and BF16 storage from hop 8: 128 sampled edges against CG (0.9 s of the
     host's 16 cores per edge), computed through sc_some_edges, which runs the
@@ -108,6 +106,24 @@ def test_lattice_1000_sampled_edges(cuda_lib):
     srcs = series.sources_for_pairs(pick[:16])
     ref, _ = series.series_entries(g.n, g.row_ptr, g.col_idx, ell, sources=srcs, end_corrected=True)
     assert np.max(np.abs(s[k[:16]] - ref[k[:16]])) < 1e-5
+    # the learned length on the same sample: a model trained on a 200 x 200 lattice (labels from
+    # the tail estimate), every edge accepted by the estimate (uncertified) or run to the cap
+    from paper_2305_16086_gb300 import binding
+
+    t = gg.perturbed_grid(200, 200, 0.05, 102)
+    init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
+    with _graph(t) as Gt:
+        Gt.estimate_lambda(allow_unconverged=True)
+        model, _ = binding.mlp_train([Gt], init, epochs=400, lr=1e-2, eps=eps, precision="fp32", ell_cap=511)
+    with _graph(g) as G:
+        G.estimate_lambda(allow_unconverged=True)
+        binding.mlp_load(G, model)
+        sl, _, rl = G.all_edges(eps=eps, policy="learned", precision="fp32", estimator="end_corrected",
+                                ell_cap=1023)
+    assert rl["uncertified"] == 1 and rl["windowed"] == 1
+    assert np.max(np.abs(sl[k] - r)) <= eps
+    assert np.all(sl[k] <= r + 1e-5)
+    assert rl["source_hops"] < rep["source_hops"]  # fewer hops than the global length 105 (+2 recorded)
 
 
 def test_batch_512_every_graph_within_eps(cuda_lib):
@@ -118,7 +134,7 @@ def test_batch_512_every_graph_within_eps(cuda_lib):
     from paper_2305_16086_gb300 import Graph, binding
 
     gs = gg.batch_graphs(512, 1000, 50_000, base_seed=4)
-    eps, lattice_ell = 1e-3, 2201
+    eps, lattice_cap = 1e-3, 4095
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {key: os.environ.get(key) for key in keys}
     os.environ.update({key: "2" for key in keys})  # eight workers of two threads share the host cores
@@ -126,13 +142,22 @@ def test_batch_512_every_graph_within_eps(cuda_lib):
         with cf.ProcessPoolExecutor(max_workers=8, mp_context=mp.get_context("spawn")) as ex:
             futs = [ex.submit(exact.reference_values, x.n, x.row_ptr, x.col_idx, 5000, 200, 100 + i,
                               bool(x.meta.get("bipartite")), 2) for i, x in enumerate(gs)]
-            # the GPU batch runs while the workers compute the exact values
+            # the GPU batch runs while the workers compute the exact values: the learned length,
+            # one model for the three families (trained on one graph of each, other seeds)
+            ts = [gg.gnp_lcc(5000, 8.0, 901), gg.barabasi_albert(5000, 5, 902), gg.perturbed_grid(70, 70, 0.05, 903)]
+            Gt = [Graph(t.row_ptr, t.col_idx) for t in ts]
+            for G, t in zip(Gt, ts):
+                G.estimate_lambda(allow_unconverged=bool(t.meta.get("bipartite")))
+            init = np.random.default_rng(0).normal(0.0, 0.2, binding.MLP_PARAMS).astype(np.float32)
+            model, _ = binding.mlp_train(Gt, init, epochs=400, lr=1e-2, eps=eps, precision="fp32", ell_cap=4095)
+            for G in Gt:
+                G.close()
             Gs = [Graph(x.row_ptr, x.col_idx) for x in gs]
-            ells = [lattice_ell if x.meta.get("bipartite") else 0 for x in gs]
-            for G, e in zip(Gs, ells):
-                if e == 0:
-                    G.estimate_lambda()
-            outs, reps = binding.batch_all_edges(Gs, ells, eps=eps, precision="fp32", estimator="end_corrected")
+            for G in Gs:
+                G.estimate_lambda(allow_unconverged=True)
+                binding.mlp_load(G, model)
+            outs, reps = binding.batch_all_edges(Gs, None, eps=eps, precision="fp32", estimator="end_corrected",
+                                                 policy="learned", ell_cap=lattice_cap)
             for G in Gs:
                 G.close()
             refs = [f.result() for f in futs]
@@ -146,6 +171,7 @@ def test_batch_512_every_graph_within_eps(cuda_lib):
     for x, out, (kk, vals), rep in zip(gs, outs, refs, reps):
         err = float(np.max(np.abs(out[kk] - vals)))
         assert err <= eps, (x.name, x.n, err)
+        assert rep["uncertified"] == (1 if x.meta.get("bipartite") else 0)
         assert np.all(out[kk] <= vals + 1e-5)  # odd lengths / end correction: lower bounds (up to FP32 error)
         worst = max(worst, err)
     assert len(refs) == 512 and worst > 0.0

@@ -37,7 +37,7 @@ def test_features_match_oracle(cuda_lib, maker):
     with _graph(g) as G:
         lam = G.estimate_lambda()
         F = binding.source_features(G)
-    ref = learned.features(*_csr(g), lam["lambda_plus"])
+    ref = learned.features(*_csr(g))
     assert np.allclose(F, ref, rtol=1e-5, atol=1e-6)
 
 
@@ -94,7 +94,7 @@ def test_training_on_gpu_tracks_the_oracle(cuda_lib):
         _, _, cap = binding.certified_lengths(G, 1e-3, "fp64")
     assert curve[-1] < 0.3 * curve[0]
     # the oracle's training from the same start on its own features and labels
-    F = learned.features(*_csr(g), lam["lambda_plus"])
+    F = learned.features(*_csr(g))
     y = np.log(learned.source_labels(g.n, g.row_ptr, learned.certified_lengths(*_csr(g), 1e-3, lam["lambda_star"], cap)))
     mu, sd = learned.standardise(F)
     X = (F - mu) / sd

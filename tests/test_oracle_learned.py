@@ -1,11 +1,15 @@
 """Pins for the learned-length oracle: features, certified lengths, MLP and Adam.
 
-  * features against their definitions on named graphs and against P^2;
+  * features against their definitions on named graphs, against P^2 and P^3,
+    and unchanged on two disjoint copies of a graph (no dependence on size);
   * per-hop terms against the series oracle and exact matrix powers;
   * certified lengths: the bound holds at tau_e, fails at tau_e - 2, and the
     truncated series at tau_e is within eps of the exact value;
   * the MLP gradient against central finite differences; Adam's first step
-    against its closed form.
+    against its closed form;
+  * the bipartite tail estimate against brute-force power-law sums, a
+    geometric tail, its special cases and the exact remainder on a lattice;
+    its labels by two routes; its extension loop within eps.
 """
 import numpy as np
 import pytest
@@ -23,33 +27,53 @@ def _P(g):
 
 
 def test_features_on_named_graphs():
-    F = learned.features(*_csr(gg.complete(6)), 0.3)
+    F = learned.features(*_csr(gg.complete(6)))
     assert np.allclose(F[:, 2], 1.0) and np.allclose(F[:, 0], np.log(5)) and np.allclose(F[:, 1], np.log(5))
-    F = learned.features(*_csr(gg.star(5)), 0.3)
+    assert np.allclose(F[:, 3], 0.0)  # regular: the neighbours' mean degree is the mean degree
+    assert np.allclose(F[:, 5], 4 / 25)  # K6: from i, 5 first steps, 4 closing second steps, 1/5 each
+    F = learned.features(*_csr(gg.star(5)))
     assert F[0, 2] == 0.0 and np.allclose(F[1:, 2], 0.0)  # no triangles; leaves have d = 1
-    assert np.isclose(F[0, 3], np.log(5 / 10)) and np.allclose(F[1:, 3], np.log(5 / 10))
+    # mean degree 10/6: the center's neighbours have degree 1, a leaf's neighbour degree 5
+    assert np.isclose(F[0, 3], np.log(1 / (10 / 6))) and np.allclose(F[1:, 3], np.log(5 / (10 / 6)))
+    assert np.allclose(F[:, 5], 0.0)  # a tree has no 3-cycles
     g = gg.barbell(4, 1)  # K4 - K4 joined by one edge: corner nodes lose clustering
-    F = learned.features(*_csr(g), 0.5)
+    F = learned.features(*_csr(g))
     assert np.isclose(F[0, 2], 1.0) and np.isclose(F[3, 2], 3 / 6)
-    assert np.allclose(F[:, 5], np.log(1 / (1 - 0.5)))
 
 
 def test_features_by_hand_on_lollipop():
-    # K4 on {0, 1, 2, 3} and the path 3 - 4 - 5: degrees 3, 3, 3, 4, 2, 1; 2m = 16
-    F = learned.features(*_csr(gg.lollipop(4, 2)), 0.4)
+    # K4 on {0, 1, 2, 3} and the path 3 - 4 - 5: degrees 3, 3, 3, 4, 2, 1; n = 6, 2m = 16
+    F = learned.features(*_csr(gg.lollipop(4, 2)))
     assert np.allclose(F[:, 0], np.log([3, 3, 3, 4, 2, 1]))
     assert np.allclose(F[:, 1], np.log([3, 3, 3, 2, 1, 2]))  # smallest neighbour degree
     assert np.allclose(F[:, 2], [1, 1, 1, 3 / 6, 0, 0])
-    assert np.allclose(F[:, 3], np.log(np.array([10, 10, 10, 11, 5, 2]) / 16))
+    mean_nb = np.array([10 / 3, 10 / 3, 10 / 3, 11 / 4, 5 / 2, 2 / 1])
+    assert np.allclose(F[:, 3], np.log(mean_nb / (16 / 6)))
     assert np.allclose(F[:, 4], [(1 / 3 + 1 / 3 + 1 / 4) / 3] * 3 + [(3 / 3 + 1 / 2) / 4, (1 / 4 + 1) / 2, 1 / 2])
+    # p_3(0,0): the triangles at 0 are (0,1,2), (0,1,3), (0,2,3), each walked both ways:
+    # 2 (1/(3*3) + 1/(3*4) + 1/(3*4)) / 3; node 3: triangles (3,0,1), (3,0,2), (3,1,2): 2 (3/9) / 4
+    p3_0 = 2 * (1 / 9 + 1 / 12 + 1 / 12) / 3
+    assert np.allclose(F[:, 5], [p3_0] * 3 + [2 * (3 / 9) / 4, 0.0, 0.0])
 
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_p2_feature_is_two_step_return_probability(seed):
     g = gg.tree_plus_gnp(50, 5.0, seed)
-    F = learned.features(*_csr(g), 0.2)
+    F = learned.features(*_csr(g))
     P = _P(g)
     assert np.allclose(F[:, 4], np.diag(P @ P), atol=1e-14)
+    assert np.allclose(F[:, 5], np.diag(P @ P @ P), atol=1e-14)
+
+
+def test_features_do_not_depend_on_the_graph_size():
+    """Two disjoint copies of a graph (as a larger graph of the family) give
+    every node the features it has in one copy."""
+    g = gg.tree_plus_gnp(60, 5.0, 3)
+    e = g.edges()
+    two = gg.from_edges(2 * g.n, np.concatenate([e[:, 0], e[:, 0] + g.n]), np.concatenate([e[:, 1], e[:, 1] + g.n]))
+    F1 = learned.features(*_csr(g))
+    F2 = learned.features(*_csr(two))
+    assert np.allclose(F2[:g.n], F1, atol=1e-14) and np.allclose(F2[g.n:], F1, atol=1e-14)
 
 
 def test_hop_terms_match_series_and_powers():
@@ -136,7 +160,7 @@ def test_training_reduces_loss_and_predictions_are_odd():
     lp, _, lam = truncation.spectrum_extremes(*_csr(g))
     cap = int(truncation.tau_entries(*_csr(g), 1e-3, lam).max())
     labels = learned.source_labels(g.n, g.row_ptr, learned.certified_lengths(*_csr(g), 1e-3, lam, cap))
-    F = learned.features(*_csr(g), lp)
+    F = learned.features(*_csr(g))
     mu, sd = learned.standardise(F)
     X = (F - mu) / sd
     y = np.log(labels)

@@ -93,6 +93,7 @@ TGTPLUS = [
 LEARNED = [
     ("features on named graphs", tl.test_features_on_named_graphs),
     ("features by hand", tl.test_features_by_hand_on_lollipop),
+    ("features independent of the size", tl.test_features_do_not_depend_on_the_graph_size),
     ("p2 feature = P^2", lambda: tl.test_p2_feature_is_two_step_return_probability(0)),
     ("hop terms vs powers", tl.test_hop_terms_match_series_and_powers),
     ("certified lengths", lambda: tl.test_certified_lengths(lambda: gg.tree_plus_gnp(500, 8.0, 2), 1e-2)),
@@ -307,8 +308,11 @@ PY_MUTANTS = [
      "F[i, 1] = math.log(deg[nb].min())", "F[i, 1] = math.log(deg[nb].max())"),
     ("learned", "p2 feature without 1/d_i", "learned",
      "F[i, 4] = np.sum(1.0 / deg[nb]) / d", "F[i, 4] = np.sum(1.0 / deg[nb])"),
-    ("learned", "volume feature over m", "learned",
-     "F[i, 3] = math.log(deg[nb].sum() / two_m)", "F[i, 3] = math.log(2.0 * deg[nb].sum() / two_m)"),
+    ("learned", "neighbour degree feature not per neighbour", "learned",
+     "F[i, 3] = math.log(deg[nb].sum() / d / mean_deg)", "F[i, 3] = math.log(deg[nb].sum() / mean_deg)"),
+    ("learned", "p3 feature with the closing node's degree twice", "learned",
+     "cyc += 1.0 / (deg[j] * deg[y])", "cyc += 1.0 / (deg[y] * deg[y])"),
+    ("learned", "p3 feature without 1/d_i", "learned", "F[i, 5] = cyc / d", "F[i, 5] = cyc"),
     ("learned", "backprop through W2 transposed", "learned",
      "dh1 = (dh2 @ W2) * (z1 > 0)", "dh1 = (dh2 @ W2.T) * (z1 > 0)"),
     ("learned", "ReLU gate of layer 2 dropped", "learned",
