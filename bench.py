@@ -70,7 +70,10 @@ KERNEL_SOURCES = ["paper_2305_16086_gb300/csrc/propagate.cuh", "paper_2305_16086
                   "paper_2305_16086_gb300/csrc/sparse_hops.cuh"]
 # kernel classes the library times separately (SC_KC_* order) and their kernels
 KERNEL_CLASSES = {"dense_hop": "k_spmm_hop", "mask_hop": "k_mask_scatter + k_hop2_mask", "sparse_hop": "k_hop_sparse",
-                  "ball_hop": "k_hop_ball", "last_hop": "k_last_diag + k_last_rows"}
+                  "ball_hop": "k_hop_ball", "last_hop": "k_last_diag + k_last_rows",
+                  "switch_test": "k_chi_tiles + k_chi_thresh + k_chi_select + k_chi_source + k_chi_entries "
+                                 "(+ the counts' copy and the host's wait)",
+                  "walks": "k_pack_counts + k_walk_chunks + k_walk_finish (+ the host's plan)"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spmm_hop_ba200k_traffic.json")
 
 

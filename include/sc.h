@@ -334,7 +334,10 @@ sc_status sc_series_meet(sc_graph *g, const int32_t *tau, double *s_out);
 #define SC_KC_SPARSE_HOP 2  /* hop 3 from the non-zero values of X_2 (k_hop_sparse) */
 #define SC_KC_BALL_HOP 3    /* hop L-1 on the two-hop balls (k_hop_ball) */
 #define SC_KC_LAST_HOP 4    /* the last hop where its gather reads it (k_last_diag + k_last_rows) */
-#define SC_KC_COUNT 5
+#define SC_KC_SWITCH_TEST 5 /* TGT+: a switch test (CalChi's column statistics, chi and R per entry, the
+                               copy of the counts and the host's wait for it) */
+#define SC_KC_WALKS 6       /* TGT+: a walk phase (walk counts, the host's plan, the walk kernels) */
+#define SC_KC_COUNT 7
 
 typedef struct sc_options {
     double eps;               /* absolute error target of Definition 2.2, 0 < eps < 1 */
@@ -579,10 +582,10 @@ typedef struct sc_mlp_train_opts {
  * the certified per-source lengths; sc_estimated_lengths on a bipartite
  * graph), standardises the features, and trains the MLP on the device (loss:
  * mean (y - log L*)^2 / 2; full-batch Adam). A feature constant over the
- * training set (such as the spectral feature of one graph) carries no
- * information: its first-layer weights are set to zero, which leaves the
- * training unchanged (its standardised input is 0) and makes the model
- * ignore it on other graphs.
+ * training set (such as the clustering of a lattice) carries no information:
+ * its first-layer weights are set to zero, which leaves the training
+ * unchanged (its standardised input is 0) and makes the model ignore it on
+ * other graphs.
  *   init_params : host float[SC_MLP_PARAMS], the starting weights (caller's choice)
  *   model_out   : host float[SC_MLP_MODEL_FLOATS]
  *   loss_curve  : host float[epochs], nullable: the loss before each step

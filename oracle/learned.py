@@ -208,7 +208,7 @@ def adam_step(theta, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 def standardise(F):
     """Mean and population standard deviation per feature. A spread at
     rounding level (below 1e-9 max(|mean|, 1)) marks a constant feature, such
-    as the graph-level spectral feature over one graph; it gets scale 1."""
+    as the clustering over a lattice; it gets scale 1."""
     mu = F.mean(axis=0)
     sd = F.std(axis=0)
     sd = np.where(sd > 1e-9 * np.maximum(np.abs(mu), 1.0), sd, 1.0)

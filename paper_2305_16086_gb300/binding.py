@@ -30,7 +30,7 @@ EST = {"plain": 0, "end_corrected": 1}
 MODE = {"tgt": 0, "tgt_plus": 1}
 SC_OUT_DEVICE, SC_OPT_RECORD_TAIL, SC_OPT_TIME_KERNELS = 1, 2, 4
 SC_OPT_WINDOWS_OFF, SC_OPT_WINDOWS_FORCE, SC_OPT_SPARSE_HOPS, SC_OPT_FULL_TOPGAMMA_SCAN = 8, 16, 32, 64
-KC_NAMES = ["dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop"]  # SC_KC_* order
+KC_NAMES = ["dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop", "switch_test", "walks"]  # SC_KC_* order
 
 # every symbol include/sc.h declares
 EXPORTS = [
@@ -88,8 +88,8 @@ class Report(ctypes.Structure):
                 ("switch_tests", ctypes.c_int32), ("switch_ms", ctypes.c_double), ("walk_ms", ctypes.c_double),
                 ("source_hops", ctypes.c_int64), ("extension_rounds", ctypes.c_int32), ("windowed", ctypes.c_int32),
                 ("walk_steps", ctypes.c_int64), ("walk_device_ms", ctypes.c_double),
-                ("kc_ms", ctypes.c_double * 5), ("kc_launches", ctypes.c_int64 * 5),
-                ("kc_bytes", ctypes.c_double * 5), ("uncertified", ctypes.c_int32),
+                ("kc_ms", ctypes.c_double * 7), ("kc_launches", ctypes.c_int64 * 7),
+                ("kc_bytes", ctypes.c_double * 7), ("uncertified", ctypes.c_int32),
                 ("reserved_r", ctypes.c_int32)]
 
     def as_dict(self):

@@ -1016,6 +1016,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
     auto hop_bytes_per_slice = [&](int32_t ell) {
         return csr_bytes + static_cast<double>(n) * B * (elem_size(prec_at(R, ell - 1)) + elem_size(prec_at(R, ell)));
     };
+    // a switch test reads the block X_ell once (the column statistics) and the degrees
+    auto test_bytes_per_slice = [&](int32_t ell) {
+        return static_cast<double>(n) * B * elem_size(prec_at(R, ell)) + 4.0 * n;
+    };
     const bool dense_only = (R.o->flags & SC_OPT_SPARSE_HOPS) == 0;
     const bool full_scan = (R.o->flags & SC_OPT_FULL_TOPGAMMA_SCAN) != 0;
     for (int64_t sb = 0; sb < nsuper; ++sb) {
@@ -1076,9 +1080,11 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 // ell-1 (their tau is capped there once the walk kernel has read it)
                 long long lhs = 0, rhs = 0, steps = 0;
                 const double t0 = wall_ms();
+                const int64_t tc = timer_open(R, s);
                 tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc,
                               g->tau_entry.get(), ell - 1, R.gamma, R.o->eps, R.log2md, full_scan, &lhs, &rhs,
                               &steps, s, vol_src.data(), rhs_src.data());
+                timer_close(R, tc, SC_KC_SWITCH_TEST, used_slices * test_bytes_per_slice(ell - 1), s);
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
                 R.launches += 4;
@@ -1094,12 +1100,14 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 }
                 if (nnow > 0) {
                     const double tw = wall_ms();
+                    const int64_t tw_ev = timer_open(R, s);
                     SC_CUDA(cudaEventRecord(ev_w0, s));
                     long long wsteps = 0;
                     const long long pairs = tgtplus_walks(g, prec_at(R, ell - 1), B, xa, src, now_list.data(), nsrc,
                                                           g->tau_entry.get(), ell - 1, R.o->seed, g->acc_g.get(), s,
                                                           &wsteps);
                     SC_CUDA(cudaEventRecord(ev_w1, s));
+                    timer_close(R, tw_ev, SC_KC_WALKS, 0.0, s);
                     SC_CUDA(cudaEventSynchronize(ev_w1));
                     R.walk_ms += wall_ms() - tw;
                     R.launches += 3;
@@ -1122,8 +1130,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                 // L - (ell-1) hops the walks would replace.
                 long long lhs = 0, rhs = 0, steps = 0;
                 const double t0 = wall_ms();
+                const int64_t tc = timer_open(R, s);
                 tgtplus_check(g, prec_at(R, ell - 1), B, xa, used_slices, src, h_src.data() + first, nsrc, g->tau_entry.get(),
                               ell - 1, R.gamma, R.o->eps, R.log2md, full_scan, &lhs, &rhs, &steps, s);
+                timer_close(R, tc, SC_KC_SWITCH_TEST, used_slices * test_bytes_per_slice(ell - 1), s);
                 R.switch_ms += wall_ms() - t0;
                 ++R.switch_tests;
                 R.launches += 3;
@@ -1203,11 +1213,13 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
             if (tt < L) {
                 // Algorithm 4's walk phase: walk tails from X_tt with the counts of the last check
                 const double t0 = wall_ms();
+                const int64_t tw_ev = timer_open(R, s);
                 SC_CUDA(cudaEventRecord(ev_w0, s));
                 long long wsteps = 0;
                 const long long pairs = tgtplus_walks(g, prec_at(R, tt), B, xa, src, h_src.data() + first, nsrc,
                                                       g->tau_entry.get(), tt, R.o->seed, g->acc_g.get(), s, &wsteps);
                 SC_CUDA(cudaEventRecord(ev_w1, s));
+                timer_close(R, tw_ev, SC_KC_WALKS, 0.0, s);
                 SC_CUDA(cudaEventSynchronize(ev_w1));
                 R.walk_ms += wall_ms() - t0;
                 R.launches += 3;

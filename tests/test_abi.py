@@ -116,7 +116,7 @@ int main(void) {
   P(SC_MODE_TGT) P(SC_MODE_TGT_PLUS) P(SC_SWITCH_COST) P(SC_SWITCH_PAPER) P(SC_SWITCH_PER_SOURCE)
   P(SC_OUT_DEVICE) P(SC_OPT_RECORD_TAIL) P(SC_OPT_TIME_KERNELS) P(SC_OPT_WINDOWS_OFF) P(SC_OPT_WINDOWS_FORCE)
   P(SC_OPT_SPARSE_HOPS) P(SC_OPT_FULL_TOPGAMMA_SCAN) P(SC_KC_DENSE_HOP) P(SC_KC_MASK_HOP) P(SC_KC_SPARSE_HOP) P(SC_KC_BALL_HOP) P(SC_KC_LAST_HOP)
-  P(SC_KC_COUNT)
+  P(SC_KC_SWITCH_TEST) P(SC_KC_WALKS) P(SC_KC_COUNT)
   P(SC_MLP_PARAMS) P(SC_MLP_FEATURES) P(SC_MLP_MODEL_FLOATS)
   return 0;
 }

@@ -32,7 +32,7 @@ class _Event:
 def _kc(kw):
     t = 1.0 if kw.get("time_kernels") else 0.0
     return {name: {"ms": t * (20.0 if name == "dense_hop" else 2.0), "launches": 4, "bytes": 4.0e8}
-            for name in ("dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop")}
+            for name in ("dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop", "switch_test", "walks")}
 
 
 def _report(kw):
@@ -151,7 +151,7 @@ def test_default_line_has_every_contract_key(fake_cuda):
     assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
     assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
     assert d["roofline"]["kernel_class"] == "dense_hop" and set(d["kernel_classes"]) == {
-        "dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop"}
+        "dense_hop", "mask_hop", "sparse_hop", "ball_hop", "last_hop", "switch_test", "walks"}
     assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"} and d["cpu_baseline"]["kind"] == "oracle"
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert list(d["e2e"]["phases_ms_of_a_warmup_pass"]) == ["create_validate", "lanczos", "model_load", "all_edges_d2h"]

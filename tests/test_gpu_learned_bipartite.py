@@ -114,7 +114,7 @@ def test_trained_model_within_eps_and_fewer_hops_than_the_global_length(cuda_lib
         model, curve = binding.mlp_train([Gt], init, epochs=300, lr=1e-2, eps=eps, precision="fp32", ell_cap=cap)
     assert curve[-1] < 0.5 * curve[0]
     W1 = model[:binding.MLP_PARAMS][:32 * 6].reshape(32, 6)
-    assert np.all(W1[:, 5] == 0.0)  # the spectral feature is constant over one graph: ignored
+    assert np.all(W1[:, 2] == 0.0) and np.all(W1[:, 5] == 0.0)  # no triangles on a lattice: constant, ignored
     r = exact.exact_dense(*_csr(test_g))
     with _graph(test_g) as G:
         G.estimate_lambda(allow_unconverged=True)
