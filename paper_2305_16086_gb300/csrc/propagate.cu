@@ -1022,6 +1022,10 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
     };
     const bool dense_only = (R.o->flags & SC_OPT_SPARSE_HOPS) == 0;
     const bool full_scan = (R.o->flags & SC_OPT_FULL_TOPGAMMA_SCAN) != 0;
+    // cost rule: the hop at which the previous block of the same length switched (-1: none
+    // yet). Blocks come longest first and neighbouring blocks switch within a hop of each
+    // other, so a block's tests start there instead of kCostRuleHops before its end.
+    int32_t prev_tt = -1, prev_L = -1;
     for (int64_t sb = 0; sb < nsuper; ++sb) {
         const int64_t first = sb * S;
         const int nsrc = static_cast<int>(std::min<int64_t>(S, ns - first));
@@ -1124,7 +1128,8 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
                     tt = ell - 1;
                     break;
                 }
-            } else if (R.plus && (paper_rule || ell - 1 >= std::max(1, L - kCostRuleHops))) {
+            } else if (R.plus && (paper_rule || (ell - 1 >= std::max(1, L - kCostRuleHops) &&
+                                                 (prev_L != L || prev_tt < 0 || ell - 1 >= prev_tt)))) {
                 // switch test after hop ell-1. Paper rule (Eq. 14): frontier volume against the
                 // sum of walk counts. Cost rule: predicted walk time against the time of the
                 // L - (ell-1) hops the walks would replace.
@@ -1210,6 +1215,8 @@ static void run_blocks(Run &R, std::vector<int32_t> sources, const std::vector<i
         } else if (R.plus) {
             R.tt_min = std::min(R.tt_min, tt);
             R.tt_max = std::max(R.tt_max, tt);
+            prev_L = L;
+            prev_tt = tt < L ? tt : -1;
             if (tt < L) {
                 // Algorithm 4's walk phase: walk tails from X_tt with the counts of the last check
                 const double t0 = wall_ms();
