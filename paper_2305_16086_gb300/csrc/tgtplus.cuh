@@ -222,49 +222,120 @@ __global__ void __launch_bounds__(kChiScanThreads)
 constexpr int kTileRows = 256;
 constexpr int kCandMax = 2048;
 
+// a 16-byte vector of stored values as accumulator-type elements, in memory order
+__device__ __forceinline__ void unpack16(const uint4 &v, float (&a)[4]) {
+    a[0] = __uint_as_float(v.x);
+    a[1] = __uint_as_float(v.y);
+    a[2] = __uint_as_float(v.z);
+    a[3] = __uint_as_float(v.w);
+}
+__device__ __forceinline__ void unpack16(const uint4 &v, double (&a)[2]) {
+    a[0] = __hiloint2double(static_cast<int>(v.y), static_cast<int>(v.x));
+    a[1] = __hiloint2double(static_cast<int>(v.w), static_cast<int>(v.z));
+}
+__device__ __forceinline__ void unpack16(const uint4 &v, float (&a)[8]) {  // bf16 pairs, low half first
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        a[2 * q] = __uint_as_float(w[q] << 16);
+        a[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+    }
+}
+
+// Per tile of kTileRows rows and column: maximum, minimum and frontier volume
+// (sum of d_x over the rows with X[x, c] != 0). Rows are read as 16-byte
+// vectors: LG lanes cover a row (VPL vectors each), a warp reads 32 / LG rows
+// per load and keeps UR such loads in flight; the lanes holding the same
+// columns are combined by shuffles, the warps through shared memory. Maxima,
+// minima and integer sums do not depend on the order of combination.
 template <typename T, int B>
 __global__ void __launch_bounds__(kChiScanThreads)
     k_chi_tiles(const int32_t *__restrict__ row_ptr, const T *__restrict__ x, int32_t n, double *__restrict__ tmax,
                 double *__restrict__ tmin, long long *__restrict__ tvol) {
     using V = typename AccOf<T>::type;
-    constexpr int TPC = kChiScanThreads / B;  // threads per column
-    const int c = threadIdx.x % B, sub = threadIdx.x / B;
+    constexpr int E = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte vector
+    constexpr int NV = B / E;                            // vectors per row
+    constexpr int LG = NV < 32 ? NV : 32;                // lanes per row
+    constexpr int VPL = NV / LG;                         // vectors per lane
+    constexpr int RPW = 32 / LG;                         // rows per warp load
+    constexpr int NW = kChiScanThreads / 32;
+    constexpr int UR = 8 / VPL;                          // row loads in flight per lane
+    constexpr int C = VPL * E;                           // columns per lane
+    static_assert(NV % LG == 0 && 32 % LG == 0, "row layout");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % LG, rsub = lane / LG;
     const int32_t r0 = blockIdx.x * kTileRows, r1 = min(n, r0 + kTileRows);
-    const T *xs = x + static_cast<int64_t>(blockIdx.y) * n * B;
-    V vmax = V(-INFINITY), vmin = V(INFINITY);
-    long long vol = 0;
-    constexpr int UR = 8;  // rows whose loads are in flight together
-    for (int32_t rb = r0 + sub; rb < r1; rb += TPC * UR) {
-        V v[UR];
+    const uint4 *xs = reinterpret_cast<const uint4 *>(x + static_cast<int64_t>(blockIdx.y) * n * B);
+    V vmax[C], vmin[C];
+    long long vol[C];
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+        vmax[e] = V(-INFINITY);
+        vmin[e] = V(INFINITY);
+        vol[e] = 0;
+    }
+    constexpr int STEP = NW * RPW;  // rows per round of the CTA's warps
+    for (int32_t rb = r0 + warp * RPW + rsub; rb < r1; rb += STEP * UR) {
+        uint4 v[UR][VPL];
         int32_t d[UR];
 #pragma unroll
         for (int u = 0; u < UR; ++u) {
-            const int32_t r = rb + u * TPC;
-            v[u] = r < r1 ? to_acc(xs[static_cast<int64_t>(r) * B + c]) : V(0);
-            d[u] = r < r1 ? row_ptr[r + 1] - row_ptr[r] : 0;
+            const int32_t r = rb + u * STEP;
+            const bool in = r < r1;
+            d[u] = in ? row_ptr[r + 1] - row_ptr[r] : 0;
+#pragma unroll
+            for (int p = 0; p < VPL; ++p)
+                v[u][p] = in ? __ldg(xs + static_cast<int64_t>(r) * NV + gl + p * LG) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < UR; ++u) {
-            if (rb + u * TPC < r1) {
-                vmax = max(vmax, v[u]);
-                vmin = min(vmin, v[u]);
-                if (v[u] != V(0)) vol += d[u];
+            if (rb + u * STEP >= r1) continue;
+#pragma unroll
+            for (int p = 0; p < VPL; ++p) {
+                V a[E];
+                unpack16(v[u][p], a);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = p * E + e;
+                    vmax[k] = max(vmax[k], a[e]);
+                    vmin[k] = min(vmin[k], a[e]);
+                    if (a[e] != V(0)) vol[k] += d[u];
+                }
             }
         }
     }
-    __shared__ double smax[kChiScanThreads], smin[kChiScanThreads];
-    __shared__ long long svol[kChiScanThreads];
-    smax[threadIdx.x] = static_cast<double>(vmax);
-    smin[threadIdx.x] = static_cast<double>(vmin);
-    svol[threadIdx.x] = vol;
+    // lanes rsub = 0 .. RPW-1 hold the same columns: combine them
+#pragma unroll
+    for (int o = LG; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            vmax[k] = max(vmax[k], __shfl_xor_sync(0xffffffffu, vmax[k], o));
+            vmin[k] = min(vmin[k], __shfl_xor_sync(0xffffffffu, vmin[k], o));
+            vol[k] += __shfl_xor_sync(0xffffffffu, vol[k], o);
+        }
+    }
+    __shared__ double smax[NW][B], smin[NW][B];
+    __shared__ long long svol[NW][B];
+    if (rsub == 0) {
+#pragma unroll
+        for (int p = 0; p < VPL; ++p)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = (gl + p * LG) * E + e;
+                smax[warp][c] = static_cast<double>(vmax[p * E + e]);
+                smin[warp][c] = static_cast<double>(vmin[p * E + e]);
+                svol[warp][c] = vol[p * E + e];
+            }
+    }
     __syncthreads();
-    if (sub == 0) {
-        double a = smax[c], b = smin[c];
-        long long w = svol[c];
-        for (int t = 1; t < TPC; ++t) {
-            a = fmax(a, smax[c + t * B]);
-            b = fmin(b, smin[c + t * B]);
-            w += svol[c + t * B];
+    for (int c = threadIdx.x; c < B; c += kChiScanThreads) {
+        double a = smax[0][c], b = smin[0][c];
+        long long w = svol[0][c];
+#pragma unroll
+        for (int q = 1; q < NW; ++q) {
+            a = fmax(a, smax[q][c]);
+            b = fmin(b, smin[q][c]);
+            w += svol[q][c];
         }
         const int64_t o = (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * B + c;
         tmax[o] = a;
