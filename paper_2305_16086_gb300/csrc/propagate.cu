@@ -1751,7 +1751,9 @@ static void all_edges_impl(sc_graph *g, const sc_options *o_in, double *s_hat, d
     // windowed blocks (the frontier as an interval) when the graph's bandwidth
     // keeps a block's last window under half the graph, or when asked for
     const int32_t beta = ensure_bandwidth(g);
-    const int32_t Lmax = ell_global + (record_after ? 2 : 0);
+    // the longest run of the first pass (a learned length's cap is reached only by extensions,
+    // which rerun few sources; the windows and the launch shape are chosen for the first pass)
+    const int32_t Lmax = (len.empty() ? 0 : *std::max_element(len.begin(), len.end())) + (record_after ? 2 : 0);
     const bool use_win = !plus && o.rows_split != -1 && !(o.flags & SC_OPT_WINDOWS_OFF) &&
                          ((o.flags & SC_OPT_WINDOWS_FORCE) ||
                           2.0 * (Lmax + 1.0) * static_cast<double>(beta) + 128.0 < 0.5 * static_cast<double>(n));
