@@ -202,3 +202,38 @@ def test_caltau_arm_section(fake_cuda, monkeypatch):
     assert c["source_hops"] == 7 * 240 and c["eq6"]["source_hops"] == 301 * 240 and c["value"] > 0
     d = _run(fake_cuda, ["--steps", "1", "--warmup", "3", "--no-e2e", "--no-arms"])
     assert d["caltau"] is None
+
+
+@pytest.mark.parametrize("need,cap", [(67, 1023), (1, 1023), (1023, 1023), (5, 7)])
+def test_empirical_length_is_the_least_odd_length_within_eps(monkeypatch, need, cap):
+    """The lattice's global judge: bisection over odd lengths with a series
+    that grows with the length (errors fall below eps from `need` on) returns
+    `need`, and None when even the cap is not within eps."""
+    import bench
+    from paper_2305_16086_gb300 import binding
+
+    r = np.array([1.0, 2.0])
+    calls = []
+
+    def fake_some_edges(G, entries, **kw):
+        ell = kw["ell_fixed"]
+        calls.append(ell)
+        err = 0.5 if ell < need else 0.0  # monotone in the length, like the end-corrected series
+        return r - err, {}
+
+    monkeypatch.setattr(binding, "some_edges", fake_some_edges)
+    ref = {"k": np.array([0, 1]), "r": r}
+    got = bench.empirical_length(None, ref, 1e-2, cap, dict(eps=1e-2))
+    assert got == need and all(c % 2 == 1 for c in calls)
+    assert len(calls) <= 12  # a bisection, not a scan
+    monkeypatch.setattr(binding, "some_edges", lambda G, e, **kw: (r - 1.0, {}))
+    assert bench.empirical_length(None, ref, 1e-2, cap, dict(eps=1e-2)) is None
+
+
+def test_errors_at_uses_the_sampled_entries():
+    import bench
+
+    ref = {"k": np.array([2, 0]), "r": np.array([0.5, 0.25])}
+    e = bench.errors_at(ref, np.array([0.2, 9.0, 0.45]))
+    assert e["sampled_edges"] == 2
+    assert e["max_abs_err"] == pytest.approx(0.05) and e["mean_abs_err"] == pytest.approx(0.05)
