@@ -43,7 +43,7 @@ def test_options_default():
     o = binding.Options()
     binding.load().sc_options_default(ctypes.byref(o))
     assert o.eps == 1e-3 and o.mode == 0 and o.precision == 1 and o.ell_policy == 0 and o.gamma == 10
-    assert o.bf16_from_hop == 0 and o.flags == 0 and o.switch_rule == 0
+    assert o.bf16_from_hop == 0 and o.flags == 0 and o.switch_rule == 0 and o.ell_cap == 0
 
 
 def test_binding_marshals_every_option():
@@ -51,11 +51,15 @@ def test_binding_marshals_every_option():
     o = binding.Graph.options(eps=2e-3, mode="tgt_plus", precision="bf16", policy="fixed", ell_fixed=9,
                               estimator="end_corrected", block_width=64, rows_split=-1, heavy_threshold=99,
                               max_slices=3, record_tail=True, time_kernels=True, seed=7, delta=0.5, gamma=4,
-                              switch="paper", windows=True, bf16_from_hop=5)
+                              switch="paper", windows=True, bf16_from_hop=5, ell_cap=1023,
+                              sparse_hops=True, full_topgamma_scan=True)
     assert (o.eps, o.mode, o.precision, o.ell_policy, o.ell_fixed, o.estimator) == (2e-3, 1, 2, 2, 9, 1)
     assert (o.block_width, o.rows_split, o.heavy_threshold, o.max_slices) == (64, -1, 99, 3)
-    assert o.flags == binding.SC_OPT_RECORD_TAIL | binding.SC_OPT_TIME_KERNELS | binding.SC_OPT_WINDOWS_FORCE
-    assert (o.seed, o.delta, o.gamma, o.switch_rule, o.bf16_from_hop) == (7, 0.5, 4, 1, 5)
+    assert o.flags == (binding.SC_OPT_RECORD_TAIL | binding.SC_OPT_TIME_KERNELS | binding.SC_OPT_WINDOWS_FORCE |
+                       binding.SC_OPT_SPARSE_HOPS | binding.SC_OPT_FULL_TOPGAMMA_SCAN)
+    assert (o.seed, o.delta, o.gamma, o.switch_rule, o.bf16_from_hop, o.ell_cap) == (7, 0.5, 4, 1, 5, 1023)
+    t = binding.MlpTrainOpts(300, 1e-2, 0.0, 0.0, 0.0, binding.PREC["fp32"], 1e-3, 4095, 0)
+    assert (t.epochs, t.precision, t.eps, t.ell_cap) == (300, 1, 1e-3, 4095)
     assert binding.Graph.options(windows=False).flags == binding.SC_OPT_WINDOWS_OFF
     assert binding.Graph.options().flags == 0
 
