@@ -88,6 +88,10 @@ TGTPLUS = [
     ("frontier = degree of the exact reach", lambda: tt.test_frontier_volume_is_the_degree_of_the_exact_reach(
         lambda: gg.lollipop(6, 4))),
     ("per-source switch", tt.test_per_source_switch_is_the_first_hop_where_eq14_holds),
+    ("even-hop bound vs the exact tail",
+     lambda: tt.test_even_hop_bound_holds_against_the_exact_tail(lambda: gg.barbell(6, 2))),
+    ("learned TGT+ at the cap", tt.test_learned_tgt_plus_at_the_cap_is_per_source_tgt_plus),
+    ("learned TGT+ extends short lengths", lambda: tt.test_learned_tgt_plus_extends_short_lengths_and_meets_eps(1)),
 ]
 
 LEARNED = [
@@ -300,6 +304,10 @@ PY_MUTANTS = [
     ("tgtplus", "source column pushed over the sender's degree", "tgtplus",
      "            q[nb] += p[v] / deg[nb]\n        p = q\n    return p",
      "            q[nb] += p[v] / deg[v]\n        p = q\n    return p"),
+    ("tgtplus", "even-hop bound one power of lambda too many", "tgtplus",
+     "    for _ in range(tau + 1 - ell):\n        f *= lam_star", "    for _ in range(tau + 2 - ell):\n        f *= lam_star"),
+    ("tgtplus", "even-hop bound over 1 - lambda^2", "tgtplus",
+     "    return f / (1.0 - lam_star) * t_l", "    return f / (1.0 - lam_star * lam_star) * t_l"),
     ("tgtplus", "Eq. 15 without the factor L", "tgtplus",
      "return 2.0 * L * (p.max() - p.min())", "return 2.0 * (p.max() - p.min())"),
     # learned.py
